@@ -1,0 +1,190 @@
+/*
+ * tpg.h -- C ABI of the GB300 prime-path / test-path library (libtpg.so).
+ *
+ * The library computes, for a control-flow graph G = (V, E) with a start
+ * vertex s and an end vertex e, the output of Problem 1 of the TPGen paper
+ * (Sec. 3): every prime path (PP) of G -- a maximal simple path, Def. 1,
+ * where a simple path may repeat only its first vertex as its last (Sec. 2)
+ * -- and a set of test paths (TPs), entry-to-exit paths that tour every PP.
+ *
+ * All compute runs in hand-written sm_103a CUDA kernels.  Entry points take
+ * plain host or device pointers and sizes; no C++ or framework type crosses
+ * this boundary.
+ *
+ * Conventions
+ *  - Vertex ids are 0..n-1.  A graph is given as int32 CSR of successor
+ *    lists: row_ptr[n+1] (row_ptr[0] = 0, non-decreasing) and col[m]
+ *    (col[row_ptr[u] .. row_ptr[u+1]) = successors of u, strictly ascending,
+ *    each in 0..n-1).  This is the CSR the paper stores on the device
+ *    (Sec. 4.1); the library derives the predecessor lists itself.
+ *  - Out-degree is not limited to 2 (the paper's restriction, Sec. 3, is a
+ *    convenience of its kernel, not of the problem).
+ *  - Canonical order of a path list: lexicographic on the int32 vertex
+ *    sequences, a proper prefix first.  A simple cycle is written with its
+ *    first vertex repeated at the end (<2,3,4,8,2> in Def. 1).  Rotations of
+ *    one cycle are distinct PPs.
+ *  - Every function returns TPG_OK (0) or a negative TPG_E* code; on error
+ *    an output handle pointer is set to NULL.  tpg_strerror() names a code.
+ *  - A handle is not to be used from two host threads at once.  Work is
+ *    issued on the handle's CUDA stream (tpg_set_stream); calls return only
+ *    after their results are complete.
+ */
+#ifndef TPG_H
+#define TPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPG_OK 0
+#define TPG_EINVAL (-1)    /* malformed input (see tpg_load_cfg) */
+#define TPG_EUNREACH (-2)  /* a PP vertex is unreachable from entry or cannot reach exit */
+#define TPG_ETOOBIG (-3)   /* n above TPG_MAX_N, or a level beyond int32 indexing */
+#define TPG_ENOMEM (-4)    /* device or pinned host allocation failed */
+#define TPG_ECUDA (-5)     /* a CUDA runtime call failed */
+#define TPG_ETIMEOUT (-6)  /* a bounded device-side wait ran out */
+#define TPG_EHANDLE (-7)   /* NULL or foreign handle */
+
+#define TPG_MAX_N 4096     /* vertices per graph (bitset of 128 words) */
+
+/* where tpg_paths arrays live */
+#define TPG_RESULT_HOST 0   /* page-locked host memory (default) */
+#define TPG_RESULT_DEVICE 1 /* device memory of the handle's GPU */
+
+typedef struct tpg_cfg tpg_cfg; /* opaque: device copy of the graph(s) + tables */
+
+/* A path list owned by the library; release it with tpg_free(). */
+typedef struct tpg_paths {
+    uint32_t magic;                 /* internal tag */
+    int32_t num_graphs;             /* 1 for tpg_load_cfg handles */
+    int64_t num_paths;              /* P */
+    int32_t location;               /* TPG_RESULT_HOST or TPG_RESULT_DEVICE */
+    int32_t reserved;
+    const int64_t *graph_path_ptr;  /* [num_graphs+1]: paths of graph g are
+                                       [graph_path_ptr[g], graph_path_ptr[g+1]) */
+    const int64_t *offsets;         /* [P+1], offsets[0] = 0 */
+    const int32_t *vertices;        /* [offsets[P]], graph-local vertex ids, canonical order per graph */
+} tpg_paths;
+
+/* Statistics of the last tpg_prime_paths call on a handle. */
+typedef struct tpg_stats {
+    int64_t simple_paths;       /* frontier nodes enumerated (simple paths incl. closed cycles) */
+    int64_t prime_paths;        /* P */
+    int64_t pp_vertices;        /* total vertex ids in the PP list */
+    int32_t levels;             /* frontier levels processed */
+    int32_t pp_levels;          /* levels that held at least one PP */
+    int64_t peak_level_nodes;   /* largest frontier level */
+    int64_t arena_bytes_used;   /* persistent path arena bytes written */
+    int64_t arena_bytes_alloc;  /* path arena bytes allocated */
+    int64_t frontier_bytes_alloc; /* ping-pong frontier bytes allocated */
+    int32_t attempts;           /* 1 + overflow retries */
+    int32_t bitset_words;       /* W: 32-bit words of the visited bitset */
+    int64_t test_paths;         /* TPs after dedup (last tpg_test_paths) */
+    int64_t tp_vertices;
+} tpg_stats;
+
+/*
+ * tpg_load_cfg -- validate one CFG and copy it to the device.
+ *
+ * Problem 1 input (Sec. 3): G, start vertex `entry`, end vertex `exit`.
+ * row_ptr[n+1] and col[row_ptr[n]] are HOST pointers; the caller keeps them.
+ * The call builds, on the device, the predecessor CSR and the all-pairs BFS
+ * tables (distance and lowest-id predecessor) used by tpg_test_paths.
+ *
+ * TPG_EINVAL if: n < 1; row_ptr[0] != 0 or row_ptr decreasing; a col entry
+ * outside 0..n-1; a successor list not strictly ascending (duplicate arc);
+ * entry or exit outside 0..n-1 or entry == exit; in-degree(entry) != 0 or
+ * out-degree(exit) != 0 (Sec. 3).  TPG_ETOOBIG if n > TPG_MAX_N.
+ * Self-loops are accepted.  On success *out owns device memory until
+ * tpg_free(*out).
+ */
+int tpg_load_cfg(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                 int32_t entry, int32_t exit, tpg_cfg **out);
+
+/*
+ * tpg_load_cfg_device -- as tpg_load_cfg, but row_ptr and col are DEVICE
+ * pointers (read on the handle's stream, copied into the handle) and the
+ * validation runs in a kernel.  `m` is the arc count (col length); `stream`
+ * is a cudaStream_t (NULL = legacy default stream) that also becomes the
+ * handle's stream.
+ */
+int tpg_load_cfg_device(int32_t n, int32_t m, const int32_t *row_ptr_dev,
+                        const int32_t *col_dev, int32_t entry, int32_t exit,
+                        void *stream, tpg_cfg **out);
+
+/*
+ * tpg_load_cfg_batch -- many independent CFGs in one handle.
+ *
+ * Graph g has n_per_graph[g] vertices with LOCAL ids; its CSR is
+ * row_ptr_cat[R_g .. R_g + n_g] (local arc offsets starting at 0) and
+ * col_cat[C_g .. C_g + m_g) with R_g = sum_{h<g} (n_h + 1) and
+ * C_g = sum_{h<g} m_h.  entries[g], exits[g] are local ids.  All HOST
+ * pointers.  Each graph is validated as in tpg_load_cfg (the first failing
+ * graph's error is returned).  Results of tpg_prime_paths / tpg_test_paths
+ * on a batch handle carry graph_path_ptr[G+1] and graph-local vertex ids.
+ */
+int tpg_load_cfg_batch(int32_t num_graphs, const int32_t *n_per_graph,
+                       const int32_t *row_ptr_cat, const int32_t *col_cat,
+                       const int32_t *entries, const int32_t *exits,
+                       tpg_cfg **out);
+
+/*
+ * tpg_prime_paths -- every PP of the graph(s) in canonical order.
+ *
+ * Def. 1 (maximal simple path).  The method: level-synchronous extension of
+ * all simple paths from every vertex (the paper's Alg. 2 seeds v.list = {v}
+ * for every v), primality by the can't-extend-at-either-end rule (Alg. 3
+ * prune step), cycle closing as in Alg. 4, then a canonical ordering.
+ * *out is allocated by the library (location per tpg_set_result_location)
+ * and released with tpg_free.  May retry internally with a larger path
+ * arena when the arena overflows; results never depend on the arena size.
+ */
+int tpg_prime_paths(tpg_cfg *g, tpg_paths **out);
+
+/*
+ * tpg_test_paths -- the TP set touring every PP (Problem 1 output).
+ *
+ * TP(p) = path(entry -> first p), then p, then path(last p -> exit), joined
+ * at shared endpoints, where path(a -> b) is read backwards from b through
+ * the BFS table P[a][x] = lowest-id u with (u, x) in E and
+ * d(a, u) = d(a, x) - 1.  The TP set is the canonical-order, duplicate-free
+ * set {TP(p)}.  Runs tpg_prime_paths internally if needed.
+ * TPG_EUNREACH if some PP cannot be toured.
+ */
+int tpg_test_paths(tpg_cfg *g, tpg_paths **out);
+
+/* Release a tpg_cfg* or tpg_paths* (tag-checked).  NULL is a no-op. */
+void tpg_free(void *handle);
+
+/* Issue the handle's work on `stream` (a cudaStream_t; NULL = default). */
+int tpg_set_stream(tpg_cfg *g, void *stream);
+
+/* TPG_RESULT_HOST (default) or TPG_RESULT_DEVICE for later results. */
+int tpg_set_result_location(tpg_cfg *g, int32_t location);
+
+/*
+ * Device allocator used for all device buffers of all handles created
+ * after the call (NULL, NULL restores cudaMallocAsync/cudaFreeAsync on the
+ * handle stream).  alloc(bytes, stream, ctx) returns a device pointer or
+ * NULL; release(ptr, stream, ctx) frees it.
+ */
+typedef void *(*tpg_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*tpg_release_fn)(void *ptr, void *stream, void *ctx);
+int tpg_set_allocator(tpg_alloc_fn alloc, tpg_release_fn release, void *ctx);
+
+/* Statistics of the handle's last calls. */
+int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);
+
+/* Static text for an error code. */
+const char *tpg_strerror(int code);
+
+/* Library version string. */
+const char *tpg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPG_H */
