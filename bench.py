@@ -1,0 +1,378 @@
+"""Benchmark: prime paths emitted per second on the 2^22-path diamond chain.
+
+One step = the whole hot path on one graph: load + validate + predecessor CSR
++ all-pairs BFS tables (device-resident input), the level-synchronous
+frontier with compaction and primality, canonical ordering and
+materialisation of the prime paths, and test-path assembly with canonical
+sort/dedup.  Workload: a chain of k=22 if-else diamonds (67 vertices, 88
+arcs), 4,194,304 prime paths of 45 vertices, 67,108,695 simple paths.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun each rank runs an independent replica
+(the single graph is not sharded), so per-GPU work is fixed: weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "prime paths emitted/sec"
+UNIT = "PP/s"
+K_DIAMONDS = 22
+ALG_BYTES_PER_NODE = 16  # lean frontier: int32 parent + int32 last vertex, written once and read once
+PROFILE = os.path.join(ROOT, "profiles", "enumerate_kernel_diamond22_traffic.txt")
+
+
+def workload():
+    from paper_2210_16998_gb300 import cfggen
+
+    return cfggen.diamond_chain(K_DIAMONDS)
+
+
+def config_dict(extra=None):
+    d = {"workload": f"diamond-chain k={K_DIAMONDS} (67 vertices, 88 arcs, 4,194,304 PPs x 45 vertices)",
+         "graphs": 1, "vertices": 67, "arcs": 88,
+         "step": "load+validate+BFS tables, frontier/compaction/primality, canonical order, PP materialise, "
+                 "TP assembly + sort/dedup",
+         "l2": "inputs > L2: arena + frontier + PP/TP outputs ~2.9 GB per step >> 129 MB L2"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    for f in ("enumerate.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2210_16998_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the frontier kernel from the committed ncu summary,
+    or None if that summary was taken on a different kernel source."""
+    if not os.path.exists(PROFILE):
+        return None
+    kv = {}
+    with open(PROFILE) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha256_16") != kernel_source_digest():
+        return None
+    try:
+        return int(float(kv["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def closed_form_check(pp):
+    """Sampled outputs against the closed form of the diamond chain: PP j in
+    canonical order takes b_i (3i+2) at diamond i iff bit (k-1-i) of j is set."""
+    import torch
+
+    P = pp.num_paths
+    assert P == 2 ** K_DIAMONDS, P
+    idx = torch.tensor([0, 1, 2, 12345, P // 3, P // 2, P - 2, P - 1], device="cuda")
+    off = pp.offsets[idx].cpu().numpy()
+    assert np.all(off == idx.cpu().numpy() * (2 * K_DIAMONDS + 1))
+    for j, o in zip(idx.cpu().numpy(), off):
+        seq = pp.vertices[int(o):int(o) + 2 * K_DIAMONDS + 1].cpu().numpy()
+        exp = [0]
+        for i in range(K_DIAMONDS):
+            exp += [3 * i + (2 if (int(j) >> (K_DIAMONDS - 1 - i)) & 1 else 1), 3 * i + 3]
+        assert list(seq) == exp, (j, seq, exp)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2210_16998_gb300 import tpg
+
+    torch.cuda.set_device(local_rank)
+    tpg.load_library(build=True)
+    cfg = workload()
+    rp = torch.as_tensor(cfg.row_ptr, device="cuda")
+    col = torch.as_tensor(cfg.col, device="cuda")
+
+    def step(check=False):
+        h = tpg.tpg_load_cfg_device(cfg.n, cfg.m, rp, col, cfg.entry, cfg.exit)
+        pp = tpg.tpg_prime_paths(h)
+        if check:
+            closed_form_check(pp)
+        tp = tpg.tpg_test_paths(h)
+        if check:
+            assert tp.num_paths == pp.num_paths  # every PP already runs entry -> exit
+            assert torch.equal(tp.vertices, pp.vertices)
+        st = tpg.tpg_get_stats(h)
+        P = pp.num_paths
+        pp.free()
+        tp.free()
+        h.close()
+        return P, st
+
+    for i in range(args.warmup):
+        step(check=(i == 0))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    launches0 = tpg.tpg_kernel_launches()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    stats, total_pp = [], 0
+    for _ in range(args.steps):
+        P, st = step()
+        total_pp += P
+        stats.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = tpg.tpg_kernel_launches() - launches0
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * total_pp / (ms / 1000.0)
+
+    # e2e through the C ABI with host buffers (H2D of the CSR, D2H of both results)
+    e2e_steps = max(3, args.steps // 4)
+    bi = int(cfg.row_ptr.nbytes + cfg.col.nbytes)
+    bo = 0
+
+    def e2e_step():
+        h = tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=tpg.TPG_RESULT_HOST)
+        pp = tpg.tpg_prime_paths(h)
+        tp = tpg.tpg_test_paths(h)
+        nbytes = 0
+        for r in (pp, tp):
+            nbytes += r.graph_path_ptr.nbytes + r.offsets.nbytes + r.vertices.nbytes
+        P = pp.num_paths
+        pp.free()
+        tp.free()
+        h.close()
+        return P, nbytes
+
+    e2e_step()  # warm the pinned pool
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_pp = 0
+    for _ in range(e2e_steps):
+        P, bo = e2e_step()
+        e2e_pp += P
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * e2e_pp / float(te.item())
+
+    if rank != 0:
+        return None
+    peak, peak_kind = measured_peaks()
+    t_enum = statistics.mean(s["t_enumerate_ms"] for s in stats)
+    nodes = stats[-1]["simple_paths"]
+    achieved = ALG_BYTES_PER_NODE * nodes / (t_enum / 1000.0) / 1e9
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded diamond-chain CFG)",
+        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": int(bo),
+                "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "enumerate_kernel", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "alg_bytes_per_launch": ALG_BYTES_PER_NODE * nodes,
+                     "launch_ms": t_enum},
+        "phases_ms": {"enumerate": t_enum, "order_materialise": statistics.mean(s["t_order_ms"] for s in stats),
+                      "test_paths": statistics.mean(s["t_test_paths_ms"] for s in stats)},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_budget)
+    return line
+
+
+def cpu_baseline(cfg, budget_s=12.0, min_runs=2):
+    """The oracle, as it stands, on the host cores: PPs + TPs of the same graph."""
+    import oracle
+
+    oracle.build()
+    times, P = [], 0
+    t_start = time.perf_counter()
+    while len(times) < min_runs or time.perf_counter() - t_start < budget_s:
+        t0 = time.perf_counter()
+        r = oracle.run_cfg(cfg, test_paths=True)
+        times.append(time.perf_counter() - t0)
+        P = r.num_pp
+        if len(times) >= 50:
+            break
+    return {"value": P / statistics.mean(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"full workload (PPs + TPs of the k=22 diamond chain), {len(times)} runs, "
+                      f"mean {statistics.mean(times):.3f} s, single-threaded C -O2",
+            "host": host_cpu()}
+
+
+def host_cpu():
+    name = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    name = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": name, "machine": os.uname().machine}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    cfg = workload()
+    for _ in range(args.warmup):
+        oracle.run_cfg(cfg, test_paths=True)
+    times, P = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.run_cfg(cfg, test_paths=True)
+        times.append(time.perf_counter() - t0)
+        P = r.num_pp
+    total = sum(times)
+    value = args.steps * P / total
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded diamond-chain CFG)",
+        "config": config_dict({"parallelism": "host CPU, 1 thread"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"full workload per step (PPs + TPs), {args.steps} steps", "host": host_cpu()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,6 +84,10 @@ typedef struct tpg_stats {
     int32_t bitset_words;       /* W: 32-bit words of the visited bitset */
     int64_t test_paths;         /* TPs after dedup (last tpg_test_paths) */
     int64_t tp_vertices;
+    float t_enumerate_ms;       /* device time of the frontier launch (CUDA events) */
+    float t_order_ms;           /* device time of ordering + materialisation */
+    float t_test_paths_ms;      /* device time of the last tpg_test_paths pipeline */
+    int32_t enumerate_grid;     /* blocks of the persistent frontier launch */
 } tpg_stats;
 
 /*
@@ -177,6 +181,9 @@ int tpg_set_allocator(tpg_alloc_fn alloc, tpg_release_fn release, void *ctx);
 
 /* Statistics of the handle's last calls. */
 int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t tpg_kernel_launches(void);
 
 /* Static text for an error code. */
 const char *tpg_strerror(int code);

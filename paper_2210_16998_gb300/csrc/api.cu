@@ -1,0 +1,1035 @@
+// C ABI of libtpg: handles, memory, validation and the host-side order of
+// kernel launches.  No arithmetic of the method runs here; the host only
+// sizes buffers, reads level counts back once per call and issues kernels.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace tpg;
+
+namespace tpg {
+std::atomic<long long> g_kernel_launches{0};
+}
+
+namespace {
+
+constexpr uint32_t MAGIC_CFG = 0x54504743u;    // "TPGC"
+constexpr uint32_t MAGIC_PATHS = 0x54504750u;  // "TPGP"
+constexpr uint32_t MAGIC_DEAD = 0xDEADBEEFu;
+
+struct AllocFns {
+    tpg_alloc_fn alloc = nullptr;
+    tpg_release_fn release = nullptr;
+    void *ctx = nullptr;
+};
+
+std::mutex g_alloc_mu;
+AllocFns g_alloc;
+
+void *dev_alloc(const AllocFns &f, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    if (f.alloc) return f.alloc(bytes, (void *)s, f.ctx);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_release(const AllocFns &f, void *p, cudaStream_t s) {
+    if (!p) return;
+    if (f.release) f.release(p, (void *)s, f.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+// A device buffer owned by a handle; grows on demand, contents not kept.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <typename T>
+    T *as() const { return (T *)p; }
+};
+
+// Reference-counted device block, shared by a handle's cache and results.
+struct Block {
+    void *p = nullptr;
+    size_t bytes = 0;
+    AllocFns fns;
+    cudaStream_t stream = nullptr;
+    std::atomic<int> refs{1};
+};
+
+Block *block_new(const AllocFns &f, size_t bytes, cudaStream_t s) {
+    void *p = dev_alloc(f, bytes, s);
+    if (!p) return nullptr;
+    Block *b = new Block();
+    b->p = p;
+    b->bytes = bytes;
+    b->fns = f;
+    b->stream = s;
+    return b;
+}
+void block_ref(Block *b) {
+    if (b) b->refs.fetch_add(1);
+}
+void block_unref(Block *b) {
+    if (b && b->refs.fetch_sub(1) == 1) {
+        dev_release(b->fns, b->p, b->stream);
+        delete b;
+    }
+}
+
+// Process-wide pool of page-locked host blocks for host results.
+struct PinnedPool {
+    std::mutex mu;
+    std::multimap<size_t, void *> free_blocks;  // capacity -> ptr
+    std::map<void *, size_t> cap;
+    size_t cached = 0;
+    static constexpr size_t LIMIT = (size_t)8 << 30;
+
+    void *get(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = free_blocks.lower_bound(bytes);
+        if (it != free_blocks.end() && it->first <= bytes * 2 + ((size_t)4 << 20)) {
+            void *p = it->second;
+            cached -= it->first;
+            free_blocks.erase(it);
+            return p;
+        }
+        const size_t c = (bytes + ((size_t)2 << 20) - 1) & ~(((size_t)2 << 20) - 1);
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cap[p] = c;
+        return p;
+    }
+    void put(void *p) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        const size_t c = cap[p];
+        if (cached + c <= LIMIT) {
+            free_blocks.emplace(c, p);
+            cached += c;
+        } else {
+            cap.erase(p);
+            cudaFreeHost(p);
+        }
+    }
+};
+PinnedPool &pinned() {
+    static PinnedPool *pool = new PinnedPool();  // never destroyed: freed with the process
+    return *pool;
+}
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return TPG_OK;
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return TPG_ENOMEM;
+    return TPG_ECUDA;
+}
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t _e = (x);                   \
+        if (_e != cudaSuccess) return cuda_err(_e); \
+    } while (0)
+#define RC(x)                         \
+    do {                              \
+        int _r = (x);                 \
+        if (_r != TPG_OK) return _r;  \
+    } while (0)
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle and result objects
+// ---------------------------------------------------------------------------
+struct PathsImpl {
+    tpg_paths pub;  // first member: a tpg_paths* is a PathsImpl*
+    int location = TPG_RESULT_HOST;
+    void *host[3] = {nullptr, nullptr, nullptr};
+    Block *dev[3] = {nullptr, nullptr, nullptr};
+};
+
+struct tpg_cfg {
+    uint32_t magic = MAGIC_CFG;
+    int device = 0;
+    int num_sms = 1;
+    cudaStream_t stream = nullptr;
+    AllocFns fns;
+    int location = TPG_RESULT_HOST;
+
+    int N = 0, G = 0, maxn = 0, W = 1, max_levels = 0;
+    long long M = 0;
+    std::vector<int> h_vbase;
+
+    DevBuf rp, col, prp, pcol, vgraph, vbase, entry, exitv, tbl_base, dist, pred;
+    DevBuf pre_len, suf_len, pre_off, suf_off, pre_seq, suf_seq;
+    GraphDev gd{};
+
+    // enumeration workspace
+    DevBuf nodes, tfl[2], tvis[2], pp_refs, levels, status, tile_ctr, ctl;
+    long long node_cap = 0, lvl_cap = 0, pp_cap = 0, status_cap = 0;
+    // generic scratch
+    DevBuf s_keys[2], s_refs[2], s_len, s_tmp, s_i32[3], s_i64[4];
+
+    // cached PP list on the device (shared with device results)
+    Block *pp_off = nullptr, *pp_vert = nullptr, *pp_graph = nullptr, *pp_gptr = nullptr;
+    long long P = 0, V = 0;
+    bool pp_valid = false;
+
+    tpg_stats stats{};
+    cudaEvent_t ev[6] = {};
+    std::vector<LevelRec> h_levels;
+    int *h_small = nullptr;  // pinned staging for small read-backs (4 KB)
+};
+
+namespace {
+
+int ensure(tpg_cfg *g, DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return TPG_OK;
+    dev_release(g->fns, b.p, g->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+    const size_t want = bytes + bytes / 4;
+    b.p = dev_alloc(g->fns, want, g->stream);
+    if (!b.p) return TPG_ENOMEM;
+    b.bytes = want;
+    return TPG_OK;
+}
+
+void release(tpg_cfg *g, DevBuf &b) {
+    dev_release(g->fns, b.p, g->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+void drop_cache(tpg_cfg *g) {
+    block_unref(g->pp_off);
+    block_unref(g->pp_vert);
+    block_unref(g->pp_graph);
+    block_unref(g->pp_gptr);
+    g->pp_off = g->pp_vert = g->pp_graph = g->pp_gptr = nullptr;
+    g->pp_valid = false;
+}
+
+void destroy_cfg(tpg_cfg *g) {
+    cudaStreamSynchronize(g->stream);
+    drop_cache(g);
+    DevBuf *all[] = {&g->rp, &g->col, &g->prp, &g->pcol, &g->vgraph, &g->vbase, &g->entry, &g->exitv,
+                     &g->tbl_base, &g->dist, &g->pred, &g->pre_len, &g->suf_len, &g->pre_off, &g->suf_off,
+                     &g->pre_seq, &g->suf_seq, &g->nodes, &g->tfl[0], &g->tfl[1], &g->tvis[0], &g->tvis[1],
+                     &g->pp_refs, &g->levels, &g->status, &g->tile_ctr, &g->ctl, &g->s_keys[0], &g->s_keys[1],
+                     &g->s_refs[0], &g->s_refs[1], &g->s_len, &g->s_tmp, &g->s_i32[0], &g->s_i32[1],
+                     &g->s_i32[2], &g->s_i64[0], &g->s_i64[1], &g->s_i64[2], &g->s_i64[3]};
+    for (DevBuf *b : all) release(g, *b);
+    cudaStreamSynchronize(g->stream);
+    if (g->h_small) cudaFreeHost(g->h_small);
+    for (cudaEvent_t e : g->ev)
+        if (e) cudaEventDestroy(e);
+    g->magic = MAGIC_DEAD;
+    delete g;
+}
+
+int validate_host(int n, const int32_t *rp, const int32_t *col, int entry, int exit) {
+    if (n < 1 || !rp) return TPG_EINVAL;
+    if (n > TPG_MAX_N) return TPG_ETOOBIG;
+    if (rp[0] != 0) return TPG_EINVAL;
+    for (int u = 0; u < n; ++u)
+        if (rp[u + 1] < rp[u]) return TPG_EINVAL;
+    if (rp[n] > 0 && !col) return TPG_EINVAL;
+    if (entry < 0 || entry >= n || exit < 0 || exit >= n || entry == exit) return TPG_EINVAL;
+    for (int u = 0; u < n; ++u) {
+        for (int e = rp[u]; e < rp[u + 1]; ++e) {
+            const int w = col[e];
+            if (w < 0 || w >= n) return TPG_EINVAL;
+            if (e > rp[u] && w <= col[e - 1]) return TPG_EINVAL;  // unsorted or duplicate arc
+            if (w == entry) return TPG_EINVAL;                    // in-degree(entry) != 0
+        }
+    }
+    if (rp[exit + 1] != rp[exit]) return TPG_EINVAL;  // out-degree(exit) != 0
+    return TPG_OK;
+}
+
+int new_cfg(void *stream, tpg_cfg **out) {
+    tpg_cfg *g = new tpg_cfg();
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        g->fns = g_alloc;
+    }
+    g->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess ||
+        cudaHostAlloc((void **)&g->h_small, 4096, cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreate(&g->ev[0]) || cudaEventCreate(&g->ev[1]) || cudaEventCreate(&g->ev[2]) ||
+        cudaEventCreate(&g->ev[3]) || cudaEventCreate(&g->ev[4]) || cudaEventCreate(&g->ev[5])) {
+        cudaGetLastError();
+        delete g;
+        return TPG_ECUDA;
+    }
+    *out = g;
+    return TPG_OK;
+}
+
+// Predecessor CSR, BFS tables and tour tables (everything after the union
+// CSR, vgraph/vbase and entry/exit are on the device).
+int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h) {
+    cudaStream_t s = g->stream;
+    g->W = bitset_words_supported(g->maxn);
+    if (g->W < 0) return TPG_ETOOBIG;
+    g->max_levels = g->maxn + 4;
+    RC(ensure(g, g->prp, sizeof(int) * (g->N + 1)));
+    RC(ensure(g, g->pcol, sizeof(int) * std::max<long long>(g->M, 1)));
+    RC(ensure(g, g->tbl_base, sizeof(long long) * tbl_base_h.size()));
+    const long long tbl = tbl_base_h.back();
+    RC(ensure(g, g->dist, sizeof(int) * std::max<long long>(tbl, 1)));
+    RC(ensure(g, g->pred, sizeof(int) * std::max<long long>(tbl, 1)));
+    RC(ensure(g, g->pre_len, sizeof(int) * g->N));
+    RC(ensure(g, g->suf_len, sizeof(int) * g->N));
+    RC(ensure(g, g->pre_off, sizeof(long long) * (g->N + 1)));
+    RC(ensure(g, g->suf_off, sizeof(long long) * (g->N + 1)));
+    RC(ensure(g, g->s_i32[0], sizeof(int) * (g->N + 1)));
+    RC(ensure(g, g->s_i64[0], sizeof(long long) * (g->N + 2)));
+    RC(ensure(g, g->s_tmp, sizeof(long long) * scan_tmp_elems(g->N + 1)));
+    CK(cudaMemcpyAsync(g->tbl_base.p, tbl_base_h.data(), sizeof(long long) * tbl_base_h.size(),
+                       cudaMemcpyHostToDevice, s));
+
+    GraphDev &d = g->gd;
+    d = GraphDev{};
+    d.N = g->N;
+    d.G = g->G;
+    d.maxn = g->maxn;
+    d.W = g->W;
+    d.M = g->M;
+    d.rp = g->rp.as<int>();
+    d.col = g->col.as<int>();
+    d.prp = g->prp.as<int>();
+    d.pcol = g->pcol.as<int>();
+    d.vgraph = g->G > 1 ? g->vgraph.as<int>() : nullptr;
+    d.vbase = g->vbase.as<int>();
+    d.entry = g->entry.as<int>();
+    d.exit = g->exitv.as<int>();
+    d.tbl_base = g->tbl_base.as<long long>();
+    d.dist = g->dist.as<int>();
+    d.pred = g->pred.as<int>();
+    d.pre_len = g->pre_len.as<int>();
+    d.suf_len = g->suf_len.as<int>();
+    d.pre_off = g->pre_off.as<long long>();
+    d.suf_off = g->suf_off.as<long long>();
+
+    CK(build_pred_csr(d, g->prp.as<int>(), g->pcol.as<int>(), g->s_i32[0].as<int>(), g->s_tmp.as<long long>(),
+                      g->s_i64[0].as<long long>(), s));
+    CK(bfs_all_pairs(d, s));
+    CK(tour_lengths(d, g->s_tmp.as<long long>(), s));
+    long long *h = (long long *)g->h_small;
+    CK(cudaMemcpyAsync(h, d.pre_off + g->N, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h + 1, d.suf_off + g->N, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const long long npre = h[0], nsuf = h[1];
+    RC(ensure(g, g->pre_seq, sizeof(int) * std::max<long long>(npre, 1)));
+    RC(ensure(g, g->suf_seq, sizeof(int) * std::max<long long>(nsuf, 1)));
+    d.pre_seq = g->pre_seq.as<int>();
+    d.suf_seq = g->suf_seq.as<int>();
+    CK(tour_fill(d, s));
+    CK(cudaStreamSynchronize(s));
+    return TPG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// prime paths
+// ---------------------------------------------------------------------------
+int alloc_workspace(tpg_cfg *g) {
+    const int W = g->W;
+    RC(ensure(g, g->nodes, sizeof(int2) * g->node_cap));
+    for (int b = 0; b < 2; ++b) {
+        RC(ensure(g, g->tfl[b], sizeof(int2) * g->lvl_cap));
+        RC(ensure(g, g->tvis[b], sizeof(unsigned) * (size_t)W * g->lvl_cap));
+    }
+    RC(ensure(g, g->pp_refs, sizeof(int) * g->pp_cap));
+    RC(ensure(g, g->levels, sizeof(LevelRec) * g->max_levels));
+    RC(ensure(g, g->status, sizeof(unsigned long long) * g->status_cap));
+    RC(ensure(g, g->tile_ctr, sizeof(int) * g->max_levels));
+    RC(ensure(g, g->ctl, 256));
+    return TPG_OK;
+}
+
+int enumerate_levels(tpg_cfg *g) {
+    cudaStream_t s = g->stream;
+    if (g->node_cap == 0) {
+        g->node_cap = std::max<long long>(4LL * g->N, 1LL << 22);
+        g->lvl_cap = std::max<long long>(g->N, 1LL << 20);
+        g->pp_cap = 1LL << 20;
+    }
+    for (int attempt = 1;; ++attempt) {
+        g->lvl_cap = std::min<long long>(std::max<long long>(g->lvl_cap, g->N), (long long)MAX31 - 1);
+        g->node_cap = std::max(g->node_cap, g->lvl_cap);
+        g->status_cap = g->node_cap / ENUM_BLOCK + 2LL * g->max_levels + 64;
+        RC(alloc_workspace(g));
+        CK(cudaMemsetAsync(g->levels.p, 0, sizeof(LevelRec) * g->max_levels, s));
+        CK(cudaMemsetAsync(g->status.p, 0, sizeof(unsigned long long) * g->status_cap, s));
+        CK(cudaMemsetAsync(g->tile_ctr.p, 0, sizeof(int) * g->max_levels, s));
+        CK(cudaMemsetAsync(g->ctl.p, 0, 256, s));
+        EnumArgs a{};
+        a.g = g->gd;
+        a.nodes = g->nodes.as<int2>();
+        a.node_cap = g->node_cap;
+        a.tfl[0] = g->tfl[0].as<int2>();
+        a.tfl[1] = g->tfl[1].as<int2>();
+        a.tvis[0] = g->tvis[0].as<unsigned>();
+        a.tvis[1] = g->tvis[1].as<unsigned>();
+        a.lvl_cap = g->lvl_cap;
+        a.pp_refs = g->pp_refs.as<int>();
+        a.pp_cap = g->pp_cap;
+        a.levels = g->levels.as<LevelRec>();
+        a.max_levels = g->max_levels;
+        a.status = g->status.as<unsigned long long>();
+        a.status_cap = g->status_cap;
+        a.tile_ctr = g->tile_ctr.as<int>();
+        a.err = g->ctl.as<int>();
+        a.bar = (unsigned *)(g->ctl.as<char>() + 64);
+        int grid = 0;
+        CK(cudaEventRecord(g->ev[0], s));
+        CK(launch_enumerate(a, g->num_sms, s, &grid));
+        CK(cudaEventRecord(g->ev[1], s));
+        g->stats.enumerate_grid = grid;
+        g->h_levels.resize(g->max_levels);
+        CK(cudaMemcpyAsync(g->h_levels.data(), g->levels.p, sizeof(LevelRec) * g->max_levels,
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(g->h_small, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        cudaEventElapsedTime(&g->stats.t_enumerate_ms, g->ev[0], g->ev[1]);
+        const int err = g->h_small[0];
+        g->stats.attempts = attempt;
+        if (err & ERR_TIMEOUT) return TPG_ETIMEOUT;
+        if (err & (ERR_OVF_COUNT | ERR_OVF_LEVELS)) return TPG_ETOOBIG;
+        if (!(err & ERR_OVERFLOW_MASK)) return TPG_OK;
+        // grow from what the failed attempt saw, then retry from scratch
+        long long seen_nodes = 0, seen_peak = 0, seen_pp = 0;
+        for (int k = 1; k < g->max_levels; ++k) {
+            const LevelRec &L = g->h_levels[k];
+            if (L.count <= 0) break;
+            seen_nodes += L.count;
+            seen_peak = std::max(seen_peak, L.count);
+            seen_pp += L.pp_count;
+        }
+        if (err & ERR_OVF_NODES) g->node_cap = std::max(g->node_cap * 4, seen_nodes * 2);
+        if (err & ERR_OVF_LEVEL) g->lvl_cap = std::max(g->lvl_cap * 2, seen_peak + seen_peak / 4);
+        if (err & ERR_OVF_PP) g->pp_cap = std::max(g->pp_cap * 4, seen_pp * 2);
+        if (err & ERR_OVF_STATUS) g->node_cap = std::max(g->node_cap, seen_nodes * 2);
+        if (attempt >= 24) return TPG_ENOMEM;
+    }
+}
+
+int run_prime_paths(tpg_cfg *g) {
+    cudaStream_t s = g->stream;
+    drop_cache(g);
+    RC(enumerate_levels(g));
+    // level summary
+    std::vector<int> pp_levels;
+    long long P = 0, V = 0, nodes = 0, peak = 0;
+    int K = 0;
+    for (int k = 1; k < g->max_levels; ++k) {
+        const LevelRec &L = g->h_levels[k];
+        if (L.count <= 0) break;
+        K = k;
+        nodes += L.count;
+        peak = std::max(peak, L.count);
+        if (L.pp_count > 0) {
+            pp_levels.push_back(k);
+            P += L.pp_count;
+            V += (long long)k * L.pp_count;
+        }
+    }
+    g->stats.simple_paths = nodes;
+    g->stats.levels = K;
+    g->stats.pp_levels = (int)pp_levels.size();
+    g->stats.peak_level_nodes = peak;
+    g->stats.prime_paths = P;
+    g->stats.pp_vertices = V;
+    g->stats.bitset_words = g->W;
+    g->stats.arena_bytes_used = nodes * (long long)sizeof(int2);
+    g->stats.arena_bytes_alloc = g->node_cap * (long long)sizeof(int2);
+    g->stats.frontier_bytes_alloc = 2 * g->lvl_cap * (long long)(sizeof(int2) + 4 * g->W);
+
+    Block *off = block_new(g->fns, sizeof(long long) * (P + 1), s);
+    Block *vert = block_new(g->fns, sizeof(int) * std::max<long long>(V, 1), s);
+    Block *gptr = block_new(g->fns, sizeof(long long) * (g->G + 1), s);
+    Block *pgraph = g->G > 1 ? block_new(g->fns, sizeof(int) * std::max<long long>(P, 1), s) : nullptr;
+    if (!off || !vert || !gptr || (g->G > 1 && !pgraph)) {
+        block_unref(off);
+        block_unref(vert);
+        block_unref(gptr);
+        block_unref(pgraph);
+        return TPG_ENOMEM;
+    }
+    g->pp_off = off;
+    g->pp_vert = vert;
+    g->pp_gptr = gptr;
+    g->pp_graph = pgraph;
+    const LevelRec *dlev = g->levels.as<LevelRec>();
+    const int2 *dnodes = g->nodes.as<int2>();
+    CK(cudaEventRecord(g->ev[2], s));
+    if (P == 0) {
+        CK(cudaMemsetAsync(off->p, 0, sizeof(long long), s));
+    } else if (pp_levels.size() == 1) {
+        const int k = pp_levels[0];
+        const int *refs = g->pp_refs.as<int>() + g->h_levels[k].pp_base;
+        CK(pp_offsets_single_level((long long *)off->p, P, k, s));
+        CK(pp_materialize(nullptr, refs, k, P, (const long long *)off->p, dnodes, dlev, g->gd, (int *)vert->p,
+                          pgraph ? (int *)pgraph->p : nullptr, s));
+    } else {
+        for (int b = 0; b < 2; ++b) {
+            RC(ensure(g, g->s_keys[b], sizeof(int) * P));
+            RC(ensure(g, g->s_refs[b], sizeof(long long) * P));
+        }
+        RC(ensure(g, g->s_len, sizeof(long long) * (P + 1)));
+        RC(ensure(g, g->s_tmp, sizeof(long long) * scan_tmp_elems(P + 1)));
+        int cur = 0;
+        long long na = 0;
+        int cur_level = 0;
+        for (int idx = (int)pp_levels.size() - 1; idx >= 0; --idx) {
+            const int k = pp_levels[idx];
+            const LevelRec &L = g->h_levels[k];
+            const int *lref = g->pp_refs.as<int>() + L.pp_base;
+            if (na == 0) {
+                CK(order_init_run(lref, k, L.pp_count, g->s_keys[cur].as<int>(), g->s_refs[cur].as<long long>(), s));
+                na = L.pp_count;
+            } else {
+                CK(order_ascend(g->s_keys[cur].as<int>(), na, dnodes, dlev, cur_level, k, s));
+                CK(order_merge(g->s_keys[cur].as<int>(), g->s_refs[cur].as<long long>(), na, lref, k, L.pp_count,
+                               g->s_keys[cur ^ 1].as<int>(), g->s_refs[cur ^ 1].as<long long>(), s));
+                cur ^= 1;
+                na += L.pp_count;
+            }
+            cur_level = k;
+        }
+        const long long *refs = g->s_refs[cur].as<long long>();
+        CK(pp_lengths(refs, P, g->s_len.as<long long>(), s));
+        CK(scan_i64(g->s_len.as<long long>(), (long long *)off->p, P, g->s_tmp.as<long long>(), s));
+        CK(pp_materialize(refs, nullptr, 0, P, (const long long *)off->p, dnodes, dlev, g->gd, (int *)vert->p,
+                          pgraph ? (int *)pgraph->p : nullptr, s));
+    }
+    if (g->G > 1) {
+        CK(graph_ptr_from_ids(pgraph ? (const int *)pgraph->p : nullptr, P, g->G, (long long *)gptr->p, s));
+    } else {
+        long long *h = (long long *)g->h_small;
+        h[0] = 0;
+        h[1] = P;
+        CK(cudaMemcpyAsync(gptr->p, h, 2 * sizeof(long long), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaEventRecord(g->ev[3], s));
+    CK(cudaStreamSynchronize(s));
+    cudaEventElapsedTime(&g->stats.t_order_ms, g->ev[2], g->ev[3]);
+    g->P = P;
+    g->V = V;
+    g->pp_valid = true;
+    return TPG_OK;
+}
+
+// Package device blocks as a result in the handle's result location.
+int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, long long V, tpg_paths **out) {
+    PathsImpl *r = new PathsImpl();
+    std::memset(&r->pub, 0, sizeof(r->pub));
+    r->pub.magic = MAGIC_PATHS;
+    r->pub.num_graphs = g->G;
+    r->pub.num_paths = P;
+    r->location = g->location;
+    r->pub.location = g->location;
+    if (g->location == TPG_RESULT_DEVICE) {
+        Block *b[3] = {gptr, off, vert};
+        for (int i = 0; i < 3; ++i) {
+            block_ref(b[i]);
+            r->dev[i] = b[i];
+        }
+        r->pub.graph_path_ptr = (const int64_t *)gptr->p;
+        r->pub.offsets = (const int64_t *)off->p;
+        r->pub.vertices = (const int32_t *)vert->p;
+    } else {
+        const size_t sz[3] = {sizeof(long long) * (g->G + 1), sizeof(long long) * (P + 1),
+                              sizeof(int) * (size_t)std::max<long long>(V, 1)};
+        Block *b[3] = {gptr, off, vert};
+        for (int i = 0; i < 3; ++i) {
+            r->host[i] = pinned().get(sz[i]);
+            if (!r->host[i]) {
+                for (int j = 0; j < i; ++j) pinned().put(r->host[j]);
+                delete r;
+                return TPG_ENOMEM;
+            }
+            if (cudaMemcpyAsync(r->host[i], b[i]->p, sz[i], cudaMemcpyDeviceToHost, g->stream) != cudaSuccess) {
+                cudaGetLastError();
+                for (int j = 0; j <= i; ++j) pinned().put(r->host[j]);
+                delete r;
+                return TPG_ECUDA;
+            }
+        }
+        if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < 3; ++j) pinned().put(r->host[j]);
+            delete r;
+            return TPG_ECUDA;
+        }
+        r->pub.graph_path_ptr = (const int64_t *)r->host[0];
+        r->pub.offsets = (const int64_t *)r->host[1];
+        r->pub.vertices = (const int32_t *)r->host[2];
+    }
+    *out = &r->pub;
+    return TPG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// test paths
+// ---------------------------------------------------------------------------
+int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, long long *oT, long long *oTV) {
+    cudaStream_t s = g->stream;
+    if (!g->pp_valid) RC(run_prime_paths(g));
+    const long long P = g->P;
+    const int *pp_graph = g->pp_graph ? (const int *)g->pp_graph->p : nullptr;
+    const long long *pp_off = (const long long *)g->pp_off->p;
+    const int *pp_vert = (const int *)g->pp_vert->p;
+    if (P == 0) {
+        Block *off = block_new(g->fns, sizeof(long long), s);
+        Block *vert = block_new(g->fns, 16, s);
+        Block *gptr = block_new(g->fns, sizeof(long long) * (g->G + 1), s);
+        if (!off || !vert || !gptr) {
+            block_unref(off);
+            block_unref(vert);
+            block_unref(gptr);
+            return TPG_ENOMEM;
+        }
+        CK(cudaMemsetAsync(off->p, 0, sizeof(long long), s));
+        CK(cudaMemsetAsync(gptr->p, 0, sizeof(long long) * (g->G + 1), s));
+        *o_off = off;
+        *o_vert = vert;
+        *o_gptr = gptr;
+        *oT = 0;
+        *oTV = 0;
+        return TPG_OK;
+    }
+    // lengths, run starts, graph ids
+    RC(ensure(g, g->s_i64[0], sizeof(long long) * (P + 1)));   // tp_len
+    RC(ensure(g, g->s_i64[1], sizeof(long long) * (P + 1)));   // run_rank
+    RC(ensure(g, g->s_i32[0], sizeof(int) * (P + 1)));         // run_start
+    RC(ensure(g, g->s_i32[1], sizeof(int) * (P + 1)));         // tp_graph
+    RC(ensure(g, g->s_tmp, sizeof(long long) * scan_tmp_elems(P + 1)));
+    RC(ensure(g, g->ctl, 256));
+    CK(cudaEventRecord(g->ev[4], s));
+    CK(cudaMemsetAsync(g->ctl.p, 0, sizeof(int), s));
+    long long *tp_len = g->s_i64[0].as<long long>();
+    long long *run_rank = g->s_i64[1].as<long long>();
+    int *run_start = g->s_i32[0].as<int>();
+    int *tp_graph = g->s_i32[1].as<int>();
+    CK(tp_lengths(pp_off, pp_vert, pp_graph, P, g->gd, tp_len, run_start, tp_graph, g->ctl.as<int>(), s));
+    Block *tp_off = block_new(g->fns, sizeof(long long) * (P + 1), s);
+    if (!tp_off) return TPG_ENOMEM;
+    int rc = TPG_OK;
+    Block *tp_vert = nullptr, *f_off = nullptr, *f_vert = nullptr, *f_gptr = nullptr;
+    long long TV = 0, R = 0, T = 0, FTV = 0;
+    long long *h = (long long *)g->h_small;
+    do {
+        if (cuda_err(scan_i64(tp_len, (long long *)tp_off->p, P, g->s_tmp.as<long long>(), s))) { rc = TPG_ECUDA; break; }
+        if (cuda_err(scan_i32_to_i64(run_start, run_rank, P, g->s_tmp.as<long long>(), s))) { rc = TPG_ECUDA; break; }
+        cudaMemcpyAsync(h, (long long *)tp_off->p + P, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h + 1, run_rank + P, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h + 2, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = TPG_ECUDA; break; }
+        TV = h[0];
+        R = h[1];
+        if (((int *)(h + 2))[0] & ERR_UNREACH) { rc = TPG_EUNREACH; break; }
+        tp_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
+        if (!tp_vert) { rc = TPG_ENOMEM; break; }
+        if (cuda_err(tp_write(pp_off, pp_vert, pp_graph, P, g->gd, (const long long *)tp_off->p, (int *)tp_vert->p, s))) {
+            rc = TPG_ECUDA;
+            break;
+        }
+        // graphs that own at least one PP: one sorted run each means no merge
+        long long graphs_with_pp = 1;
+        if (g->G > 1) {
+            std::vector<long long> gp(g->G + 1);
+            cudaMemcpyAsync(gp.data(), g->pp_gptr->p, sizeof(long long) * (g->G + 1), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) { rc = TPG_ECUDA; break; }
+            graphs_with_pp = 0;
+            for (int i = 0; i < g->G; ++i) graphs_with_pp += gp[i + 1] > gp[i];
+        }
+        if (R == graphs_with_pp) {
+            // every graph's TPs form one run: sorted, and distinct PPs with a
+            // common first vertex give distinct TPs, so nothing to dedup
+            f_off = tp_off;
+            f_vert = tp_vert;
+            tp_off = tp_vert = nullptr;
+            f_gptr = block_new(g->fns, sizeof(long long) * (g->G + 1), s);
+            if (!f_gptr) { rc = TPG_ENOMEM; break; }
+            if (cudaMemcpyAsync(f_gptr->p, g->pp_gptr->p, sizeof(long long) * (g->G + 1), cudaMemcpyDeviceToDevice, s)) {
+                rc = TPG_ECUDA;
+                break;
+            }
+            T = P;
+            FTV = TV;
+            break;
+        }
+        // pairwise merge rounds over the runs
+        if ((rc = ensure(g, g->s_i64[2], sizeof(long long) * (R + 2))) ||
+            (rc = ensure(g, g->s_i64[3], sizeof(long long) * (R + 2))) ||
+            (rc = ensure(g, g->s_refs[0], sizeof(long long) * (P + 1))) ||
+            (rc = ensure(g, g->s_refs[1], sizeof(long long) * (P + 1))))
+            break;
+        long long *bounds[2] = {g->s_i64[2].as<long long>(), g->s_i64[3].as<long long>()};
+        long long *perm[2] = {g->s_refs[0].as<long long>(), g->s_refs[1].as<long long>()};
+        if (cuda_err(tp_run_bounds(run_start, run_rank, P, R, bounds[0], s))) { rc = TPG_ECUDA; break; }
+        if (cuda_err(tp_iota(perm[0], P, s))) { rc = TPG_ECUDA; break; }
+        int cb = 0, cp = 0;
+        long long Rc = R;
+        while (Rc > 1 && rc == TPG_OK) {
+            if (cuda_err(tp_merge_round(perm[cp], perm[cp ^ 1], bounds[cb], Rc, P, (const long long *)tp_off->p,
+                                        (const int *)tp_vert->p, tp_graph, s)) ||
+                cuda_err(tp_halve_bounds(bounds[cb], Rc, bounds[cb ^ 1], s)))
+                rc = TPG_ECUDA;
+            cp ^= 1;
+            cb ^= 1;
+            Rc = (Rc + 1) / 2;
+        }
+        if (rc) break;
+        // dedup + compaction
+        int *keep = g->s_i32[0].as<int>();                 // reuse run_start
+        long long *keep_len = g->s_i64[0].as<long long>(); // reuse tp_len
+        long long *keep_off = g->s_i64[1].as<long long>(); // reuse run_rank
+        long long *keep_rank = perm[cp ^ 1];
+        if (cuda_err(tp_dedup_flags(perm[cp], P, (const long long *)tp_off->p, (const int *)tp_vert->p, tp_graph,
+                                    keep_len, keep, s)) ||
+            cuda_err(scan_i64(keep_len, keep_off, P, g->s_tmp.as<long long>(), s)) ||
+            cuda_err(scan_i32_to_i64(keep, keep_rank, P, g->s_tmp.as<long long>(), s))) {
+            rc = TPG_ECUDA;
+            break;
+        }
+        cudaMemcpyAsync(h, keep_rank + P, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h + 1, keep_off + P, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = TPG_ECUDA; break; }
+        T = h[0];
+        FTV = h[1];
+        f_off = block_new(g->fns, sizeof(long long) * (T + 1), s);
+        f_vert = block_new(g->fns, sizeof(int) * std::max<long long>(FTV, 1), s);
+        f_gptr = block_new(g->fns, sizeof(long long) * (g->G + 1), s);
+        if (!f_off || !f_vert || !f_gptr) { rc = TPG_ENOMEM; break; }
+        if ((rc = ensure(g, g->s_i32[2], sizeof(int) * (T + 1)))) break;
+        int *f_graph = g->s_i32[2].as<int>();
+        if (cuda_err(tp_gather(perm[cp], keep, keep_rank, P, (const long long *)tp_off->p, (const int *)tp_vert->p,
+                               tp_graph, keep_off, (long long *)f_off->p, (int *)f_vert->p, f_graph, s))) {
+            rc = TPG_ECUDA;
+            break;
+        }
+        h[2] = FTV;
+        if (cudaMemcpyAsync((long long *)f_off->p + T, h + 2, sizeof(long long), cudaMemcpyHostToDevice, s) ||
+            cuda_err(graph_ptr_from_ids(f_graph, T, g->G, (long long *)f_gptr->p, s))) {
+            rc = TPG_ECUDA;
+            break;
+        }
+    } while (false);
+    cudaEventRecord(g->ev[5], s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == TPG_OK) rc = TPG_ECUDA;
+    if (rc == TPG_OK) cudaEventElapsedTime(&g->stats.t_test_paths_ms, g->ev[4], g->ev[5]);
+    block_unref(tp_off);
+    block_unref(tp_vert);
+    if (rc != TPG_OK) {
+        block_unref(f_off);
+        block_unref(f_vert);
+        block_unref(f_gptr);
+        return rc;
+    }
+    *o_off = f_off;
+    *o_vert = f_vert;
+    *o_gptr = f_gptr;
+    *oT = T;
+    *oTV = FTV;
+    g->stats.test_paths = T;
+    g->stats.tp_vertices = FTV;
+    return TPG_OK;
+}
+
+bool is_cfg(const void *p) { return p && ((const tpg_cfg *)p)->magic == MAGIC_CFG; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// exported functions
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *tpg_version(void) { return "tpg 0.1 (sm_103a)"; }
+
+int64_t tpg_kernel_launches(void) { return g_kernel_launches.load(); }
+
+const char *tpg_strerror(int code) {
+    switch (code) {
+        case TPG_OK: return "ok";
+        case TPG_EINVAL: return "invalid argument or malformed graph";
+        case TPG_EUNREACH: return "a prime-path vertex is unreachable from entry or cannot reach exit";
+        case TPG_ETOOBIG: return "graph or output too large";
+        case TPG_ENOMEM: return "out of memory";
+        case TPG_ECUDA: return "CUDA runtime error";
+        case TPG_ETIMEOUT: return "bounded device wait timed out";
+        case TPG_EHANDLE: return "invalid handle";
+        default: return "unknown error";
+    }
+}
+
+int tpg_set_allocator(tpg_alloc_fn alloc, tpg_release_fn release, void *ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) return TPG_EINVAL;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.ctx = ctx;
+    return TPG_OK;
+}
+
+int tpg_load_cfg(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t entry, int32_t exit,
+                 tpg_cfg **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    RC(validate_host(n, row_ptr, col, entry, exit));
+    tpg_cfg *g = nullptr;
+    RC(new_cfg(nullptr, &g));
+    const long long m = row_ptr[n];
+    g->N = n;
+    g->G = 1;
+    g->maxn = n;
+    g->M = m;
+    g->h_vbase = {0, n};
+    int rc = TPG_OK;
+    do {
+        if ((rc = ensure(g, g->rp, sizeof(int) * (n + 1)))) break;
+        if ((rc = ensure(g, g->col, sizeof(int) * std::max<long long>(m, 1)))) break;
+        if ((rc = ensure(g, g->vbase, sizeof(int) * 2))) break;
+        if ((rc = ensure(g, g->entry, sizeof(int)))) break;
+        if ((rc = ensure(g, g->exitv, sizeof(int)))) break;
+        cudaStream_t s = g->stream;
+        int ee[2] = {entry, exit};
+        if (cudaMemcpyAsync(g->rp.p, row_ptr, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s) ||
+            (m > 0 && cudaMemcpyAsync(g->col.p, col, sizeof(int) * m, cudaMemcpyHostToDevice, s)) ||
+            cudaMemcpyAsync(g->vbase.p, g->h_vbase.data(), sizeof(int) * 2, cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(g->entry.p, &ee[0], sizeof(int), cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(g->exitv.p, &ee[1], sizeof(int), cudaMemcpyHostToDevice, s) ||
+            cudaStreamSynchronize(s)) {
+            rc = cuda_err(cudaGetLastError());
+            if (!rc) rc = TPG_ECUDA;
+            break;
+        }
+        rc = preprocess(g, {0, (long long)n * n});
+    } while (false);
+    if (rc) {
+        destroy_cfg(g);
+        return rc;
+    }
+    *out = g;
+    return TPG_OK;
+}
+
+int tpg_load_cfg_device(int32_t n, int32_t m, const int32_t *row_ptr_dev, const int32_t *col_dev, int32_t entry,
+                        int32_t exit, void *stream, tpg_cfg **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (n < 1 || m < 0 || !row_ptr_dev || (m > 0 && !col_dev)) return TPG_EINVAL;
+    if (n > TPG_MAX_N) return TPG_ETOOBIG;
+    tpg_cfg *g = nullptr;
+    RC(new_cfg(stream, &g));
+    g->N = n;
+    g->G = 1;
+    g->maxn = n;
+    g->M = m;
+    g->h_vbase = {0, n};
+    int rc = TPG_OK;
+    do {
+        if ((rc = ensure(g, g->rp, sizeof(int) * (n + 1)))) break;
+        if ((rc = ensure(g, g->col, sizeof(int) * std::max<int>(m, 1)))) break;
+        if ((rc = ensure(g, g->vbase, sizeof(int) * 2))) break;
+        if ((rc = ensure(g, g->entry, sizeof(int)))) break;
+        if ((rc = ensure(g, g->exitv, sizeof(int)))) break;
+        if ((rc = ensure(g, g->ctl, 256))) break;
+        cudaStream_t s = g->stream;
+        int *hs = g->h_small;
+        hs[0] = entry;
+        hs[1] = exit;
+        hs[2] = 0;
+        hs[3] = n;
+        if (cudaMemcpyAsync(g->rp.p, row_ptr_dev, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s) ||
+            (m > 0 && cudaMemcpyAsync(g->col.p, col_dev, sizeof(int) * m, cudaMemcpyDeviceToDevice, s)) ||
+            cudaMemcpyAsync(g->entry.p, hs, sizeof(int), cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(g->exitv.p, hs + 1, sizeof(int), cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(g->vbase.p, hs + 2, 2 * sizeof(int), cudaMemcpyHostToDevice, s) ||
+            cudaMemsetAsync(g->ctl.p, 0, sizeof(int), s) ||
+            validate_csr_device(g->rp.as<int>(), g->col.as<int>(), n, m, entry, exit, g->ctl.as<int>(), s) ||
+            cudaMemcpyAsync(hs + 8, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s)) {
+            rc = TPG_ECUDA;
+            cudaGetLastError();
+            break;
+        }
+        if (hs[8] & ERR_INVAL) {
+            rc = TPG_EINVAL;
+            break;
+        }
+        rc = preprocess(g, {0, (long long)n * n});
+    } while (false);
+    if (rc) {
+        destroy_cfg(g);
+        return rc;
+    }
+    *out = g;
+    return TPG_OK;
+}
+
+int tpg_load_cfg_batch(int32_t num_graphs, const int32_t *n_per_graph, const int32_t *row_ptr_cat,
+                       const int32_t *col_cat, const int32_t *entries, const int32_t *exits, tpg_cfg **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (num_graphs < 1 || !n_per_graph || !row_ptr_cat || !entries || !exits) return TPG_EINVAL;
+    const int G = num_graphs;
+    std::vector<long long> rp_base(G + 1), arc_base(G + 1), tbl_base(G + 1);
+    std::vector<int> vbase(G + 1), gent(G), gext(G);
+    long long N = 0, M = 0, R = 0, T = 0;
+    int maxn = 0;
+    for (int g = 0; g < G; ++g) {
+        const int n = n_per_graph[g];
+        if (n < 1) return TPG_EINVAL;
+        if (n > TPG_MAX_N) return TPG_ETOOBIG;
+        rp_base[g] = R;
+        arc_base[g] = M;
+        vbase[g] = (int)N;
+        tbl_base[g] = T;
+        const int32_t *rp = row_ptr_cat + R;
+        const int32_t *cl = col_cat ? col_cat + M : nullptr;
+        RC(validate_host(n, rp, cl, entries[g], exits[g]));
+        gent[g] = entries[g] + (int)N;
+        gext[g] = exits[g] + (int)N;
+        M += rp[n];
+        R += n + 1;
+        N += n;
+        T += (long long)n * n;
+        maxn = std::max(maxn, n);
+    }
+    rp_base[G] = R;
+    arc_base[G] = M;
+    vbase[G] = (int)N;
+    tbl_base[G] = T;
+    if (N >= (1LL << 31) - 1 || M >= (1LL << 31) - 1) return TPG_ETOOBIG;
+    tpg_cfg *g = nullptr;
+    RC(new_cfg(nullptr, &g));
+    g->N = (int)N;
+    g->G = G;
+    g->maxn = maxn;
+    g->M = M;
+    g->h_vbase = vbase;
+    int rc = TPG_OK;
+    DevBuf t_rp, t_col, t_rpb, t_ab;
+    do {
+        cudaStream_t s = g->stream;
+        if ((rc = ensure(g, g->rp, sizeof(int) * (N + 1)))) break;
+        if ((rc = ensure(g, g->col, sizeof(int) * std::max<long long>(M, 1)))) break;
+        if ((rc = ensure(g, g->vgraph, sizeof(int) * N))) break;
+        if ((rc = ensure(g, g->vbase, sizeof(int) * (G + 1)))) break;
+        if ((rc = ensure(g, g->entry, sizeof(int) * G))) break;
+        if ((rc = ensure(g, g->exitv, sizeof(int) * G))) break;
+        if ((rc = ensure(g, t_rp, sizeof(int) * R))) break;
+        if ((rc = ensure(g, t_col, sizeof(int) * std::max<long long>(M, 1)))) break;
+        if ((rc = ensure(g, t_rpb, sizeof(long long) * (G + 1)))) break;
+        if ((rc = ensure(g, t_ab, sizeof(long long) * (G + 1)))) break;
+        if (cudaMemcpyAsync(t_rp.p, row_ptr_cat, sizeof(int) * R, cudaMemcpyHostToDevice, s) ||
+            (M > 0 && cudaMemcpyAsync(t_col.p, col_cat, sizeof(int) * M, cudaMemcpyHostToDevice, s)) ||
+            cudaMemcpyAsync(t_rpb.p, rp_base.data(), sizeof(long long) * (G + 1), cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(t_ab.p, arc_base.data(), sizeof(long long) * (G + 1), cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(g->vbase.p, vbase.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(g->entry.p, gent.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(g->exitv.p, gext.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s) ||
+            build_union_csr(nullptr, t_rpb.as<long long>(), t_ab.as<long long>(), t_rp.as<int>(), t_col.as<int>(), G,
+                            (int)N, M, g->rp.as<int>(), g->col.as<int>(), g->vgraph.as<int>(), g->vbase.as<int>(), s) ||
+            cudaStreamSynchronize(s)) {
+            rc = TPG_ECUDA;
+            cudaGetLastError();
+            break;
+        }
+        rc = preprocess(g, tbl_base);
+    } while (false);
+    release(g, t_rp);
+    release(g, t_col);
+    release(g, t_rpb);
+    release(g, t_ab);
+    if (rc) {
+        destroy_cfg(g);
+        return rc;
+    }
+    *out = g;
+    return TPG_OK;
+}
+
+int tpg_prime_paths(tpg_cfg *g, tpg_paths **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    RC(run_prime_paths(g));
+    return make_result(g, g->pp_off, g->pp_vert, g->pp_gptr, g->P, g->V, out);
+}
+
+int tpg_test_paths(tpg_cfg *g, tpg_paths **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    Block *off = nullptr, *vert = nullptr, *gptr = nullptr;
+    long long T = 0, TV = 0;
+    RC(run_test_paths(g, &off, &vert, &gptr, &T, &TV));
+    const int rc = make_result(g, off, vert, gptr, T, TV, out);
+    block_unref(off);
+    block_unref(vert);
+    block_unref(gptr);
+    return rc;
+}
+
+void tpg_free(void *handle) {
+    if (!handle) return;
+    const uint32_t magic = *(const uint32_t *)handle;
+    if (magic == MAGIC_CFG) {
+        destroy_cfg((tpg_cfg *)handle);
+    } else if (magic == MAGIC_PATHS) {
+        PathsImpl *r = (PathsImpl *)handle;
+        for (int i = 0; i < 3; ++i) {
+            if (r->host[i]) pinned().put(r->host[i]);
+            block_unref(r->dev[i]);
+        }
+        r->pub.magic = MAGIC_DEAD;
+        delete r;
+    }
+}
+
+int tpg_set_stream(tpg_cfg *g, void *stream) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return TPG_ECUDA;
+    }
+    g->stream = (cudaStream_t)stream;
+    return TPG_OK;
+}
+
+int tpg_set_result_location(tpg_cfg *g, int32_t location) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (location != TPG_RESULT_HOST && location != TPG_RESULT_DEVICE) return TPG_EINVAL;
+    g->location = location;
+    return TPG_OK;
+}
+
+int tpg_get_stats(const tpg_cfg *g, tpg_stats *out) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (!out) return TPG_EINVAL;
+    *out = g->stats;
+    return TPG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+// Shared device helpers and internal structures of libtpg.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tpg.h"
+
+namespace tpg {
+
+// ---------------------------------------------------------------------------
+// error flags raised by kernels (bitwise OR into one int in device memory)
+// ---------------------------------------------------------------------------
+enum : int {
+    ERR_OVF_NODES = 1,    // persistent path arena full
+    ERR_OVF_LEVEL = 2,    // ping-pong frontier full
+    ERR_OVF_PP = 4,       // PP reference list full
+    ERR_OVF_STATUS = 8,   // look-back status array full
+    ERR_TIMEOUT = 16,     // a bounded wait ran out
+    ERR_UNREACH = 32,     // TP: vertex not reachable / cannot reach exit
+    ERR_INVAL = 64,       // device-side validation failed
+    ERR_OVF_LEVELS = 128, // more levels than the level table holds
+    ERR_OVF_COUNT = 256,  // a level count passed 2^31 - 1
+};
+constexpr int ERR_OVERFLOW_MASK = ERR_OVF_NODES | ERR_OVF_LEVEL | ERR_OVF_PP | ERR_OVF_STATUS;
+
+// wall-clock limit of every device-side spin (nanoseconds)
+constexpr unsigned long long SPIN_LIMIT_NS = 4ull * 1000 * 1000 * 1000;
+
+// One frontier level of the path arena.  Written by the last tile of the
+// previous level (node_base, count, status_base) and by the last tile of
+// this level (pp_count).  64 bytes.
+struct LevelRec {
+    long long node_base;    // index of the level's first node in the arena
+    long long count;        // nodes in the level (may exceed capacity on overflow)
+    long long pp_base;      // index of the level's first PP reference
+    long long pp_count;     // PPs found in the level
+    long long status_base;  // first look-back status word of the level
+    long long children;     // nodes of the next level (copy, for statistics)
+    long long pad[2];
+};
+
+// Device view of one handle's graph(s): the union of all graphs with global
+// vertex ids (graph g owns ids vbase[g] .. vbase[g+1]-1).
+struct GraphDev {
+    int N;            // total vertices
+    int G;            // graphs
+    int maxn;         // largest graph
+    int W;            // 32-bit words of the per-path visited bitset
+    long long M;      // total arcs
+    const int *rp, *col;     // successor CSR (global ids)
+    const int *prp, *pcol;   // predecessor CSR (global ids)
+    const int *vgraph;       // [N] graph of each vertex
+    const int *vbase;        // [G+1]
+    const int *entry, *exit; // [G] global ids
+    const long long *tbl_base;  // [G+1] offsets of the per-graph n_g x n_g BFS tables
+    int *dist, *pred;           // BFS tables, local ids: [tbl_base[g] + a*n_g + x]
+    int *pre_len, *suf_len;     // [N] vertex counts of path(entry->v), path(v->exit), 0 = none
+    long long *pre_off, *suf_off;  // [N+1]
+    int *pre_seq, *suf_seq;     // local ids
+};
+
+// ---------------------------------------------------------------------------
+// memory-model helpers (PTX ISA: ld/st .relaxed.gpu, %globaltimer)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// bar[0] = arrival count, bar[1] = generation.  Every wait is bounded by
+// SPIN_LIMIT_NS; on expiry ERR_TIMEOUT is raised and false returned.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire_u32(bar + 1);
+        __threadfence();
+        unsigned prev = atomicAdd(bar, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(bar + 1) == gen) {
+                __nanosleep(100);
+                if (global_ns() - t0 > SPIN_LIMIT_NS) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// look-back status words: flag(2) | a(31) | b(31), values saturate at 2^31-1
+// ---------------------------------------------------------------------------
+constexpr unsigned long long ST_AGG = 1ull, ST_PRE = 2ull;
+constexpr unsigned long long MAX31 = (1ull << 31) - 1;
+
+__device__ __forceinline__ unsigned long long st_pack(unsigned long long flag, unsigned long long a,
+                                                      unsigned long long b) {
+    a = a > MAX31 ? MAX31 : a;
+    b = b > MAX31 ? MAX31 : b;
+    return (flag << 62) | (a << 31) | b;
+}
+__device__ __forceinline__ unsigned long long st_flag(unsigned long long s) { return s >> 62; }
+__device__ __forceinline__ unsigned long long st_a(unsigned long long s) { return (s >> 31) & MAX31; }
+__device__ __forceinline__ unsigned long long st_b(unsigned long long s) { return s & MAX31; }
+
+// Decoupled look-back (single-pass prefix) of a tile's pair aggregate
+// (agg_a, agg_b); run by the FIRST WARP of the block.  Returns the exclusive
+// prefix of the tile in (pa, pb) on every lane of warp 0.  status[] must be
+// zero before the first tile of the scan publishes.  Tiles are claimed in
+// increasing order by running blocks, so every predecessor is resident or
+// finished and each wait ends; the wait is still bounded.
+__device__ __forceinline__ void lookback_pair(unsigned long long *status, long long tile,
+                                              unsigned long long agg_a, unsigned long long agg_b,
+                                              unsigned long long &pa, unsigned long long &pb,
+                                              int *err) {
+    const int lane = threadIdx.x & 31;
+    pa = 0;
+    pb = 0;
+    if (tile == 0) {
+        if (lane == 0) st_relaxed_u64(status, st_pack(ST_PRE, agg_a, agg_b));
+        return;
+    }
+    if (lane == 0) st_relaxed_u64(status + tile, st_pack(ST_AGG, agg_a, agg_b));
+    long long j = tile - 1;
+    unsigned long long t0 = global_ns();
+    bool timed_out = false;
+    while (true) {
+        long long idx = j - lane;
+        unsigned long long s = (idx >= 0) ? ld_relaxed_u64(status + idx) : st_pack(ST_PRE, 0, 0);
+        while (true) {
+            bool pending = st_flag(s) == 0;
+            if (!__any_sync(0xffffffffu, pending)) break;
+            if (pending) {
+                __nanosleep(32);
+                s = ld_relaxed_u64(status + idx);
+            }
+            bool late = global_ns() - t0 > SPIN_LIMIT_NS;
+            if (__shfl_sync(0xffffffffu, late, 0)) {
+                timed_out = true;
+                break;
+            }
+        }
+        if (timed_out) {
+            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+            break;
+        }
+        unsigned pre_mask = __ballot_sync(0xffffffffu, st_flag(s) == ST_PRE);
+        int stop = pre_mask ? (__ffs(pre_mask) - 1) : 31;
+        unsigned long long va = (lane <= stop) ? st_a(s) : 0ull;
+        unsigned long long vb = (lane <= stop) ? st_b(s) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            va += __shfl_xor_sync(0xffffffffu, va, o);
+            vb += __shfl_xor_sync(0xffffffffu, vb, o);
+        }
+        pa += va;
+        pb += vb;
+        if (pre_mask) break;
+        j -= 32;
+    }
+    if (lane == 0) st_relaxed_u64(status + tile, st_pack(ST_PRE, pa + agg_a, pb + agg_b));
+}
+
+// Block-wide exclusive scan of two 32-bit counters packed as (a << 32 | b);
+// the per-block sums must stay below 2^32.  Returns the exclusive prefix and
+// writes the block total to `total`.  BLOCK threads, BLOCK % 32 == 0.
+template <int BLOCK>
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long v,
+                                                                   unsigned long long &total) {
+    constexpr int NW = BLOCK / 32;
+    __shared__ unsigned long long s_warp[NW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = (lane < NW) ? s_warp[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) s_warp[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long warp_prefix = wid ? s_warp[wid - 1] : 0ull;
+    total = s_warp[NW - 1];
+    unsigned long long r = warp_prefix + x - v;
+    __syncthreads();
+    return r;
+}
+
+// Block-wide exclusive scan of int64 values.
+template <int BLOCK>
+__device__ __forceinline__ long long block_excl_scan_i64(long long v, long long &total) {
+    constexpr int NW = BLOCK / 32;
+    __shared__ long long s_w[NW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = (lane < NW) ? s_w[lane] : 0ll;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) s_w[lane] = w;
+    }
+    __syncthreads();
+    long long wp = wid ? s_w[wid - 1] : 0ll;
+    total = s_w[NW - 1];
+    long long r = wp + x - v;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace tpg

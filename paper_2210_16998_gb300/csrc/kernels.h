@@ -1,0 +1,94 @@
+// Internal kernel entry points of libtpg (host-callable launchers).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "common.cuh"
+
+namespace tpg {
+
+// kernels launched by this library in this process (tpg_kernel_launches)
+extern std::atomic<long long> g_kernel_launches;
+inline void note_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+constexpr int ENUM_BLOCK = 256;
+
+struct EnumArgs {
+    GraphDev g;
+    int2 *nodes;             // persistent arena {last, parent}
+    long long node_cap;
+    int2 *tfl[2];            // ping-pong {first, last}
+    unsigned *tvis[2];       // ping-pong bitsets, W word-arrays of lvl_cap each
+    long long lvl_cap;
+    int *pp_refs;            // PP node indices (relative to their level), level-major
+    long long pp_cap;
+    LevelRec *levels;        // [max_levels]
+    int max_levels;
+    unsigned long long *status;  // look-back status words (zeroed)
+    long long status_cap;
+    int *tile_ctr;           // [max_levels] (zeroed)
+    int *err;                // error flags (zeroed)
+    unsigned *bar;           // grid barrier {count, generation} (zeroed)
+};
+
+// enumerate.cu
+int bitset_words_supported(int maxn);
+cudaError_t launch_enumerate(const EnumArgs &args, int num_sms, cudaStream_t s, int *grid_out);
+
+// scan.cu: exclusive scan of int64 (in may equal out); tmp must hold
+// scan_tmp_elems(n) int64 values.  out[n] receives the total.
+size_t scan_tmp_elems(long long n);
+cudaError_t scan_i64(const long long *in, long long *out, long long n, long long *tmp, cudaStream_t s);
+// exclusive scan of int32 inputs into int64 outputs (out[n] = total)
+cudaError_t scan_i32_to_i64(const int *in, long long *out, long long n, long long *tmp, cudaStream_t s);
+
+// order.cu
+// canonical ordering of PP references across levels (ancestor-index merge)
+cudaError_t order_init_run(const int *pp_refs_level, int level, long long n, int *keys,
+                           long long *refs, cudaStream_t s);
+cudaError_t order_ascend(int *keys, long long n, const int2 *nodes, const LevelRec *levels,
+                         int from_level, int to_level, cudaStream_t s);
+cudaError_t order_merge(const int *ka, const long long *ra, long long na, const int *kb, int level_b,
+                        long long nb, int *kc, long long *rc, cudaStream_t s);
+cudaError_t pp_lengths(const long long *refs, long long n, long long *len_out, cudaStream_t s);
+cudaError_t pp_offsets_single_level(long long *off, long long n, int level, cudaStream_t s);
+cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,
+                           const long long *offsets, const int2 *nodes, const LevelRec *levels,
+                           const GraphDev &g, int *out_vertices, int *out_graph, cudaStream_t s);
+cudaError_t graph_ptr_from_ids(const int *ids, long long n, int G, long long *ptr, cudaStream_t s);
+
+// preprocess.cu
+cudaError_t build_union_csr(const int *unused, const long long *rp_base_dev,
+                            const long long *arc_base_dev, const int *rp_cat, const int *col_cat,
+                            int G, int N, long long M, int *rp, int *col, int *vgraph, int *vbase_out,
+                            cudaStream_t s);
+cudaError_t validate_csr_device(const int *rp, const int *col, int n, long long m, int entry, int exit,
+                                int *err, cudaStream_t s);
+cudaError_t build_pred_csr(const GraphDev &g, int *prp, int *pcol, int *indeg_tmp, long long *scan_tmp,
+                           long long *scan_buf, cudaStream_t s);
+cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s);
+cudaError_t tour_lengths(const GraphDev &g, long long *scan_tmp, cudaStream_t s);
+cudaError_t tour_fill(const GraphDev &g, cudaStream_t s);
+
+// testpaths.cu
+cudaError_t tp_lengths(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
+                       const GraphDev &g, long long *tp_len, int *run_start, int *tp_graph, int *err,
+                       cudaStream_t s);
+cudaError_t tp_write(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
+                     const GraphDev &g, const long long *tp_off, int *tp_vert, cudaStream_t s);
+cudaError_t tp_run_bounds(const int *run_start, const long long *run_rank, long long P, long long R,
+                          long long *bounds, cudaStream_t s);
+cudaError_t tp_merge_round(const long long *perm_in, long long *perm_out, const long long *bounds,
+                           long long R, long long P, const long long *tp_off, const int *tp_vert,
+                           const int *tp_graph, cudaStream_t s);
+cudaError_t tp_halve_bounds(const long long *bounds, long long R, long long *out, cudaStream_t s);
+cudaError_t tp_iota(long long *perm, long long P, cudaStream_t s);
+cudaError_t tp_dedup_flags(const long long *perm, long long P, const long long *tp_off, const int *tp_vert,
+                           const int *tp_graph, long long *keep_len, int *keep, cudaStream_t s);
+cudaError_t tp_gather(const long long *perm, const int *keep, const long long *keep_rank, long long P,
+                      const long long *tp_off, const int *tp_vert, const int *tp_graph,
+                      const long long *keep_off, long long *final_off, int *out_vert, int *out_graph,
+                      cudaStream_t s);
+
+}  // namespace tpg

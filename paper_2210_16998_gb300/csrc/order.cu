@@ -1,0 +1,207 @@
+// Canonical order of the prime paths (kernel (e) for PPs) and their
+// materialisation as vertex sequences.
+//
+// Every level of the path arena is in lexicographic order, and the prime
+// paths form an antichain of the prefix tree (a PP is never a proper prefix
+// of a simple path, Def. 1).  So for two PPs x (k vertices) and y (>= k
+// vertices), x < y exactly when x's index in level k is below the index of
+// y's level-k ancestor.  The canonical list is built from the deepest level
+// upward: the run accumulated so far is keyed by each element's ancestor
+// index at the current level (one parent-link step per level), and merged
+// with that level's own PPs by key.  Keys of the two inputs never tie.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tpg {
+
+__global__ void order_init_run_kernel(const int *pp, int level, long long n, int *keys, long long *refs) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = pp[i];
+        keys[i] = r;
+        refs[i] = ((long long)level << 32) | (unsigned)r;
+    }
+}
+
+cudaError_t order_init_run(const int *pp_refs_level, int level, long long n, int *keys, long long *refs,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8);
+    order_init_run_kernel<<<grid, 256, 0, s>>>(pp_refs_level, level, n, keys, refs);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void order_ascend_kernel(int *keys, long long n, const int2 *nodes, const LevelRec *levels,
+                                    int from_level, int to_level) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int key = keys[i];
+        for (int j = from_level; j > to_level; --j) key = nodes[levels[j].node_base + key].y;
+        keys[i] = key;
+    }
+}
+
+cudaError_t order_ascend(int *keys, long long n, const int2 *nodes, const LevelRec *levels, int from_level,
+                         int to_level, cudaStream_t s) {
+    if (n <= 0 || from_level <= to_level) return cudaSuccess;
+    const long long blocks = (n + 255) / 256;
+    order_ascend_kernel<<<(unsigned)(blocks < 1 << 20 ? blocks : 1 << 20), 256, 0, s>>>(
+        keys, n, nodes, levels, from_level, to_level);
+    note_launch();
+    return cudaGetLastError();
+}
+
+constexpr int MERGE_ITEMS = 8;
+
+// Merge path: thread t produces outputs [t*ITEMS, t*ITEMS + ITEMS).  On equal
+// keys A goes first (cannot happen between A and B here, but keeps the merge
+// stable in general).
+__global__ void order_merge_kernel(const int *ka, const long long *ra, long long na, const int *kb,
+                                   int level_b, long long nb, int *kc, long long *rc) {
+    const long long total = na + nb;
+    const long long diag = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * MERGE_ITEMS;
+    if (diag >= total) return;
+    long long lo = diag > nb ? diag - nb : 0;
+    long long hi = diag < na ? diag : na;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (ka[mid] <= kb[diag - mid - 1]) lo = mid + 1;
+        else hi = mid;
+    }
+    long long i = lo, j = diag - lo;
+    for (int t = 0; t < MERGE_ITEMS && diag + t < total; ++t) {
+        const bool take_a = (i < na) && (j >= nb || ka[i] <= kb[j]);
+        if (take_a) {
+            kc[diag + t] = ka[i];
+            rc[diag + t] = ra[i];
+            ++i;
+        } else {
+            const int r = kb[j];
+            kc[diag + t] = r;
+            rc[diag + t] = ((long long)level_b << 32) | (unsigned)r;
+            ++j;
+        }
+    }
+}
+
+cudaError_t order_merge(const int *ka, const long long *ra, long long na, const int *kb, int level_b, long long nb,
+                        int *kc, long long *rc, cudaStream_t s) {
+    const long long total = na + nb;
+    if (total <= 0) return cudaSuccess;
+    const long long threads = (total + MERGE_ITEMS - 1) / MERGE_ITEMS;
+    order_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ka, ra, na, kb, level_b, nb, kc, rc);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void pp_lengths_kernel(const long long *refs, long long n, long long *len) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        len[i] = refs[i] >> 32;
+}
+
+cudaError_t pp_lengths(const long long *refs, long long n, long long *len_out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = (n + 255) / 256;
+    pp_lengths_kernel<<<(unsigned)(blocks < 1 << 20 ? blocks : 1 << 20), 256, 0, s>>>(refs, n, len_out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void pp_offsets_single_kernel(long long *off, long long n, int level) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= n;
+         i += (long long)gridDim.x * blockDim.x)
+        off[i] = i * level;
+}
+
+cudaError_t pp_offsets_single_level(long long *off, long long n, int level, cudaStream_t s) {
+    const long long blocks = (n + 1 + 255) / 256;
+    pp_offsets_single_kernel<<<(unsigned)(blocks < 1 << 20 ? blocks : 1 << 20), 256, 0, s>>>(off, n, level);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// One warp materialises 32 consecutive PPs: each lane walks its path's parent
+// links from the last vertex back to the first, writing into a per-warp
+// shared-memory window; the warp then stores the window contiguously.  If
+// the window does not fit, lanes store directly.
+constexpr int MAT_WARPS = 8;
+constexpr int MAT_BUF = 2048;  // int32 per warp (8 KB)
+
+__global__ void __launch_bounds__(MAT_WARPS * 32)
+    pp_materialize_kernel(const long long *refs, const int *single_refs, int single_level, long long n,
+                          const long long *offsets, const int2 *nodes, const LevelRec *levels, GraphDev g,
+                          int *out, int *out_graph) {
+    __shared__ int buf[MAT_WARPS][MAT_BUF];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long nwarps = (long long)gridDim.x * MAT_WARPS;
+    for (long long w0 = (blockIdx.x * (long long)MAT_WARPS + wid) * 32; w0 < n; w0 += nwarps * 32) {
+        const long long idx = w0 + lane;
+        const bool valid = idx < n;
+        int level = 0, rel = 0;
+        if (valid) {
+            if (refs) {
+                const long long r = refs[idx];
+                level = (int)(r >> 32);
+                rel = (int)(r & 0xffffffffll);
+            } else {
+                level = single_level;
+                rel = single_refs[idx];
+            }
+        }
+        const long long w_end_idx = (w0 + 32 < n) ? w0 + 32 : n;
+        const long long start = offsets[w0];
+        const long long span = offsets[w_end_idx] - start;
+        const long long off = valid ? offsets[idx] : 0;
+        const bool staged = span <= MAT_BUF;
+        int node = rel, root = 0;
+        for (int j = level; j >= 1; --j) {
+            const int2 rec = nodes[levels[j].node_base + node];
+            const int v = rec.x;
+            const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
+            if (staged) buf[wid][off - start + (j - 1)] = loc;
+            else out[off + (j - 1)] = loc;
+            root = v;
+            node = rec.y;
+        }
+        if (valid && out_graph) out_graph[idx] = g.vgraph ? g.vgraph[root] : 0;
+        if (staged) {
+            __syncwarp();
+            for (long long t = lane; t < span; t += 32) out[start + t] = buf[wid][t];
+            __syncwarp();
+        }
+    }
+}
+
+cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,
+                           const long long *offsets, const int2 *nodes, const LevelRec *levels, const GraphDev &g,
+                           int *out_vertices, int *out_graph, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long warps = (n + 31) / 32;
+    long long blocks = (warps + MAT_WARPS - 1) / MAT_WARPS;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    pp_materialize_kernel<<<(unsigned)blocks, MAT_WARPS * 32, 0, s>>>(refs, single_refs, single_level, n, offsets,
+                                                                     nodes, levels, g, out_vertices, out_graph);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// graph_path_ptr[g] = first path index whose graph id is >= g (ids sorted).
+__global__ void graph_ptr_kernel(const int *ids, long long n, int G, long long *ptr) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cur = (i < n) ? ids[i] : G;
+        const int prev = (i > 0) ? ids[i - 1] : -1;
+        for (int gg = prev + 1; gg <= cur; ++gg) ptr[gg] = i;
+    }
+}
+
+cudaError_t graph_ptr_from_ids(const int *ids, long long n, int G, long long *ptr, cudaStream_t s) {
+    const long long blocks = (n + 1 + 255) / 256;
+    graph_ptr_kernel<<<(unsigned)(blocks < 1 << 20 ? blocks : 1 << 20), 256, 0, s>>>(ids, n, G, ptr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tpg

@@ -1,0 +1,230 @@
+// Load-time preprocessing (row a1): union CSR of a batch, device-side CSR
+// validation, predecessor CSR, all-pairs BFS tables with the lowest-id
+// predecessor tie-break, and the per-vertex tour tables path(entry -> v) and
+// path(v -> exit) used to assemble test paths.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tpg {
+
+// One block per graph: global ids for the batch (graph g owns vertices
+// vbase[g] .. vbase[g+1]-1 and arcs arc_base[g] .. arc_base[g+1]-1).
+__global__ void union_csr_kernel(const long long *rp_base, const long long *arc_base, const int *vbase,
+                                 const int *rp_cat, const int *col_cat, int G, int N, long long M, int *rp,
+                                 int *col, int *vgraph) {
+    const int g = blockIdx.x;
+    const int vb = vbase[g], ng = vbase[g + 1] - vb;
+    const long long rb = rp_base[g], ab = arc_base[g], mg = arc_base[g + 1] - ab;
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+        rp[vb + i] = (int)(ab + rp_cat[rb + i]);
+        vgraph[vb + i] = g;
+    }
+    for (long long e = threadIdx.x; e < mg; e += blockDim.x) col[ab + e] = col_cat[ab + e] + vb;
+    if (g == G - 1 && threadIdx.x == 0) rp[N] = (int)M;
+}
+
+cudaError_t build_union_csr(const int *, const long long *rp_base_dev, const long long *arc_base_dev,
+                            const int *rp_cat, const int *col_cat, int G, int N, long long M, int *rp, int *col,
+                            int *vgraph, int *vbase_dev, cudaStream_t s) {
+    union_csr_kernel<<<G, 256, 0, s>>>(rp_base_dev, arc_base_dev, vbase_dev, rp_cat, col_cat, G, N, M, rp, col,
+                                       vgraph);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Device-side validation of one CSR (same rules as the host check).
+__global__ void validate_kernel(const int *rp, const int *col, int n, long long m, int entry, int exit,
+                                int *err) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    int bad = 0;
+    if (tid == 0) {
+        if (rp[0] != 0 || (long long)rp[n] != m) bad = 1;
+        if (entry < 0 || entry >= n || exit < 0 || exit >= n || entry == exit) bad = 1;
+        else if (rp[exit + 1] != rp[exit]) bad = 1;
+    }
+    for (int u = tid; u < n && !bad; u += stride) {
+        const int a = rp[u], b = rp[u + 1];
+        if (b < a || a < 0 || (long long)b > m) { bad = 1; break; }
+        for (int e = a; e < b; ++e) {
+            const int w = col[e];
+            if (w < 0 || w >= n || (e > a && w <= col[e - 1]) || w == entry) { bad = 1; break; }
+        }
+    }
+    if (bad) atomicOr(err, ERR_INVAL);
+}
+
+cudaError_t validate_csr_device(const int *rp, const int *col, int n, long long m, int entry, int exit, int *err,
+                                cudaStream_t s) {
+    int blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    validate_kernel<<<blocks, 256, 0, s>>>(rp, col, n, m, entry, exit, err);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void indeg_kernel(const int *col, long long M, int *indeg) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < M; e += (long long)gridDim.x * blockDim.x)
+        atomicAdd(indeg + col[e], 1);
+}
+
+__global__ void to_i32_kernel(const long long *in, int *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (int)in[i];
+}
+
+__global__ void pred_scatter_kernel(const int *rp, const int *col, int N, int *cursor, int *pcol) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < N; u += gridDim.x * blockDim.x)
+        for (int e = rp[u]; e < rp[u + 1]; ++e) pcol[atomicAdd(cursor + col[e], 1)] = u;
+}
+
+// ascending order inside every predecessor list (lists are short)
+__global__ void pred_sort_kernel(const int *prp, int *pcol, int N) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+        const int a = prp[v], b = prp[v + 1];
+        for (int i = a + 1; i < b; ++i) {
+            const int x = pcol[i];
+            int j = i - 1;
+            while (j >= a && pcol[j] > x) {
+                pcol[j + 1] = pcol[j];
+                --j;
+            }
+            pcol[j + 1] = x;
+        }
+    }
+}
+
+static unsigned grid_for(long long n, int block = 256) {
+    long long b = (n + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > (1 << 20)) b = 1 << 20;
+    return (unsigned)b;
+}
+
+cudaError_t build_pred_csr(const GraphDev &g, int *prp, int *pcol, int *indeg_tmp, long long *scan_tmp,
+                           long long *scan_buf, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(indeg_tmp, 0, sizeof(int) * (size_t)g.N, s);
+    if (e != cudaSuccess) return e;
+    if (g.M > 0) {
+        indeg_kernel<<<grid_for(g.M), 256, 0, s>>>(g.col, g.M, indeg_tmp);
+        note_launch();
+    }
+    if ((e = scan_i32_to_i64(indeg_tmp, scan_buf, g.N, scan_tmp, s)) != cudaSuccess) return e;
+    to_i32_kernel<<<grid_for(g.N + 1), 256, 0, s>>>(scan_buf, prp, g.N + 1);
+    note_launch();
+    to_i32_kernel<<<grid_for(g.N), 256, 0, s>>>(scan_buf, indeg_tmp, g.N);  // cursor = start
+    pred_scatter_kernel<<<grid_for(g.N), 256, 0, s>>>(g.rp, g.col, g.N, indeg_tmp, pcol);
+    note_launch();
+    pred_sort_kernel<<<grid_for(g.N), 256, 0, s>>>(prp, pcol, g.N);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// One block per source vertex a: pull-style BFS inside a's graph.  A vertex
+// x first reached at distance d+1 takes as predecessor the lowest-id u with
+// an arc u -> x and dist(u) = d.
+constexpr int BFS_BLOCK = 128;
+
+__global__ void __launch_bounds__(BFS_BLOCK) bfs_kernel(GraphDev g) {
+    extern __shared__ int dist_s[];
+    const int a = blockIdx.x;
+    const int gid = g.vgraph ? g.vgraph[a] : 0;
+    const int vb = g.vgraph ? g.vbase[gid] : 0;
+    const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
+    const int al = a - vb;
+    int *drow = g.dist + g.tbl_base[gid] + (long long)al * ng;
+    int *prow = g.pred + g.tbl_base[gid] + (long long)al * ng;
+    for (int x = threadIdx.x; x < ng; x += BFS_BLOCK) {
+        dist_s[x] = (x == al) ? 0 : -1;
+        prow[x] = -1;
+    }
+    __syncthreads();
+    for (int d = 0;; ++d) {
+        int changed = 0;
+        for (int x = threadIdx.x; x < ng; x += BFS_BLOCK) {
+            if (dist_s[x] != -1) continue;
+            int best = 0x7fffffff;
+            for (int e = g.prp[vb + x]; e < g.prp[vb + x + 1]; ++e) {
+                const int u = g.pcol[e] - vb;
+                if (dist_s[u] == d && u < best) best = u;
+            }
+            if (best != 0x7fffffff) {
+                dist_s[x] = d + 1;  // other threads only test == d this round
+                prow[x] = best;
+                changed = 1;
+            }
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+    for (int x = threadIdx.x; x < ng; x += BFS_BLOCK) drow[x] = dist_s[x];
+}
+
+cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s) {
+    const size_t smem = sizeof(int) * (size_t)g.maxn;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    bfs_kernel<<<g.N, BFS_BLOCK, smem, s>>>(g);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// pre_len[v] = vertices of path(entry -> v) (0 if none); suf_len[v] = vertices
+// of path(v -> exit).
+__global__ void tour_len_kernel(GraphDev g) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x) {
+        const int gid = g.vgraph ? g.vgraph[v] : 0;
+        const int vb = g.vgraph ? g.vbase[gid] : 0;
+        const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
+        const int en = g.entry[gid] - vb, ex = g.exit[gid] - vb, vl = v - vb;
+        const int *D = g.dist + g.tbl_base[gid];
+        const int d1 = D[(long long)en * ng + vl];
+        const int d2 = D[(long long)vl * ng + ex];
+        g.pre_len[v] = d1 >= 0 ? d1 + 1 : 0;
+        g.suf_len[v] = d2 >= 0 ? d2 + 1 : 0;
+    }
+}
+
+__global__ void tour_fill_kernel(GraphDev g) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x) {
+        const int gid = g.vgraph ? g.vgraph[v] : 0;
+        const int vb = g.vgraph ? g.vbase[gid] : 0;
+        const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
+        const int en = g.entry[gid] - vb, ex = g.exit[gid] - vb, vl = v - vb;
+        const int *P = g.pred + g.tbl_base[gid];
+        // path(entry -> v), backwards from v through P[entry][.]
+        int len = g.pre_len[v];
+        int *dst = g.pre_seq + g.pre_off[v];
+        int x = vl;
+        for (int i = len - 1; i >= 0; --i) {
+            dst[i] = x;
+            if (i > 0) x = P[(long long)en * ng + x];
+        }
+        // path(v -> exit), backwards from exit through P[v][.]
+        len = g.suf_len[v];
+        dst = g.suf_seq + g.suf_off[v];
+        x = ex;
+        for (int i = len - 1; i >= 0; --i) {
+            dst[i] = x;
+            if (i > 0) x = P[(long long)vl * ng + x];
+        }
+    }
+}
+
+cudaError_t tour_lengths(const GraphDev &g, long long *scan_tmp, cudaStream_t s) {
+    tour_len_kernel<<<grid_for(g.N), 256, 0, s>>>(g);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = scan_i32_to_i64(g.pre_len, g.pre_off, g.N, scan_tmp, s)) != cudaSuccess) return e;
+    return scan_i32_to_i64(g.suf_len, g.suf_off, g.N, scan_tmp, s);
+}
+
+cudaError_t tour_fill(const GraphDev &g, cudaStream_t s) {
+    tour_fill_kernel<<<grid_for(g.N), 256, 0, s>>>(g);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tpg

@@ -1,0 +1,385 @@
+"""Python binding of libtpg (ctypes; argument marshalling only).
+
+Every function of ``include/tpg.h`` has a Python function of the same name.
+All path computation happens in the CUDA kernels of ``libtpg.so``; this
+module only converts arrays to pointers and results to numpy arrays (host
+results) or zero-copy torch tensors (device results).  PyTorch supplies the
+device memory (its caching allocator is installed as the library allocator)
+and the CUDA stream (the current torch stream at load time).
+
+There is no CPU fallback: if the library is not built, or no GPU is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+TPG_OK = 0
+TPG_EINVAL = -1
+TPG_EUNREACH = -2
+TPG_ETOOBIG = -3
+TPG_ENOMEM = -4
+TPG_ECUDA = -5
+TPG_ETIMEOUT = -6
+TPG_EHANDLE = -7
+TPG_RESULT_HOST = 0
+TPG_RESULT_DEVICE = 1
+TPG_MAX_N = 4096
+
+HEADER = os.path.join(_build.INCLUDE, "tpg.h")
+
+
+class TPGError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib_strerror(code)
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+class _Paths(ctypes.Structure):
+    _fields_ = [
+        ("magic", ctypes.c_uint32),
+        ("num_graphs", ctypes.c_int32),
+        ("num_paths", ctypes.c_int64),
+        ("location", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("graph_path_ptr", ctypes.c_void_p),
+        ("offsets", ctypes.c_void_p),
+        ("vertices", ctypes.c_void_p),
+    ]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [
+        ("simple_paths", ctypes.c_int64),
+        ("prime_paths", ctypes.c_int64),
+        ("pp_vertices", ctypes.c_int64),
+        ("levels", ctypes.c_int32),
+        ("pp_levels", ctypes.c_int32),
+        ("peak_level_nodes", ctypes.c_int64),
+        ("arena_bytes_used", ctypes.c_int64),
+        ("arena_bytes_alloc", ctypes.c_int64),
+        ("frontier_bytes_alloc", ctypes.c_int64),
+        ("attempts", ctypes.c_int32),
+        ("bitset_words", ctypes.c_int32),
+        ("test_paths", ctypes.c_int64),
+        ("tp_vertices", ctypes.c_int64),
+        ("t_enumerate_ms", ctypes.c_float),
+        ("t_order_ms", ctypes.c_float),
+        ("t_test_paths_ms", ctypes.c_float),
+        ("enumerate_grid", ctypes.c_int32),
+    ]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+_callbacks = None
+
+
+def declared_functions():
+    """Names of the functions declared in include/tpg.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tpg_[a-z_0-9]+)\s*\(", text)) - {"tpg_alloc_fn", "tpg_release_fn"})
+
+
+def library_path(build: bool = False) -> str:
+    if build:
+        return _build.build()
+    return _build.LIB
+
+
+def load_library(path: str | None = None, build: bool = False, install_torch_allocator: bool = True):
+    """Load libtpg.so (building it first if asked) and declare the signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or library_path(build)
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtpg.so is not built ({path}); call __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        P = ctypes.c_void_p
+        lib.tpg_load_cfg.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(P)]
+        lib.tpg_load_cfg_device.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32,
+                                            P, ctypes.POINTER(P)]
+        lib.tpg_load_cfg_batch.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.POINTER(P)]
+        lib.tpg_prime_paths.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
+        lib.tpg_test_paths.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
+        lib.tpg_free.argtypes = [P]
+        lib.tpg_free.restype = None
+        lib.tpg_set_stream.argtypes = [P, P]
+        lib.tpg_set_result_location.argtypes = [P, ctypes.c_int32]
+        lib.tpg_set_allocator.argtypes = [_ALLOC_FN, _RELEASE_FN, P]
+        lib.tpg_get_stats.argtypes = [P, ctypes.POINTER(_Stats)]
+        lib.tpg_strerror.argtypes = [ctypes.c_int]
+        lib.tpg_strerror.restype = ctypes.c_char_p
+        lib.tpg_version.restype = ctypes.c_char_p
+        lib.tpg_kernel_launches.restype = ctypes.c_int64
+        for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
+                     "tpg_test_paths", "tpg_set_stream", "tpg_set_result_location", "tpg_set_allocator",
+                     "tpg_get_stats"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+    if install_torch_allocator:
+        _install_torch_allocator()
+    return _lib
+
+
+def _install_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _callbacks
+    import torch
+
+    if not torch.cuda.is_available():
+        return
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:  # out of memory -> the library returns TPG_ENOMEM
+            return None
+
+    def _release(ptr, stream, ctx):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    cb = (_ALLOC_FN(_alloc), _RELEASE_FN(_release))
+    rc = _lib.tpg_set_allocator(cb[0], cb[1], None)
+    if rc != TPG_OK:
+        raise TPGError(rc, "tpg_set_allocator")
+    _callbacks = cb
+
+
+def _lib_strerror(code: int) -> str:
+    if _lib is None:
+        return f"error {code}"
+    return _lib.tpg_strerror(code).decode()
+
+
+def tpg_strerror(code: int) -> str:
+    return load_library().tpg_strerror(int(code)).decode()
+
+
+def tpg_version() -> str:
+    return load_library().tpg_version().decode()
+
+
+def _check(rc: int, where: str):
+    if rc != TPG_OK:
+        raise TPGError(rc, where)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+class Cfg:
+    """A loaded graph (or batch of graphs): owns a tpg_cfg*."""
+
+    def __init__(self, handle: int, num_graphs: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.num_graphs = num_graphs
+
+    def close(self):
+        if self.handle:
+            load_library().tpg_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class _CudaArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+class Paths:
+    """A path list returned by the library (owns a tpg_paths*)."""
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+        p = ptr.contents
+        self.num_graphs = int(p.num_graphs)
+        self.num_paths = int(p.num_paths)
+        self.location = int(p.location)
+        self._raw = (p.graph_path_ptr, p.offsets, p.vertices)
+        if self.location == TPG_RESULT_HOST:
+            gp = np.ctypeslib.as_array(ctypes.cast(p.graph_path_ptr, ctypes.POINTER(ctypes.c_int64)),
+                                       shape=(self.num_graphs + 1,))
+            off = np.ctypeslib.as_array(ctypes.cast(p.offsets, ctypes.POINTER(ctypes.c_int64)),
+                                        shape=(self.num_paths + 1,))
+            nv = int(off[-1])
+            vert = (np.ctypeslib.as_array(ctypes.cast(p.vertices, ctypes.POINTER(ctypes.c_int32)), shape=(nv,))
+                    if nv else np.zeros(0, np.int32))
+            self.graph_path_ptr, self.offsets, self.vertices = gp, off, vert
+        else:
+            import torch
+
+            self.graph_path_ptr = torch.as_tensor(_CudaArray(p.graph_path_ptr, (self.num_graphs + 1,), "<i8"),
+                                                  device="cuda")
+            self.offsets = torch.as_tensor(_CudaArray(p.offsets, (self.num_paths + 1,), "<i8"), device="cuda")
+            nv = int(self.offsets[-1].item())
+            self.vertices = (torch.as_tensor(_CudaArray(p.vertices, (nv,), "<i4"), device="cuda")
+                             if nv else torch.zeros(0, dtype=torch.int32, device="cuda"))
+
+    @property
+    def num_vertices(self) -> int:
+        return int(self.offsets[-1])
+
+    def host_arrays(self):
+        """(graph_path_ptr, offsets, vertices) as numpy copies."""
+        if self.location == TPG_RESULT_HOST:
+            return self.graph_path_ptr.copy(), self.offsets.copy(), self.vertices.copy()
+        return (self.graph_path_ptr.cpu().numpy(), self.offsets.cpu().numpy(), self.vertices.cpu().numpy())
+
+    def to_lists(self, graph: int | None = None):
+        gp, off, v = self.host_arrays()
+        lo, hi = (0, self.num_paths) if graph is None else (int(gp[graph]), int(gp[graph + 1]))
+        return [tuple(int(x) for x in v[off[i]:off[i + 1]]) for i in range(lo, hi)]
+
+    def free(self):
+        if self._ptr is not None:
+            # drop views first: device tensors alias library memory
+            self.graph_path_ptr = self.offsets = self.vertices = None
+            load_library().tpg_free(ctypes.cast(self._ptr, ctypes.c_void_p))
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+
+def _current_stream():
+    import torch
+
+    if torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def tpg_load_cfg(n, row_ptr, col, entry, exit, location=TPG_RESULT_HOST) -> Cfg:
+    lib = load_library()
+    rp, rpp = _i32(row_ptr)
+    cl, clp = _i32(col if len(col) else np.zeros(1, np.int32))
+    h = ctypes.c_void_p()
+    _check(lib.tpg_load_cfg(int(n), rpp, clp, int(entry), int(exit), ctypes.byref(h)), "tpg_load_cfg")
+    cfg = Cfg(h.value, 1)
+    tpg_set_stream(cfg, _current_stream())
+    tpg_set_result_location(cfg, location)
+    return cfg
+
+
+def tpg_load_cfg_device(n, m, row_ptr_dev, col_dev, entry, exit, stream=None, location=TPG_RESULT_DEVICE) -> Cfg:
+    """row_ptr_dev / col_dev: int32 CUDA tensors (or raw device addresses)."""
+    lib = load_library()
+
+    def addr(t):
+        return ctypes.c_void_p(t if isinstance(t, int) else t.data_ptr())
+
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    h = ctypes.c_void_p()
+    _check(lib.tpg_load_cfg_device(int(n), int(m), addr(row_ptr_dev), addr(col_dev), int(entry), int(exit), s,
+                                   ctypes.byref(h)), "tpg_load_cfg_device")
+    cfg = Cfg(h.value, 1)
+    tpg_set_result_location(cfg, location)
+    return cfg
+
+
+def tpg_load_cfg_batch(n_per_graph, row_ptr_cat, col_cat, entries, exits, location=TPG_RESULT_HOST) -> Cfg:
+    lib = load_library()
+    ns, nsp = _i32(n_per_graph)
+    rp, rpp = _i32(row_ptr_cat)
+    cl, clp = _i32(col_cat if len(col_cat) else np.zeros(1, np.int32))
+    en, enp = _i32(entries)
+    ex, exp = _i32(exits)
+    h = ctypes.c_void_p()
+    _check(lib.tpg_load_cfg_batch(len(ns), nsp, rpp, clp, enp, exp, ctypes.byref(h)), "tpg_load_cfg_batch")
+    cfg = Cfg(h.value, len(ns))
+    tpg_set_stream(cfg, _current_stream())
+    tpg_set_result_location(cfg, location)
+    return cfg
+
+
+def tpg_prime_paths(cfg: Cfg) -> Paths:
+    out = ctypes.POINTER(_Paths)()
+    _check(load_library().tpg_prime_paths(cfg.handle, ctypes.byref(out)), "tpg_prime_paths")
+    return Paths(out)
+
+
+def tpg_test_paths(cfg: Cfg) -> Paths:
+    out = ctypes.POINTER(_Paths)()
+    _check(load_library().tpg_test_paths(cfg.handle, ctypes.byref(out)), "tpg_test_paths")
+    return Paths(out)
+
+
+def tpg_free(obj):
+    if isinstance(obj, (Cfg,)):
+        obj.close()
+    elif isinstance(obj, Paths):
+        obj.free()
+
+
+def tpg_set_stream(cfg: Cfg, stream):
+    s = stream if isinstance(stream, ctypes.c_void_p) else ctypes.c_void_p(stream)
+    _check(load_library().tpg_set_stream(cfg.handle, s), "tpg_set_stream")
+
+
+def tpg_set_result_location(cfg: Cfg, location: int):
+    _check(load_library().tpg_set_result_location(cfg.handle, int(location)), "tpg_set_result_location")
+
+
+def tpg_set_allocator(alloc=None, release=None):
+    """Install Python callables alloc(nbytes, stream) -> ptr / release(ptr, stream), or None for the default."""
+    global _callbacks
+    lib = load_library(install_torch_allocator=False)
+    if alloc is None:
+        _check(lib.tpg_set_allocator(_ALLOC_FN(), _RELEASE_FN(), None), "tpg_set_allocator")
+        _callbacks = None
+        return
+    cb = (_ALLOC_FN(lambda n, s, c: alloc(n, s)), _RELEASE_FN(lambda p, s, c: release(p, s)))
+    _check(lib.tpg_set_allocator(cb[0], cb[1], None), "tpg_set_allocator")
+    _callbacks = cb
+
+
+def tpg_get_stats(cfg: Cfg) -> dict:
+    st = _Stats()
+    _check(load_library().tpg_get_stats(cfg.handle, ctypes.byref(st)), "tpg_get_stats")
+    return {name: (float(getattr(st, name)) if name.startswith("t_") else int(getattr(st, name)))
+            for name, _ in _Stats._fields_}
+
+
+def tpg_kernel_launches() -> int:
+    return int(load_library().tpg_kernel_launches())

@@ -1,0 +1,176 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Every comparison is bit-exact: the outputs are integer vertex sequences in
+canonical order (offsets int64, vertices int32).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_16998_gb300 import cfggen as G
+from paper_2210_16998_gb300 import tpg
+
+from .helpers import assert_paths_equal, ring_with_tail, wrap_digraph
+from .test_oracle import fig1_cfg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    tpg.load_library(build=True)
+
+
+def gpu_run(cfg, location=tpg.TPG_RESULT_HOST, test_paths=True):
+    with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=location) as h:
+        pp = tpg.tpg_prime_paths(h)
+        ppa = pp.host_arrays()
+        pp.free()
+        tpa = None
+        if test_paths:
+            tp = tpg.tpg_test_paths(h)
+            tpa = tp.host_arrays()
+            tp.free()
+        stats = tpg.tpg_get_stats(h)
+    return ppa, tpa, stats
+
+
+def check_cfg(cfg, test_paths=True, location=tpg.TPG_RESULT_HOST):
+    ref = oracle.run_cfg(cfg, test_paths=test_paths)
+    (gp, off, vert), tpa, stats = gpu_run(cfg, location, test_paths)
+    assert list(gp) == [0, len(off) - 1]
+    assert_paths_equal(off, vert, ref.pp_offsets, ref.pp_vertices, f"{cfg.name} PP")
+    assert stats["simple_paths"] == ref.n_simple
+    if test_paths:
+        tgp, toff, tvert = tpa
+        assert list(tgp) == [0, len(toff) - 1]
+        assert_paths_equal(toff, tvert, ref.tp_offsets, ref.tp_vertices, f"{cfg.name} TP")
+    return ref, stats
+
+
+def test_fig1_worked_example():
+    cfg, rows = fig1_cfg()
+    ref, stats = check_cfg(cfg)
+    assert stats["prime_paths"] == 19
+
+
+def test_config1_structured_24():
+    ref, stats = check_cfg(G.config1_cfg())
+    assert stats["prime_paths"] == ref.num_pp
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 10])
+def test_diamond_chain_small(k):
+    ref, stats = check_cfg(G.diamond_chain(k))
+    assert stats["prime_paths"] == 2 ** k
+
+
+def test_diamond_chain_k22_full():
+    """The 2^22-PP chain, compared in full and with its closed forms."""
+    cfg = G.diamond_chain(22)
+    ref, stats = check_cfg(cfg, test_paths=True)
+    assert stats["prime_paths"] == 4_194_304
+    assert stats["simple_paths"] == 67_108_695
+    assert stats["pp_vertices"] == 4_194_304 * 45
+    assert stats["peak_level_nodes"] == 8_388_608
+
+
+def test_config3_cyclic_120():
+    cfg = G.config3_cfg()
+    ref, stats = check_cfg(cfg)
+    assert stats["prime_paths"] == 1_086_398
+
+
+@pytest.mark.parametrize("r", [29, 30, 31, 32, 33, 61, 62, 63, 64, 93, 94, 95, 126, 127, 128, 158, 190, 254, 255])
+def test_bitset_word_boundaries(r):
+    check_cfg(ring_with_tail(r))
+
+
+@pytest.mark.parametrize("r", [300, 1000])
+def test_wide_bitsets(r):
+    check_cfg(ring_with_tail(r))
+
+
+def test_max_vertices_ring():
+    cfg = ring_with_tail(tpg.TPG_MAX_N - 2)
+    assert cfg.n == tpg.TPG_MAX_N
+    check_cfg(cfg, test_paths=False)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_random_digraphs_wrapped(seed):
+    rng = G.SplitMix64(1000 + seed)
+    k = rng.randint(4, 9)
+    inner = G.random_digraph(k, 0.35, 77 + seed, self_loops=(seed % 2 == 0))
+    check_cfg(wrap_digraph(inner))
+
+
+@pytest.mark.parametrize("seed", [G.BATCH_SEED0 + i for i in range(8)])
+def test_batch_graphs_single(seed):
+    check_cfg(G.random_cfg(seed))
+
+
+def test_minimal_graph():
+    rp, col = G.csr_from_arcs(2, [(0, 1)])
+    ref, stats = check_cfg(G.CFG(2, rp, col, 0, 1, "edge"))
+    assert stats["prime_paths"] == 1
+
+
+def test_device_result_location():
+    cfg = G.config3_cfg()
+    ref = oracle.run_cfg(cfg)
+    (gp, off, vert), (tgp, toff, tvert), _ = gpu_run(cfg, location=tpg.TPG_RESULT_DEVICE)
+    assert_paths_equal(off, vert, ref.pp_offsets, ref.pp_vertices, "device PP")
+    assert_paths_equal(toff, tvert, ref.tp_offsets, ref.tp_vertices, "device TP")
+
+
+def test_device_load():
+    import torch
+
+    cfg = G.config1_cfg()
+    ref = oracle.run_cfg(cfg)
+    rp = torch.as_tensor(cfg.row_ptr, device="cuda")
+    col = torch.as_tensor(cfg.col, device="cuda")
+    with tpg.tpg_load_cfg_device(cfg.n, cfg.m, rp, col, cfg.entry, cfg.exit) as h:
+        pp = tpg.tpg_prime_paths(h)
+        gp, off, vert = pp.host_arrays()
+        pp.free()
+    assert_paths_equal(off, vert, ref.pp_offsets, ref.pp_vertices, "device-load PP")
+
+
+def test_device_load_rejects_bad_csr():
+    import torch
+
+    rp = torch.as_tensor(np.array([0, 1, 2], np.int32), device="cuda")
+    col = torch.as_tensor(np.array([1, 0], np.int32), device="cuda")  # arc into the entry
+    with pytest.raises(tpg.TPGError) as e:
+        tpg.tpg_load_cfg_device(2, 2, rp, col, 0, 1)
+    assert e.value.code == tpg.TPG_EINVAL
+
+
+def test_unreachable_reports_error():
+    rp, col = G.csr_from_arcs(4, [(0, 1), (1, 3), (2, 2)])
+    with tpg.tpg_load_cfg(4, rp, col, 0, 3) as h:
+        pp = tpg.tpg_prime_paths(h)
+        assert pp.to_lists() == [(0, 1, 3), (2, 2)]
+        pp.free()
+        with pytest.raises(tpg.TPGError) as e:
+            tpg.tpg_test_paths(h)
+        assert e.value.code == tpg.TPG_EUNREACH
+
+
+def test_repeated_calls_are_identical():
+    cfg = G.config3_cfg()
+    with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit) as h:
+        outs = []
+        for _ in range(3):
+            p = tpg.tpg_prime_paths(h)
+            outs.append(p.host_arrays())
+            p.free()
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            np.testing.assert_array_equal(a, b)
