@@ -182,6 +182,46 @@ int tpg_set_allocator(tpg_alloc_fn alloc, tpg_release_fn release, void *ctx);
 /* Statistics of the handle's last calls. */
 int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);
 
+/*
+ * tpg_prime_paths_noalloc -- prime paths of one small graph, allocating
+ * nothing.  (The paper has no counterpart; this is a convenience of the
+ * library.)
+ *
+ * For callers that cannot allocate memory when they need the result: code
+ * issuing work while its stream is captured into a CUDA graph (cudaMalloc is
+ * not permitted during capture), code working inside a memory budget fixed
+ * in advance, and hosts whose framework owns every allocation.  The call
+ * runs the same kernels as tpg_load_cfg + tpg_prime_paths, keeps every
+ * temporary in one fixed-size device array built into the library (about
+ * 29 MB, held by every GPU that loads the library until the process exits),
+ * and writes into buffers the caller owns.  It calls no cudaMalloc,
+ * cudaFree, cudaHostAlloc or other allocating routine.
+ *
+ * n, m: vertices and arcs; row_ptr_dev[n+1], col_dev[m]: DEVICE int32 CSR
+ * (ascending successor lists, ids 0..n-1).  No entry/exit rule applies: PPs
+ * are defined on any digraph.  offsets_dev[cap_paths+1] (int64) and
+ * vertices_dev[cap_vertices] (int32) are DEVICE buffers of the caller;
+ * on TPG_OK they hold the canonical PP list, exactly as tpg_prime_paths
+ * returns it, and *num_paths / *num_vertices its sizes.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream); the call returns after the
+ * results are complete.
+ *
+ * Limits: n <= 128, m <= 16384, at most 2^20 simple paths in all, 2^18 in
+ * one level and 2^18 PPs; beyond them the call returns TPG_ETOOBIG.  If the
+ * caller's buffers are too small it returns TPG_ETOOBIG with *num_paths and
+ * *num_vertices set to the sizes needed.  TPG_EINVAL for a malformed CSR.
+ *
+ * The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call reuses the same array and clears what must start at zero;
+ * calls whose GPU work overlaps (e.g. on two streams at once) race on it.
+ */
+int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_ptr_dev,
+                            const int32_t *col_dev, int64_t *offsets_dev,
+                            int64_t cap_paths, int32_t *vertices_dev,
+                            int64_t cap_vertices, void *stream,
+                            int64_t *num_paths, int64_t *num_vertices);
+
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t tpg_kernel_launches(void);
 

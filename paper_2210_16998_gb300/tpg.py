@@ -128,6 +128,10 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_strerror.restype = ctypes.c_char_p
         lib.tpg_version.restype = ctypes.c_char_p
         lib.tpg_kernel_launches.restype = ctypes.c_int64
+        lib.tpg_prime_paths_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_int64, P,
+                                                ctypes.c_int64, P, ctypes.POINTER(ctypes.c_int64),
+                                                ctypes.POINTER(ctypes.c_int64)]
+        lib.tpg_prime_paths_noalloc.restype = ctypes.c_int
         for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
                      "tpg_test_paths", "tpg_set_stream", "tpg_set_result_location", "tpg_set_allocator",
                      "tpg_get_stats"):
@@ -379,6 +383,23 @@ def tpg_get_stats(cfg: Cfg) -> dict:
     _check(load_library().tpg_get_stats(cfg.handle, ctypes.byref(st)), "tpg_get_stats")
     return {name: (float(getattr(st, name)) if name.startswith("t_") else int(getattr(st, name)))
             for name, _ in _Stats._fields_}
+
+
+def tpg_prime_paths_noalloc(n, m, row_ptr_dev, col_dev, offsets_dev, vertices_dev, stream=None):
+    """Prime paths of one small graph into caller-owned device buffers, with no
+    allocation inside the library (for callers that cannot allocate at call
+    time, e.g. during stream capture).  row_ptr_dev/col_dev/offsets_dev/
+    vertices_dev are CUDA tensors (int32, int32, int64, int32).  Returns
+    (rc, num_paths, num_vertices); rc is TPG_OK or a TPG_E* code (TPG_ETOOBIG
+    also when the output buffers are too small, with the sizes needed)."""
+    lib = load_library()
+    npaths, nverts = ctypes.c_int64(0), ctypes.c_int64(0)
+    s = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    rc = lib.tpg_prime_paths_noalloc(int(n), int(m), ctypes.c_void_p(row_ptr_dev.data_ptr()),
+                                     ctypes.c_void_p(col_dev.data_ptr()), ctypes.c_void_p(offsets_dev.data_ptr()),
+                                     int(offsets_dev.numel()) - 1, ctypes.c_void_p(vertices_dev.data_ptr()),
+                                     int(vertices_dev.numel()), s, ctypes.byref(npaths), ctypes.byref(nverts))
+    return int(rc), int(npaths.value), int(nverts.value)
 
 
 def tpg_kernel_launches() -> int:
