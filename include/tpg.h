@@ -88,6 +88,8 @@ typedef struct tpg_stats {
     float t_order_ms;           /* device time of ordering + materialisation */
     float t_test_paths_ms;      /* device time of the last tpg_test_paths pipeline */
     int32_t enumerate_grid;     /* blocks of the persistent frontier launch */
+    int32_t tile_block;         /* threads per block of the frontier launch */
+    int32_t tile_items;         /* paths per thread (tile = block * items paths) */
 } tpg_stats;
 
 /*
@@ -178,6 +180,23 @@ int tpg_set_result_location(tpg_cfg *g, int32_t location);
 typedef void *(*tpg_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*tpg_release_fn)(void *ptr, void *stream, void *ctx);
 int tpg_set_allocator(tpg_alloc_fn alloc, tpg_release_fn release, void *ctx);
+
+/*
+ * Tile shape of the frontier kernel for this handle: `block` threads per
+ * block, `items` paths per thread.  Supported: block 128 or 256 with items
+ * 1, 2 or 4, block 512 with items 1 or 2 (bitsets of <= 8 words); block 256
+ * items 1 for wider bitsets.  TPG_EINVAL otherwise.  Results never depend
+ * on the shape; the autotuner uses this.
+ */
+int tpg_set_tile_shape(tpg_cfg *g, int32_t block, int32_t items);
+
+/*
+ * Initial capacities of the handle's path arena: total simple paths,
+ * simple paths of one level, and prime paths.  The arena grows (and the
+ * enumeration restarts from scratch) when one is exceeded, so results never
+ * depend on them; a pre-sizing policy (e.g. the learned sizer) sets them.
+ */
+int tpg_set_capacity(tpg_cfg *g, int64_t nodes, int64_t level_nodes, int64_t prime_paths);
 
 /* Statistics of the handle's last calls. */
 int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);

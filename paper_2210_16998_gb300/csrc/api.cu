@@ -3,6 +3,7 @@
 // sizes buffers, reads level counts back once per call and issues kernels.
 #include <algorithm>
 #include <atomic>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -179,8 +180,10 @@ struct tpg_cfg {
     GraphDev gd{};
 
     // enumeration workspace
-    DevBuf nodes, tfl[2], tvis[2], pp_refs, levels, status, tile_ctr, ctl;
+    std::vector<DevBuf> node_segs, pp_segs;  // the arena: chains of segments
+    DevBuf tfl[2], tvis[2], levels, status, tile_ctr, ctl;
     long long node_cap = 0, lvl_cap = 0, pp_cap = 0, status_cap = 0;
+    EnumShape shape{0, 0};
     // generic scratch
     DevBuf s_keys[2], s_refs[2], s_len, s_tmp, s_i32[3], s_i64[4];
 
@@ -230,11 +233,13 @@ void destroy_cfg(tpg_cfg *g) {
     drop_cache(g);
     DevBuf *all[] = {&g->rp, &g->col, &g->prp, &g->pcol, &g->vgraph, &g->vbase, &g->entry, &g->exitv,
                      &g->tbl_base, &g->dist, &g->pred, &g->pre_len, &g->suf_len, &g->pre_off, &g->suf_off,
-                     &g->pre_seq, &g->suf_seq, &g->nodes, &g->tfl[0], &g->tfl[1], &g->tvis[0], &g->tvis[1],
-                     &g->pp_refs, &g->levels, &g->status, &g->tile_ctr, &g->ctl, &g->s_keys[0], &g->s_keys[1],
+                     &g->pre_seq, &g->suf_seq, &g->tfl[0], &g->tfl[1], &g->tvis[0], &g->tvis[1],
+                     &g->levels, &g->status, &g->tile_ctr, &g->ctl, &g->s_keys[0], &g->s_keys[1],
                      &g->s_refs[0], &g->s_refs[1], &g->s_len, &g->s_tmp, &g->s_i32[0], &g->s_i32[1],
                      &g->s_i32[2], &g->s_i64[0], &g->s_i64[1], &g->s_i64[2], &g->s_i64[3]};
     for (DevBuf *b : all) release(g, *b);
+    for (auto &b : g->node_segs) release(g, b);
+    for (auto &b : g->pp_segs) release(g, b);
     cudaStreamSynchronize(g->stream);
     if (g->h_small) cudaFreeHost(g->h_small);
     for (cudaEvent_t e : g->ev)
@@ -350,85 +355,169 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h) {
 // ---------------------------------------------------------------------------
 // prime paths
 // ---------------------------------------------------------------------------
-int alloc_workspace(tpg_cfg *g) {
-    const int W = g->W;
-    RC(ensure(g, g->nodes, sizeof(int2) * g->node_cap));
-    for (int b = 0; b < 2; ++b) {
-        RC(ensure(g, g->tfl[b], sizeof(int2) * g->lvl_cap));
-        RC(ensure(g, g->tvis[b], sizeof(unsigned) * (size_t)W * g->lvl_cap));
-    }
-    RC(ensure(g, g->pp_refs, sizeof(int) * g->pp_cap));
+// Fixed-size parts of the enumeration workspace (level table, tile
+// counters, control words, look-back status).
+int alloc_fixed_workspace(tpg_cfg *g) {
     RC(ensure(g, g->levels, sizeof(LevelRec) * g->max_levels));
-    RC(ensure(g, g->status, sizeof(unsigned long long) * g->status_cap));
     RC(ensure(g, g->tile_ctr, sizeof(int) * g->max_levels));
     RC(ensure(g, g->ctl, 256));
+    RC(ensure(g, g->status, sizeof(unsigned long long) * g->status_cap));
     return TPG_OK;
+}
+
+// Ping-pong frontier buffers of capacity g->lvl_cap.
+int alloc_frontier(tpg_cfg *g) {
+    for (int b = 0; b < 2; ++b) {
+        RC(ensure(g, g->tfl[b], sizeof(int2) * g->lvl_cap));
+        RC(ensure(g, g->tvis[b], sizeof(unsigned) * (size_t)g->W * g->lvl_cap));
+    }
+    return TPG_OK;
+}
+
+// A new arena segment of `cap` nodes (or PP references) at the end of the chain.
+int push_segment(tpg_cfg *g, std::vector<DevBuf> &segs, size_t elem, long long cap) {
+    DevBuf b;
+    b.p = dev_alloc(g->fns, elem * (size_t)cap, g->stream);
+    if (!b.p) return TPG_ENOMEM;
+    b.bytes = elem * (size_t)cap;
+    segs.push_back(b);
+    return TPG_OK;
+}
+
+// Start a call with one segment per chain, sized to everything the previous
+// call used (or to the initial capacities on a handle's first call).
+int prepare_segments(tpg_cfg *g, std::vector<DevBuf> &segs, size_t elem, long long want) {
+    size_t total = 0;
+    for (auto &b : segs) total += b.bytes;
+    const size_t need = std::max<size_t>(total, elem * (size_t)want);
+    if (segs.size() == 1 && segs[0].bytes >= need) return TPG_OK;
+    for (auto &b : segs) release(g, b);
+    segs.clear();
+    return push_segment(g, segs, elem, (long long)(need / elem));
 }
 
 int enumerate_levels(tpg_cfg *g) {
     cudaStream_t s = g->stream;
     if (g->node_cap == 0) {
-        g->node_cap = std::max<long long>(4LL * g->N, 1LL << 22);
-        g->lvl_cap = std::max<long long>(g->N, 1LL << 20);
-        g->pp_cap = 1LL << 20;
+        g->node_cap = std::max<long long>(4LL * g->N, 1LL << 24);
+        g->lvl_cap = std::max<long long>(g->N, 1LL << 22);
+        g->pp_cap = 1LL << 22;
     }
-    for (int attempt = 1;; ++attempt) {
-        g->lvl_cap = std::min<long long>(std::max<long long>(g->lvl_cap, g->N), (long long)MAX31 - 1);
-        g->node_cap = std::max(g->node_cap, g->lvl_cap);
-        g->status_cap = g->node_cap / ENUM_BLOCK + 2LL * g->max_levels + 64;
-        RC(alloc_workspace(g));
-        CK(cudaMemsetAsync(g->levels.p, 0, sizeof(LevelRec) * g->max_levels, s));
-        CK(cudaMemsetAsync(g->status.p, 0, sizeof(unsigned long long) * g->status_cap, s));
-        CK(cudaMemsetAsync(g->tile_ctr.p, 0, sizeof(int) * g->max_levels, s));
-        CK(cudaMemsetAsync(g->ctl.p, 0, 256, s));
+    g->lvl_cap = std::min<long long>(std::max<long long>(g->lvl_cap, g->N), (long long)MAX31 - 1);
+    g->node_cap = std::max(g->node_cap, (long long)g->N);
+    if (g->status_cap < g->node_cap / ENUM_MIN_TILE + 2LL * g->max_levels + 64)
+        g->status_cap = g->node_cap / ENUM_MIN_TILE + 2LL * g->max_levels + 64;
+    RC(prepare_segments(g, g->node_segs, sizeof(int2), g->node_cap));
+    RC(prepare_segments(g, g->pp_segs, sizeof(int), g->pp_cap));
+    RC(alloc_frontier(g));
+    RC(alloc_fixed_workspace(g));
+    if (!enum_shape_supported(g->W, g->shape)) g->shape = default_enum_shape(g->W);
+    CK(cudaMemsetAsync(g->levels.p, 0, sizeof(LevelRec) * g->max_levels, s));
+    CK(cudaMemsetAsync(g->status.p, 0, sizeof(unsigned long long) * g->status_cap, s));
+    CK(cudaMemsetAsync(g->tile_ctr.p, 0, sizeof(int) * g->max_levels, s));
+    CK(cudaMemsetAsync(g->ctl.p, 0, 256, s));
+    int start_level = 1;
+    int2 *next_override = nullptr;
+    float total_ms = 0.f;
+    for (int launch = 1;; ++launch) {
+        DevBuf &seg = g->node_segs.back();
+        DevBuf &ppseg = g->pp_segs.back();
         EnumArgs a{};
         a.g = g->gd;
-        a.nodes = g->nodes.as<int2>();
-        a.node_cap = g->node_cap;
+        a.seg = seg.as<int2>();
+        a.seg_cap = (long long)(seg.bytes / sizeof(int2));
+        a.next_nodes = next_override;
+        a.pp_seg = ppseg.as<int>();
+        a.pp_seg_cap = (long long)(ppseg.bytes / sizeof(int));
         a.tfl[0] = g->tfl[0].as<int2>();
         a.tfl[1] = g->tfl[1].as<int2>();
         a.tvis[0] = g->tvis[0].as<unsigned>();
         a.tvis[1] = g->tvis[1].as<unsigned>();
         a.lvl_cap = g->lvl_cap;
-        a.pp_refs = g->pp_refs.as<int>();
-        a.pp_cap = g->pp_cap;
         a.levels = g->levels.as<LevelRec>();
         a.max_levels = g->max_levels;
+        a.start_level = start_level;
+        a.seed_level1 = (launch == 1) ? 1 : 0;
         a.status = g->status.as<unsigned long long>();
         a.status_cap = g->status_cap;
         a.tile_ctr = g->tile_ctr.as<int>();
         a.err = g->ctl.as<int>();
+        a.stop_level = g->ctl.as<int>() + 1;
         a.bar = (unsigned *)(g->ctl.as<char>() + 64);
         int grid = 0;
         CK(cudaEventRecord(g->ev[0], s));
-        CK(launch_enumerate(a, g->num_sms, s, &grid));
+        CK(launch_enumerate(a, g->shape, g->num_sms, s, &grid));
         CK(cudaEventRecord(g->ev[1], s));
         g->stats.enumerate_grid = grid;
+        g->stats.tile_block = g->shape.block;
+        g->stats.tile_items = g->shape.items;
         g->h_levels.resize(g->max_levels);
         CK(cudaMemcpyAsync(g->h_levels.data(), g->levels.p, sizeof(LevelRec) * g->max_levels,
                            cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(g->h_small, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(g->h_small, g->ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        cudaEventElapsedTime(&g->stats.t_enumerate_ms, g->ev[0], g->ev[1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]);
+        total_ms += ms;
+        g->stats.t_enumerate_ms = total_ms;
+        g->stats.attempts = launch;
         const int err = g->h_small[0];
-        g->stats.attempts = attempt;
         if (err & ERR_TIMEOUT) return TPG_ETIMEOUT;
         if (err & (ERR_OVF_COUNT | ERR_OVF_LEVELS)) return TPG_ETOOBIG;
         if (!(err & ERR_OVERFLOW_MASK)) return TPG_OK;
-        // grow from what the failed attempt saw, then retry from scratch
-        long long seen_nodes = 0, seen_peak = 0, seen_pp = 0;
-        for (int k = 1; k < g->max_levels; ++k) {
-            const LevelRec &L = g->h_levels[k];
-            if (L.count <= 0) break;
-            seen_nodes += L.count;
-            seen_peak = std::max(seen_peak, L.count);
-            seen_pp += L.pp_count;
+        if (launch >= 64) return TPG_ENOMEM;
+        // resume at level k with room for what it produces
+        const int k = g->h_small[1];
+        if (k < 1 || k + 1 >= g->max_levels) return TPG_ECUDA;
+        const LevelRec L = g->h_levels[k];
+        next_override = nullptr;
+        if (err & ERR_OVF_NODES) {
+            long long total = 0;
+            for (auto &b : g->node_segs) total += (long long)(b.bytes / sizeof(int2));
+            RC(push_segment(g, g->node_segs, sizeof(int2), std::max(L.children, 3 * total)));
+            next_override = g->node_segs.back().as<int2>();
         }
-        if (err & ERR_OVF_NODES) g->node_cap = std::max(g->node_cap * 4, seen_nodes * 2);
-        if (err & ERR_OVF_LEVEL) g->lvl_cap = std::max(g->lvl_cap * 2, seen_peak + seen_peak / 4);
-        if (err & ERR_OVF_PP) g->pp_cap = std::max(g->pp_cap * 4, seen_pp * 2);
-        if (err & ERR_OVF_STATUS) g->node_cap = std::max(g->node_cap, seen_nodes * 2);
-        if (attempt >= 24) return TPG_ENOMEM;
+        if (err & ERR_OVF_PP) {
+            long long total = 0;
+            for (auto &b : g->pp_segs) total += (long long)(b.bytes / sizeof(int));
+            RC(push_segment(g, g->pp_segs, sizeof(int), std::max(L.pp_count, 3 * total)));
+            int *pp_new = g->pp_segs.back().as<int>();
+            CK(cudaMemcpyAsync((char *)g->levels.p + sizeof(LevelRec) * k + offsetof(LevelRec, pp), &pp_new,
+                               sizeof(int *), cudaMemcpyHostToDevice, s));
+        }
+        if (err & ERR_OVF_LEVEL) {
+            const long long cap_new = std::min<long long>(std::max(L.children + L.children / 4, 2 * g->lvl_cap),
+                                                          (long long)MAX31 - 1);
+            DevBuf nfl, nvis;
+            const int b = k & 1;
+            RC(ensure(g, nfl, sizeof(int2) * cap_new));
+            RC(ensure(g, nvis, sizeof(unsigned) * (size_t)g->W * cap_new));
+            CK(relayout_frontier(g->tfl[b].as<int2>(), g->tvis[b].as<unsigned>(), g->lvl_cap, nfl.as<int2>(),
+                                 nvis.as<unsigned>(), cap_new, L.count, g->W, s));
+            release(g, g->tfl[b]);
+            release(g, g->tvis[b]);
+            g->tfl[b] = nfl;
+            g->tvis[b] = nvis;
+            release(g, g->tfl[b ^ 1]);
+            release(g, g->tvis[b ^ 1]);
+            g->lvl_cap = cap_new;
+            RC(ensure(g, g->tfl[b ^ 1], sizeof(int2) * cap_new));
+            RC(ensure(g, g->tvis[b ^ 1], sizeof(unsigned) * (size_t)g->W * cap_new));
+        }
+        if (err & ERR_OVF_STATUS) {
+            g->status_cap *= 2;
+            release(g, g->status);
+            RC(ensure(g, g->status, sizeof(unsigned long long) * g->status_cap));
+        }
+        // level k restarts its look-back from an empty status array
+        long long zero = 0;
+        CK(cudaMemsetAsync(g->status.p, 0, sizeof(unsigned long long) * g->status_cap, s));
+        CK(cudaMemcpyAsync((char *)g->levels.p + sizeof(LevelRec) * k + offsetof(LevelRec, status_base), &zero,
+                           sizeof(long long), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(g->tile_ctr.p, 0, sizeof(int) * g->max_levels, s));
+        CK(cudaMemsetAsync(g->ctl.p, 0, 256, s));
+        CK(cudaStreamSynchronize(s));  // the host-side values above must be consumed first
+        start_level = k;
     }
 }
 
@@ -460,7 +549,9 @@ int run_prime_paths(tpg_cfg *g) {
     g->stats.pp_vertices = V;
     g->stats.bitset_words = g->W;
     g->stats.arena_bytes_used = nodes * (long long)sizeof(int2);
-    g->stats.arena_bytes_alloc = g->node_cap * (long long)sizeof(int2);
+    long long seg_bytes = 0;
+    for (auto &b : g->node_segs) seg_bytes += (long long)b.bytes;
+    g->stats.arena_bytes_alloc = seg_bytes;
     g->stats.frontier_bytes_alloc = 2 * g->lvl_cap * (long long)(sizeof(int2) + 4 * g->W);
 
     Block *off = block_new(g->fns, sizeof(long long) * (P + 1), s);
@@ -479,15 +570,14 @@ int run_prime_paths(tpg_cfg *g) {
     g->pp_gptr = gptr;
     g->pp_graph = pgraph;
     const LevelRec *dlev = g->levels.as<LevelRec>();
-    const int2 *dnodes = g->nodes.as<int2>();
     CK(cudaEventRecord(g->ev[2], s));
     if (P == 0) {
         CK(cudaMemsetAsync(off->p, 0, sizeof(long long), s));
     } else if (pp_levels.size() == 1) {
         const int k = pp_levels[0];
-        const int *refs = g->pp_refs.as<int>() + g->h_levels[k].pp_base;
+        const int *refs = g->h_levels[k].pp;
         CK(pp_offsets_single_level((long long *)off->p, P, k, s));
-        CK(pp_materialize(nullptr, refs, k, P, (const long long *)off->p, dnodes, dlev, g->gd, (int *)vert->p,
+        CK(pp_materialize(nullptr, refs, k, P, (const long long *)off->p, dlev, g->gd, (int *)vert->p,
                           pgraph ? (int *)pgraph->p : nullptr, s));
     } else {
         for (int b = 0; b < 2; ++b) {
@@ -502,12 +592,12 @@ int run_prime_paths(tpg_cfg *g) {
         for (int idx = (int)pp_levels.size() - 1; idx >= 0; --idx) {
             const int k = pp_levels[idx];
             const LevelRec &L = g->h_levels[k];
-            const int *lref = g->pp_refs.as<int>() + L.pp_base;
+            const int *lref = L.pp;
             if (na == 0) {
                 CK(order_init_run(lref, k, L.pp_count, g->s_keys[cur].as<int>(), g->s_refs[cur].as<long long>(), s));
                 na = L.pp_count;
             } else {
-                CK(order_ascend(g->s_keys[cur].as<int>(), na, dnodes, dlev, cur_level, k, s));
+                CK(order_ascend(g->s_keys[cur].as<int>(), na, dlev, cur_level, k, s));
                 CK(order_merge(g->s_keys[cur].as<int>(), g->s_refs[cur].as<long long>(), na, lref, k, L.pp_count,
                                g->s_keys[cur ^ 1].as<int>(), g->s_refs[cur ^ 1].as<long long>(), s));
                 cur ^= 1;
@@ -518,7 +608,7 @@ int run_prime_paths(tpg_cfg *g) {
         const long long *refs = g->s_refs[cur].as<long long>();
         CK(pp_lengths(refs, P, g->s_len.as<long long>(), s));
         CK(scan_i64(g->s_len.as<long long>(), (long long *)off->p, P, g->s_tmp.as<long long>(), s));
-        CK(pp_materialize(refs, nullptr, 0, P, (const long long *)off->p, dnodes, dlev, g->gd, (int *)vert->p,
+        CK(pp_materialize(refs, nullptr, 0, P, (const long long *)off->p, dlev, g->gd, (int *)vert->p,
                           pgraph ? (int *)pgraph->p : nullptr, s));
     }
     if (g->G > 1) {
@@ -1015,6 +1105,23 @@ int tpg_set_stream(tpg_cfg *g, void *stream) {
         return TPG_ECUDA;
     }
     g->stream = (cudaStream_t)stream;
+    return TPG_OK;
+}
+
+int tpg_set_tile_shape(tpg_cfg *g, int32_t block, int32_t items) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    const EnumShape sh{block, items};
+    if (!enum_shape_supported(g->W, sh)) return TPG_EINVAL;
+    g->shape = sh;
+    return TPG_OK;
+}
+
+int tpg_set_capacity(tpg_cfg *g, int64_t nodes, int64_t level_nodes, int64_t prime_paths) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (nodes < 1 || level_nodes < 1 || prime_paths < 1) return TPG_EINVAL;
+    g->node_cap = nodes;
+    g->lvl_cap = level_nodes;
+    g->pp_cap = prime_paths;
     return TPG_OK;
 }
 

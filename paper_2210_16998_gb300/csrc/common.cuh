@@ -26,16 +26,18 @@ constexpr int ERR_OVERFLOW_MASK = ERR_OVF_NODES | ERR_OVF_LEVEL | ERR_OVF_PP | E
 // wall-clock limit of every device-side spin (nanoseconds)
 constexpr unsigned long long SPIN_LIMIT_NS = 4ull * 1000 * 1000 * 1000;
 
-// One frontier level of the path arena.  Written by the last tile of the
-// previous level (node_base, count, status_base) and by the last tile of
-// this level (pp_count).  64 bytes.
+// One frontier level of the path arena.  The arena is a chain of segments;
+// a level lives inside one segment, so a level is addressed by a pointer.
+// Written by the last tile of the previous level (nodes, count, pp,
+// status_base) and by the last tile of this level (pp_count, children).
+// 64 bytes.
 struct LevelRec {
-    long long node_base;    // index of the level's first node in the arena
-    long long count;        // nodes in the level (may exceed capacity on overflow)
-    long long pp_base;      // index of the level's first PP reference
+    int2 *nodes;            // the level's first node {last vertex, parent index}
+    long long count;        // nodes in the level
+    int *pp;                // the level's first PP reference
     long long pp_count;     // PPs found in the level
     long long status_base;  // first look-back status word of the level
-    long long children;     // nodes of the next level (copy, for statistics)
+    long long children;     // nodes of the next level (exact, also on overflow)
     long long pad[2];
 };
 

@@ -19,8 +19,13 @@
 // lexicographic order.  A closed cycle becomes a node of the next level and
 // is reported there as a PP.
 //
-// Path arena (persistent, level-major): node = {last vertex (global id),
-// index of the parent in the previous level}.  Frontier (ping-pong, two
+// Path arena: a chain of segments; each level lies inside one segment and is
+// addressed by a pointer in its level record; node = {last vertex (global
+// id), index of the parent in the previous level}.  When the next level does
+// not fit in the current segment (or the frontier or the PP list is full),
+// the launch stops after recording the exact size that was needed; the host
+// supplies a larger segment or buffer and relaunches AT THAT LEVEL, so no
+// finished level is ever recomputed or copied.  Frontier (ping-pong, two
 // buffers): node = {first, last} (int2) and the visited bitset stored as W
 // separate word arrays (word j of node i at j * lvl_cap + i).
 #include "common.cuh"
@@ -49,7 +54,7 @@ __global__ void init_level1_kernel(EnumArgs a) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
          i += (long long)gridDim.x * blockDim.x) {
         const int v = (int)i;
-        a.nodes[i] = make_int2(v, -1);
+        a.seg[i] = make_int2(v, -1);
         a.tfl[1][i] = make_int2(v, v);
         const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
 #pragma unroll
@@ -58,31 +63,40 @@ __global__ void init_level1_kernel(EnumArgs a) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         LevelRec r = {};
-        r.node_base = 0;
+        r.nodes = a.seg;
         r.count = g.N;
-        r.pp_base = 0;
+        r.pp = a.pp_seg;
         r.status_base = 0;
         a.levels[1] = r;
     }
 }
 
-template <int W, int BLOCK>
+// Per level, a block claims tiles of TILE = BLOCK * ITEMS consecutive paths;
+// thread t owns paths tile*TILE + j*BLOCK + t (j < ITEMS), so every load is
+// coalesced.  The per-path counts (children, PP flag) are scanned in path
+// order through shared memory (striped -> blocked -> striped), and the tile's
+// offset in the next level comes from the decoupled look-back.
+template <int W, int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK) enumerate_kernel(EnumArgs a) {
+    constexpr int TILE = BLOCK * ITEMS;
+    __shared__ unsigned long long s_cnt[TILE];
     __shared__ long long s_tile;
     __shared__ unsigned long long s_pa, s_pb;
     const GraphDev &g = a.g;
     const int tid = threadIdx.x;
 
-    for (int k = 1; k + 1 < a.max_levels; ++k) {
+    for (int k = a.start_level; k + 1 < a.max_levels; ++k) {
         if (__ldcg(a.err) & (ERR_OVERFLOW_MASK | ERR_TIMEOUT | ERR_OVF_LEVELS | ERR_OVF_COUNT)) break;
         const LevelRec *Lp = a.levels + k;
         const long long count = __ldcg(&Lp->count);
         if (count <= 0) break;
-        const long long node_base = __ldcg(&Lp->node_base);
-        const long long pp_base = __ldcg(&Lp->pp_base);
+        int2 *const lnodes = (int2 *)__ldcg((const unsigned long long *)&Lp->nodes);
+        int *const lpp = (int *)__ldcg((const unsigned long long *)&Lp->pp);
         const long long status_base = __ldcg(&Lp->status_base);
-        const long long next_base = node_base + count;
-        const long long ntiles = (count + BLOCK - 1) / BLOCK;
+        int2 *const next = (k == a.start_level && a.next_nodes) ? a.next_nodes : lnodes + count;
+        const long long next_off = next - a.seg;     // offset of the next level in the segment
+        const long long pp_off = lpp - a.pp_seg;     // offset of this level's PPs in their segment
+        const long long ntiles = (count + TILE - 1) / TILE;
         const int2 *in_fl = a.tfl[k & 1];
         const unsigned *in_vis = a.tvis[k & 1];
         int2 *out_fl = a.tfl[(k + 1) & 1];
@@ -95,50 +109,78 @@ __global__ void __launch_bounds__(BLOCK) enumerate_kernel(EnumArgs a) {
             const long long tile = s_tile;
             if (tile >= ntiles) break;
 
-            const long long i = tile * BLOCK + tid;
-            const bool valid = i < count;
-            int first = 0, last = 0, vb = 0, nch = 0;
-            bool pp = false;
-            unsigned vis[W];
+            int first[ITEMS], last[ITEMS], vb[ITEMS], nch[ITEMS], e0[ITEMS], e1[ITEMS];
+            bool pp[ITEMS];
+            unsigned vis[ITEMS][W];
 #pragma unroll
-            for (int j = 0; j < W; ++j) vis[j] = 0u;
-            int e0 = 0, e1 = 0;
-            if (valid) {
-                const int2 fl = __ldcg(in_fl + i);
-                first = fl.x;
-                last = fl.y;
-                if (k >= 2 && first == last) {
-                    pp = true;  // closed simple cycle: never extended, always prime
+            for (int j = 0; j < ITEMS; ++j) {
+                first[j] = last[j] = vb[j] = nch[j] = e0[j] = e1[j] = 0;
+                pp[j] = false;
+#pragma unroll
+                for (int w = 0; w < W; ++w) vis[j][w] = 0u;
+            }
+            // loads first (all ITEMS in flight), then the per-path work
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const long long i = tile * TILE + (long long)j * BLOCK + tid;
+                if (i < count) {
+                    const int2 fl = __ldcg(in_fl + i);
+                    first[j] = fl.x;
+                    last[j] = fl.y;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) vis[j][w] = __ldcg(in_vis + w * a.lvl_cap + i);
                 } else {
-                    vb = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + first)) : 0;
-#pragma unroll
-                    for (int j = 0; j < W; ++j) vis[j] = __ldcg(in_vis + j * a.lvl_cap + i);
-                    e0 = __ldg(g.rp + last);
-                    e1 = __ldg(g.rp + last + 1);
-                    for (int e = e0; e < e1; ++e) {
-                        const int w = __ldg(g.col + e);
-                        if (w == first || !test_bit<W>(vis, w - vb)) ++nch;
-                    }
-                    if (nch == 0) {
-                        // right-maximal; left-maximal iff every predecessor u of
-                        // the first vertex is on the path and is not its last
-                        // vertex (u.p would otherwise be simple)
-                        bool lm = true;
-                        const int p0 = __ldg(g.prp + first), p1 = __ldg(g.prp + first + 1);
-                        for (int e = p0; e < p1; ++e) {
-                            const int u = __ldg(g.pcol + e);
-                            if (u == last || !test_bit<W>(vis, u - vb)) {
-                                lm = false;
-                                break;
-                            }
-                        }
-                        pp = lm;
-                    }
+                    first[j] = -1;
                 }
             }
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if (first[j] < 0) continue;
+                if (k >= 2 && first[j] == last[j]) {
+                    pp[j] = true;  // closed simple cycle: never extended, always prime
+                    continue;
+                }
+                vb[j] = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + first[j])) : 0;
+                e0[j] = __ldg(g.rp + last[j]);
+                e1[j] = __ldg(g.rp + last[j] + 1);
+                int c = 0;
+                for (int e = e0[j]; e < e1[j]; ++e) {
+                    const int w = __ldg(g.col + e);
+                    if (w == first[j] || !test_bit<W>(vis[j], w - vb[j])) ++c;
+                }
+                nch[j] = c;
+                if (c == 0) {
+                    // right-maximal; left-maximal iff every predecessor u of
+                    // the first vertex is on the path and is not its last
+                    // vertex (u.p would otherwise be simple)
+                    bool lm = true;
+                    const int p0 = __ldg(g.prp + first[j]), p1 = __ldg(g.prp + first[j] + 1);
+                    for (int e = p0; e < p1; ++e) {
+                        const int u = __ldg(g.pcol + e);
+                        if (u == last[j] || !test_bit<W>(vis[j], u - vb[j])) {
+                            lm = false;
+                            break;
+                        }
+                    }
+                    pp[j] = lm;
+                }
+            }
+            // exclusive scan of (children, PP) in path order
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                s_cnt[j * BLOCK + tid] = ((unsigned long long)nch[j] << 32) | (pp[j] ? 1ull : 0ull);
+            __syncthreads();
+            unsigned long long run = 0;
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) run += s_cnt[tid * ITEMS + q];
             unsigned long long total;
-            const unsigned long long ex = block_excl_scan_u64<BLOCK>(
-                ((unsigned long long)nch << 32) | (pp ? 1ull : 0ull), total);
+            unsigned long long base = block_excl_scan_u64<BLOCK>(run, total);
+#pragma unroll
+            for (int q = 0; q < ITEMS; ++q) {
+                const unsigned long long v = s_cnt[tid * ITEMS + q];
+                s_cnt[tid * ITEMS + q] = base;
+                base += v;
+            }
             const unsigned long long agg_c = total >> 32, agg_p = total & 0xffffffffull;
             if (tid < 32) {
                 unsigned long long pa, pb;
@@ -149,53 +191,60 @@ __global__ void __launch_bounds__(BLOCK) enumerate_kernel(EnumArgs a) {
                 }
             }
             __syncthreads();
-            long long cpos = (long long)s_pa + (long long)(ex >> 32);
-            const long long ppos = (long long)s_pb + (long long)(ex & 0xffffffffull);
-            if (nch > 0) {
-                for (int e = e0; e < e1; ++e) {
-                    const int w = __ldg(g.col + e);
-                    const bool closes = (w == first);
-                    if (closes || !test_bit<W>(vis, w - vb)) {
-                        const long long gi = next_base + cpos;
-                        if (cpos < a.lvl_cap && gi < a.node_cap) {
-                            a.nodes[gi] = make_int2(w, (int)i);
-                            out_fl[cpos] = make_int2(first, w);
-                            if (!closes) {
-                                const int b = w - vb;
 #pragma unroll
-                                for (int j = 0; j < W; ++j)
-                                    out_vis[j * a.lvl_cap + cpos] =
-                                        vis[j] | ((j == (b >> 5)) ? (1u << (b & 31)) : 0u);
+            for (int j = 0; j < ITEMS; ++j) {
+                const unsigned long long ex = s_cnt[j * BLOCK + tid];
+                const long long i = tile * TILE + (long long)j * BLOCK + tid;
+                if (nch[j] > 0) {
+                    long long cpos = (long long)s_pa + (long long)(ex >> 32);
+                    for (int e = e0[j]; e < e1[j]; ++e) {
+                        const int w = __ldg(g.col + e);
+                        const bool closes = (w == first[j]);
+                        if (closes || !test_bit<W>(vis[j], w - vb[j])) {
+                            if (cpos < a.lvl_cap && next_off + cpos < a.seg_cap) {
+                                next[cpos] = make_int2(w, (int)i);
+                                out_fl[cpos] = make_int2(first[j], w);
+                                if (!closes) {
+                                    const int b = w - vb[j];
+#pragma unroll
+                                    for (int ww = 0; ww < W; ++ww)
+                                        out_vis[ww * a.lvl_cap + cpos] =
+                                            vis[j][ww] | ((ww == (b >> 5)) ? (1u << (b & 31)) : 0u);
+                                }
                             }
+                            ++cpos;
                         }
-                        ++cpos;
                     }
                 }
-            }
-            if (pp) {
-                const long long q = pp_base + ppos;
-                if (q < a.pp_cap) a.pp_refs[q] = (int)i;
+                if (pp[j]) {
+                    const long long q = (long long)s_pb + (long long)(ex & 0xffffffffull);
+                    if (pp_off + q < a.pp_seg_cap) lpp[q] = (int)i;
+                }
             }
             if (tile == ntiles - 1 && tid == 0) {
                 const long long C = (long long)s_pa + (long long)agg_c;
                 const long long P = (long long)s_pb + (long long)agg_p;
                 int e = 0;
                 if (C >= (long long)MAX31 || P >= (long long)MAX31) e |= ERR_OVF_COUNT;
-                if (next_base + C > a.node_cap) e |= ERR_OVF_NODES;
+                if (next_off + C > a.seg_cap) e |= ERR_OVF_NODES;
                 if (C > a.lvl_cap) e |= ERR_OVF_LEVEL;
-                if (pp_base + P > a.pp_cap) e |= ERR_OVF_PP;
-                const long long nt_next = (C + BLOCK - 1) / BLOCK;
+                if (pp_off + P > a.pp_seg_cap) e |= ERR_OVF_PP;
+                const long long nt_next = (C + TILE - 1) / TILE;
                 if (status_base + ntiles + nt_next > a.status_cap) e |= ERR_OVF_STATUS;
                 if (k + 2 >= a.max_levels && C > 0) e |= ERR_OVF_LEVELS;
                 a.levels[k].pp_count = P;
                 a.levels[k].children = C;
-                LevelRec r = {};
-                r.node_base = next_base;
-                r.count = C;
-                r.pp_base = pp_base + P;
-                r.status_base = status_base + ntiles;
-                a.levels[k + 1] = r;
-                if (e) atomicOr(a.err, e);
+                if (e) {
+                    *a.stop_level = k;
+                    atomicOr(a.err, e);
+                } else {
+                    LevelRec r = {};
+                    r.nodes = next;
+                    r.count = C;
+                    r.pp = lpp + P;
+                    r.status_base = status_base + ntiles;
+                    a.levels[k + 1] = r;
+                }
             }
             __syncthreads();
         }
@@ -206,27 +255,82 @@ __global__ void __launch_bounds__(BLOCK) enumerate_kernel(EnumArgs a) {
 // ---------------------------------------------------------------------------
 // host-side launch
 // ---------------------------------------------------------------------------
-template <int W, int BLOCK>
-static cudaError_t launch_w(const EnumArgs &args, int num_sms, cudaStream_t s, int *grid_out) {
+template <int W, int BLOCK, int ITEMS>
+static cudaError_t launch_wbi(const EnumArgs &args, int num_sms, cudaStream_t s, int *grid_out) {
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &blocks_per_sm, enumerate_kernel<W, BLOCK>, BLOCK, 0);
+            &blocks_per_sm, enumerate_kernel<W, BLOCK, ITEMS>, BLOCK, 0);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     const int grid = num_sms * blocks_per_sm;
     *grid_out = grid;
-    init_level1_kernel<W><<<(args.g.N + 255) / 256, 256, 0, s>>>(args);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (args.seed_level1) {
+        init_level1_kernel<W><<<(args.g.N + 255) / 256, 256, 0, s>>>(args);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     EnumArgs a = args;
     void *params[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void *)enumerate_kernel<W, BLOCK>, dim3(grid), dim3(BLOCK),
+    e = cudaLaunchCooperativeKernel((const void *)enumerate_kernel<W, BLOCK, ITEMS>, dim3(grid), dim3(BLOCK),
                                     params, 0, s);
     if (e == cudaSuccess) note_launch();
     return e;
+}
+
+// tile shapes available per bitset width (the autotuner picks among them)
+template <int W>
+static cudaError_t launch_w(const EnumArgs &args, EnumShape shape, int num_sms, cudaStream_t s, int *grid_out) {
+    if constexpr (W <= 8) {
+        if (shape.block == 128) {
+            if (shape.items == 1) return launch_wbi<W, 128, 1>(args, num_sms, s, grid_out);
+            if (shape.items == 2) return launch_wbi<W, 128, 2>(args, num_sms, s, grid_out);
+            if (shape.items == 4) return launch_wbi<W, 128, 4>(args, num_sms, s, grid_out);
+        } else if (shape.block == 256) {
+            if (shape.items == 1) return launch_wbi<W, 256, 1>(args, num_sms, s, grid_out);
+            if (shape.items == 2) return launch_wbi<W, 256, 2>(args, num_sms, s, grid_out);
+            if (shape.items == 4) return launch_wbi<W, 256, 4>(args, num_sms, s, grid_out);
+        } else if (shape.block == 512) {
+            if (shape.items == 1) return launch_wbi<W, 512, 1>(args, num_sms, s, grid_out);
+            if (shape.items == 2) return launch_wbi<W, 512, 2>(args, num_sms, s, grid_out);
+        }
+        return cudaErrorInvalidValue;
+    } else {
+        return launch_wbi<W, 256, 1>(args, num_sms, s, grid_out);
+    }
+}
+
+__global__ void relayout_kernel(const int2 *fl_old, const unsigned *vis_old, long long cap_old, int2 *fl_new,
+                                unsigned *vis_new, long long cap_new, long long count, int W) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        fl_new[i] = fl_old[i];
+        for (int w = 0; w < W; ++w) vis_new[w * cap_new + i] = vis_old[w * cap_old + i];
+    }
+}
+
+cudaError_t relayout_frontier(const int2 *fl_old, const unsigned *vis_old, long long cap_old, int2 *fl_new,
+                              unsigned *vis_new, long long cap_new, long long count, int W, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    relayout_kernel<<<(unsigned)blocks, 256, 0, s>>>(fl_old, vis_old, cap_old, fl_new, vis_new, cap_new, count, W);
+    note_launch();
+    return cudaGetLastError();
+}
+
+bool enum_shape_supported(int W, EnumShape shape) {
+    if (W > 8) return shape.block == 256 && shape.items == 1;
+    if (shape.block == 128 || shape.block == 256) return shape.items == 1 || shape.items == 2 || shape.items == 4;
+    if (shape.block == 512) return shape.items == 1 || shape.items == 2;
+    return false;
+}
+
+EnumShape default_enum_shape(int W) {
+    if (W > 8) return EnumShape{256, 1};
+    return EnumShape{256, 4};
 }
 
 int bitset_words_supported(int maxn) {
@@ -237,20 +341,20 @@ int bitset_words_supported(int maxn) {
     return -1;
 }
 
-cudaError_t launch_enumerate(const EnumArgs &args, int num_sms, cudaStream_t s, int *grid_out) {
-    constexpr int B = ENUM_BLOCK;
+cudaError_t launch_enumerate(const EnumArgs &args, EnumShape shape, int num_sms, cudaStream_t s, int *grid_out) {
+    if (!enum_shape_supported(args.g.W, shape)) return cudaErrorInvalidValue;
     switch (args.g.W) {
-        case 1: return launch_w<1, B>(args, num_sms, s, grid_out);
-        case 2: return launch_w<2, B>(args, num_sms, s, grid_out);
-        case 3: return launch_w<3, B>(args, num_sms, s, grid_out);
-        case 4: return launch_w<4, B>(args, num_sms, s, grid_out);
-        case 5: return launch_w<5, B>(args, num_sms, s, grid_out);
-        case 6: return launch_w<6, B>(args, num_sms, s, grid_out);
-        case 8: return launch_w<8, B>(args, num_sms, s, grid_out);
-        case 16: return launch_w<16, B>(args, num_sms, s, grid_out);
-        case 32: return launch_w<32, B>(args, num_sms, s, grid_out);
-        case 64: return launch_w<64, B>(args, num_sms, s, grid_out);
-        case 128: return launch_w<128, B>(args, num_sms, s, grid_out);
+        case 1: return launch_w<1>(args, shape, num_sms, s, grid_out);
+        case 2: return launch_w<2>(args, shape, num_sms, s, grid_out);
+        case 3: return launch_w<3>(args, shape, num_sms, s, grid_out);
+        case 4: return launch_w<4>(args, shape, num_sms, s, grid_out);
+        case 5: return launch_w<5>(args, shape, num_sms, s, grid_out);
+        case 6: return launch_w<6>(args, shape, num_sms, s, grid_out);
+        case 8: return launch_w<8>(args, shape, num_sms, s, grid_out);
+        case 16: return launch_w<16>(args, shape, num_sms, s, grid_out);
+        case 32: return launch_w<32>(args, shape, num_sms, s, grid_out);
+        case 64: return launch_w<64>(args, shape, num_sms, s, grid_out);
+        case 128: return launch_w<128>(args, shape, num_sms, s, grid_out);
         default: return cudaErrorInvalidValue;
     }
 }

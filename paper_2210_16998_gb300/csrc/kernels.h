@@ -12,29 +12,42 @@ namespace tpg {
 extern std::atomic<long long> g_kernel_launches;
 inline void note_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
-constexpr int ENUM_BLOCK = 256;
+constexpr int ENUM_MIN_TILE = 128;  // smallest tile (status words are sized for it)
 
 struct EnumArgs {
     GraphDev g;
-    int2 *nodes;             // persistent arena {last, parent}
-    long long node_cap;
+    int2 *seg;               // current arena segment (nodes {last, parent})
+    long long seg_cap;
+    int2 *next_nodes;        // where level start_level+1 starts (null: right after level start_level)
+    int *pp_seg;             // current PP-reference segment
+    long long pp_seg_cap;
     int2 *tfl[2];            // ping-pong {first, last}
     unsigned *tvis[2];       // ping-pong bitsets, W word-arrays of lvl_cap each
     long long lvl_cap;
-    int *pp_refs;            // PP node indices (relative to their level), level-major
-    long long pp_cap;
     LevelRec *levels;        // [max_levels]
     int max_levels;
+    int start_level;         // first level processed by this launch
+    int seed_level1;         // 1 on a fresh run: level 1 is written first (never on a resume)
     unsigned long long *status;  // look-back status words (zeroed)
     long long status_cap;
-    int *tile_ctr;           // [max_levels] (zeroed)
+    int *tile_ctr;           // [max_levels] (zeroed from start_level on)
     int *err;                // error flags (zeroed)
+    int *stop_level;         // level whose next level did not fit (written with the flags)
     unsigned *bar;           // grid barrier {count, generation} (zeroed)
 };
 
 // enumerate.cu
+struct EnumShape {
+    int block;  // threads per block
+    int items;  // paths per thread; a tile is block * items consecutive paths
+};
 int bitset_words_supported(int maxn);
-cudaError_t launch_enumerate(const EnumArgs &args, int num_sms, cudaStream_t s, int *grid_out);
+bool enum_shape_supported(int W, EnumShape shape);
+EnumShape default_enum_shape(int W);
+cudaError_t launch_enumerate(const EnumArgs &args, EnumShape shape, int num_sms, cudaStream_t s, int *grid_out);
+// copy the first `count` frontier records to buffers of another capacity
+cudaError_t relayout_frontier(const int2 *fl_old, const unsigned *vis_old, long long cap_old, int2 *fl_new,
+                              unsigned *vis_new, long long cap_new, long long count, int W, cudaStream_t s);
 
 // scan.cu: exclusive scan of int64 (in may equal out); tmp must hold
 // scan_tmp_elems(n) int64 values.  out[n] receives the total.
@@ -47,15 +60,15 @@ cudaError_t scan_i32_to_i64(const int *in, long long *out, long long n, long lon
 // canonical ordering of PP references across levels (ancestor-index merge)
 cudaError_t order_init_run(const int *pp_refs_level, int level, long long n, int *keys,
                            long long *refs, cudaStream_t s);
-cudaError_t order_ascend(int *keys, long long n, const int2 *nodes, const LevelRec *levels,
-                         int from_level, int to_level, cudaStream_t s);
+cudaError_t order_ascend(int *keys, long long n, const LevelRec *levels, int from_level, int to_level,
+                         cudaStream_t s);
 cudaError_t order_merge(const int *ka, const long long *ra, long long na, const int *kb, int level_b,
                         long long nb, int *kc, long long *rc, cudaStream_t s);
 cudaError_t pp_lengths(const long long *refs, long long n, long long *len_out, cudaStream_t s);
 cudaError_t pp_offsets_single_level(long long *off, long long n, int level, cudaStream_t s);
 cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,
-                           const long long *offsets, const int2 *nodes, const LevelRec *levels,
-                           const GraphDev &g, int *out_vertices, int *out_graph, cudaStream_t s);
+                           const long long *offsets, const LevelRec *levels, const GraphDev &g,
+                           int *out_vertices, int *out_graph, cudaStream_t s);
 cudaError_t graph_ptr_from_ids(const int *ids, long long n, int G, long long *ptr, cudaStream_t s);
 
 // preprocess.cu

@@ -30,6 +30,8 @@ constexpr long long NA_NODE_CAP = 1LL << 20;  // simple paths in the arena
 constexpr long long NA_LVL_CAP = 1LL << 18;   // simple paths in one level
 constexpr long long NA_PP_CAP = 1LL << 18;    // prime paths
 constexpr int NA_W = 4;
+constexpr EnumShape NA_SHAPE = {256, 1};  // tile of 256 paths
+constexpr int NA_TILE = 256;
 constexpr int NA_MAX_LEVELS = NA_MAXN + 4;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -57,7 +59,7 @@ constexpr NaLayout na_layout() {
     L.tvis0 = o;   o = align256(o + sizeof(unsigned) * NA_W * NA_LVL_CAP);
     L.tvis1 = o;   o = align256(o + sizeof(unsigned) * NA_W * NA_LVL_CAP);
     L.pprefs = o;  o = align256(o + sizeof(int) * NA_PP_CAP);
-    L.status = o;  o = align256(o + sizeof(unsigned long long) * (NA_NODE_CAP / ENUM_BLOCK + 2 * NA_MAX_LEVELS + 64));
+    L.status = o;  o = align256(o + sizeof(unsigned long long) * (NA_NODE_CAP / NA_TILE + 2 * NA_MAX_LEVELS + 64));
     L.keys0 = o;   o = align256(o + sizeof(int) * NA_PP_CAP);
     L.keys1 = o;   o = align256(o + sizeof(int) * NA_PP_CAP);
     L.refs0 = o;   o = align256(o + sizeof(long long) * NA_PP_CAP);
@@ -183,21 +185,25 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     // 3. the frontier kernel over the scratch arena
     EnumArgs a{};
     a.g = d;
-    a.nodes = (int2 *)(S + NA.nodes);
-    a.node_cap = NA_NODE_CAP;
+    a.seg = (int2 *)(S + NA.nodes);
+    a.seg_cap = NA_NODE_CAP;
+    a.next_nodes = nullptr;
     a.tfl[0] = (int2 *)(S + NA.tfl0);
     a.tfl[1] = (int2 *)(S + NA.tfl1);
     a.tvis[0] = (unsigned *)(S + NA.tvis0);
     a.tvis[1] = (unsigned *)(S + NA.tvis1);
     a.lvl_cap = NA_LVL_CAP;
-    a.pp_refs = (int *)(S + NA.pprefs);
-    a.pp_cap = NA_PP_CAP;
+    a.pp_seg = (int *)(S + NA.pprefs);
+    a.pp_seg_cap = NA_PP_CAP;
     a.levels = (LevelRec *)(S + NA.levels);
     a.max_levels = n + 4;
+    a.start_level = 1;
+    a.seed_level1 = 1;
     a.status = (unsigned long long *)(S + NA.status);
-    a.status_cap = NA_NODE_CAP / ENUM_BLOCK + 2 * NA_MAX_LEVELS + 64;
+    a.status_cap = NA_NODE_CAP / NA_TILE + 2 * NA_MAX_LEVELS + 64;
     a.tile_ctr = (int *)(S + NA.tile);
     a.err = err;
+    a.stop_level = err + 1;
     a.bar = (unsigned *)(S + NA.ctl + 64);
     NA_CK(cudaMemsetAsync(a.levels, 0, sizeof(LevelRec) * NA_MAX_LEVELS, s));
     NA_CK(cudaMemsetAsync(a.status, 0, sizeof(unsigned long long) * a.status_cap, s));
@@ -206,7 +212,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     int num_sms = 1, dev = 0, grid = 0;
     NA_CK(cudaGetDevice(&dev));
     NA_CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-    NA_CK(launch_enumerate(a, num_sms, s, &grid));
+    NA_CK(launch_enumerate(a, NA_SHAPE, num_sms, s, &grid));
     LevelRec lv[NA_MAX_LEVELS];
     NA_CK(cudaMemcpyAsync(lv, a.levels, sizeof(LevelRec) * NA_MAX_LEVELS, cudaMemcpyDeviceToHost, s));
     NA_CK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -231,15 +237,14 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     if (P > cap_paths || V > cap_vertices) return TPG_ETOOBIG;
 
     // 5. canonical order and materialisation into the caller's buffers
-    const int2 *dnodes = a.nodes;
     const LevelRec *dlev = a.levels;
     if (P == 0) {
         NA_CK(cudaMemsetAsync(offsets_dev, 0, sizeof(long long), s));
     } else if (npl == 1) {
         const int k = pp_levels[0];
         NA_CK(pp_offsets_single_level((long long *)offsets_dev, P, k, s));
-        NA_CK(pp_materialize(nullptr, a.pp_refs + lv[k].pp_base, k, P, (const long long *)offsets_dev, dnodes, dlev,
-                             d, vertices_dev, nullptr, s));
+        NA_CK(pp_materialize(nullptr, lv[k].pp, k, P, (const long long *)offsets_dev, dlev, d, vertices_dev,
+                             nullptr, s));
     } else {
         int *keys[2] = {(int *)(S + NA.keys0), (int *)(S + NA.keys1)};
         long long *refs[2] = {(long long *)(S + NA.refs0), (long long *)(S + NA.refs1)};
@@ -247,12 +252,12 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
         long long na = 0;
         for (int idx = npl - 1; idx >= 0; --idx) {
             const int k = pp_levels[idx];
-            const int *lref = a.pp_refs + lv[k].pp_base;
+            const int *lref = lv[k].pp;
             if (na == 0) {
                 NA_CK(order_init_run(lref, k, lv[k].pp_count, keys[cur], refs[cur], s));
                 na = lv[k].pp_count;
             } else {
-                NA_CK(order_ascend(keys[cur], na, dnodes, dlev, cur_level, k, s));
+                NA_CK(order_ascend(keys[cur], na, dlev, cur_level, k, s));
                 NA_CK(order_merge(keys[cur], refs[cur], na, lref, k, lv[k].pp_count, keys[cur ^ 1], refs[cur ^ 1], s));
                 cur ^= 1;
                 na += lv[k].pp_count;
@@ -261,7 +266,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
         }
         NA_CK(pp_lengths(refs[cur], P, (long long *)(S + NA.len), s));
         NA_CK(scan_i64((long long *)(S + NA.len), (long long *)offsets_dev, P, (long long *)(S + NA.ltmp), s));
-        NA_CK(pp_materialize(refs[cur], nullptr, 0, P, (const long long *)offsets_dev, dnodes, dlev, d, vertices_dev,
+        NA_CK(pp_materialize(refs[cur], nullptr, 0, P, (const long long *)offsets_dev, dlev, d, vertices_dev,
                              nullptr, s));
     }
     NA_CK(cudaStreamSynchronize(s));

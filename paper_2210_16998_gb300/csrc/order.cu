@@ -32,22 +32,21 @@ cudaError_t order_init_run(const int *pp_refs_level, int level, long long n, int
     return cudaGetLastError();
 }
 
-__global__ void order_ascend_kernel(int *keys, long long n, const int2 *nodes, const LevelRec *levels,
-                                    int from_level, int to_level) {
+__global__ void order_ascend_kernel(int *keys, long long n, const LevelRec *levels, int from_level, int to_level) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         int key = keys[i];
-        for (int j = from_level; j > to_level; --j) key = nodes[levels[j].node_base + key].y;
+        for (int j = from_level; j > to_level; --j) key = levels[j].nodes[key].y;
         keys[i] = key;
     }
 }
 
-cudaError_t order_ascend(int *keys, long long n, const int2 *nodes, const LevelRec *levels, int from_level,
-                         int to_level, cudaStream_t s) {
+cudaError_t order_ascend(int *keys, long long n, const LevelRec *levels, int from_level, int to_level,
+                         cudaStream_t s) {
     if (n <= 0 || from_level <= to_level) return cudaSuccess;
     const long long blocks = (n + 255) / 256;
     order_ascend_kernel<<<(unsigned)(blocks < 1 << 20 ? blocks : 1 << 20), 256, 0, s>>>(
-        keys, n, nodes, levels, from_level, to_level);
+        keys, n, levels, from_level, to_level);
     note_launch();
     return cudaGetLastError();
 }
@@ -131,8 +130,8 @@ constexpr int MAT_BUF = 2048;  // int32 per warp (8 KB)
 
 __global__ void __launch_bounds__(MAT_WARPS * 32)
     pp_materialize_kernel(const long long *refs, const int *single_refs, int single_level, long long n,
-                          const long long *offsets, const int2 *nodes, const LevelRec *levels, GraphDev g,
-                          int *out, int *out_graph) {
+                          const long long *offsets, const LevelRec *levels, GraphDev g, int *out,
+                          int *out_graph) {
     __shared__ int buf[MAT_WARPS][MAT_BUF];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long nwarps = (long long)gridDim.x * MAT_WARPS;
@@ -157,7 +156,7 @@ __global__ void __launch_bounds__(MAT_WARPS * 32)
         const bool staged = span <= MAT_BUF;
         int node = rel, root = 0;
         for (int j = level; j >= 1; --j) {
-            const int2 rec = nodes[levels[j].node_base + node];
+            const int2 rec = levels[j].nodes[node];
             const int v = rec.x;
             const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
             if (staged) buf[wid][off - start + (j - 1)] = loc;
@@ -175,14 +174,14 @@ __global__ void __launch_bounds__(MAT_WARPS * 32)
 }
 
 cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,
-                           const long long *offsets, const int2 *nodes, const LevelRec *levels, const GraphDev &g,
-                           int *out_vertices, int *out_graph, cudaStream_t s) {
+                           const long long *offsets, const LevelRec *levels, const GraphDev &g, int *out_vertices,
+                           int *out_graph, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const long long warps = (n + 31) / 32;
     long long blocks = (warps + MAT_WARPS - 1) / MAT_WARPS;
     if (blocks > 152 * 64) blocks = 152 * 64;
     pp_materialize_kernel<<<(unsigned)blocks, MAT_WARPS * 32, 0, s>>>(refs, single_refs, single_level, n, offsets,
-                                                                     nodes, levels, g, out_vertices, out_graph);
+                                                                     levels, g, out_vertices, out_graph);
     note_launch();
     return cudaGetLastError();
 }

@@ -75,6 +75,8 @@ class _Stats(ctypes.Structure):
         ("t_order_ms", ctypes.c_float),
         ("t_test_paths_ms", ctypes.c_float),
         ("enumerate_grid", ctypes.c_int32),
+        ("tile_block", ctypes.c_int32),
+        ("tile_items", ctypes.c_int32),
     ]
 
 
@@ -122,6 +124,8 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_free.restype = None
         lib.tpg_set_stream.argtypes = [P, P]
         lib.tpg_set_result_location.argtypes = [P, ctypes.c_int32]
+        lib.tpg_set_tile_shape.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+        lib.tpg_set_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         lib.tpg_set_allocator.argtypes = [_ALLOC_FN, _RELEASE_FN, P]
         lib.tpg_get_stats.argtypes = [P, ctypes.POINTER(_Stats)]
         lib.tpg_strerror.argtypes = [ctypes.c_int]
@@ -134,7 +138,7 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_prime_paths_noalloc.restype = ctypes.c_int
         for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
                      "tpg_test_paths", "tpg_set_stream", "tpg_set_result_location", "tpg_set_allocator",
-                     "tpg_get_stats"):
+                     "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_capacity"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     if install_torch_allocator:
@@ -363,6 +367,15 @@ def tpg_set_stream(cfg: Cfg, stream):
 
 def tpg_set_result_location(cfg: Cfg, location: int):
     _check(load_library().tpg_set_result_location(cfg.handle, int(location)), "tpg_set_result_location")
+
+
+def tpg_set_tile_shape(cfg: Cfg, block: int, items: int):
+    _check(load_library().tpg_set_tile_shape(cfg.handle, int(block), int(items)), "tpg_set_tile_shape")
+
+
+def tpg_set_capacity(cfg: Cfg, nodes: int, level_nodes: int, prime_paths: int):
+    _check(load_library().tpg_set_capacity(cfg.handle, int(nodes), int(level_nodes), int(prime_paths)),
+           "tpg_set_capacity")
 
 
 def tpg_set_allocator(alloc=None, release=None):

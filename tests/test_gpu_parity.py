@@ -25,8 +25,12 @@ def _lib():
     tpg.load_library(build=True)
 
 
-def gpu_run(cfg, location=tpg.TPG_RESULT_HOST, test_paths=True):
+def gpu_run(cfg, location=tpg.TPG_RESULT_HOST, test_paths=True, capacity=None, shape=None):
     with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=location) as h:
+        if capacity:
+            tpg.tpg_set_capacity(h, *capacity)
+        if shape:
+            tpg.tpg_set_tile_shape(h, *shape)
         pp = tpg.tpg_prime_paths(h)
         ppa = pp.host_arrays()
         pp.free()
@@ -39,9 +43,9 @@ def gpu_run(cfg, location=tpg.TPG_RESULT_HOST, test_paths=True):
     return ppa, tpa, stats
 
 
-def check_cfg(cfg, test_paths=True, location=tpg.TPG_RESULT_HOST):
-    ref = oracle.run_cfg(cfg, test_paths=test_paths)
-    (gp, off, vert), tpa, stats = gpu_run(cfg, location, test_paths)
+def check_cfg(cfg, test_paths=True, location=tpg.TPG_RESULT_HOST, capacity=None, shape=None, ref=None):
+    ref = ref or oracle.run_cfg(cfg, test_paths=test_paths)
+    (gp, off, vert), tpa, stats = gpu_run(cfg, location, test_paths, capacity, shape)
     assert list(gp) == [0, len(off) - 1]
     assert_paths_equal(off, vert, ref.pp_offsets, ref.pp_vertices, f"{cfg.name} PP")
     assert stats["simple_paths"] == ref.n_simple
@@ -174,3 +178,31 @@ def test_repeated_calls_are_identical():
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             np.testing.assert_array_equal(a, b)
+
+
+@pytest.fixture(scope="module")
+def config3_ref():
+    return oracle.run_cfg(G.config3_cfg())
+
+
+@pytest.mark.parametrize("caps", [(200, 130, 7), (5000, 700, 64), (100000, 4000, 100000)])
+def test_tiny_arena_resumes_at_the_failing_level(caps, config3_ref):
+    """Arena, frontier and PP capacities far below the need: the launch stops
+    and resumes with new segments; the result must not change."""
+    ref, stats = check_cfg(G.config3_cfg(), capacity=caps, ref=config3_ref)
+    assert stats["attempts"] > 1
+    assert stats["prime_paths"] == ref.num_pp
+
+
+@pytest.mark.parametrize("shape", [(128, 1), (128, 2), (128, 4), (256, 1), (256, 2), (256, 4), (512, 1), (512, 2)])
+def test_every_tile_shape(shape, config3_ref):
+    ref, stats = check_cfg(G.config3_cfg(), shape=shape, ref=config3_ref)
+    assert (stats["tile_block"], stats["tile_items"]) == shape
+
+
+def test_unsupported_tile_shape_rejected():
+    cfg = G.config1_cfg()
+    with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit) as h:
+        with pytest.raises(tpg.TPGError) as e:
+            tpg.tpg_set_tile_shape(h, 512, 4)
+        assert e.value.code == tpg.TPG_EINVAL
