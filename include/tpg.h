@@ -90,6 +90,11 @@ typedef struct tpg_stats {
     int32_t enumerate_grid;     /* blocks of the persistent frontier launch */
     int32_t tile_block;         /* threads per block of the frontier launch */
     int32_t tile_items;         /* paths per thread (tile = block * items paths) */
+    float t_graph_ms;           /* device time of the last tpg_graph_launch replay */
+    int32_t graph_launches;     /* tpg_graph_launch calls on this handle */
+    int32_t graph_fallbacks;    /* of them, replays whose capacities were too small */
+    int32_t graph_flags;        /* status word of the last replay (0 = complete) */
+    int32_t graph_enum_error;   /* frontier-launch error word of the last replay */
 } tpg_stats;
 
 /*
@@ -197,6 +202,33 @@ int tpg_set_tile_shape(tpg_cfg *g, int32_t block, int32_t items);
  * depend on them; a pre-sizing policy (e.g. the learned sizer) sets them.
  */
 int tpg_set_capacity(tpg_cfg *g, int64_t nodes, int64_t level_nodes, int64_t prime_paths);
+
+/*
+ * Graph mode (batched persistent launch captured in a CUDA graph).
+ *
+ * tpg_graph_capture records the whole hot path of the handle -- the
+ * persistent frontier launch over every graph of the handle, the PP ordering
+ * and materialisation, TP assembly, sort and dedup -- as one CUDA graph whose
+ * kernels read every size from device memory, with fixed buffer capacities:
+ * those set by tpg_set_capacity / tpg_set_output_capacity, else the exact
+ * sizes of the handle's last tpg_prime_paths + tpg_test_paths (run once
+ * first if there was none).  The capture is tied to the handle's stream
+ * (a private stream if it is the legacy default stream).
+ *
+ * tpg_graph_launch replays it and returns the PP and TP lists in *pp and
+ * *tp (result location as set).  Device results of a replay alias the
+ * capture's output buffers: they stay valid until the next replay on this
+ * handle.  If a capacity proved too small, the call computes the exact
+ * result with the host-driven path instead, counts a fallback in the stats
+ * and re-captures on the next launch; results are identical either way.
+ *
+ * tpg_set_output_capacity sets the output capacities used by the next
+ * capture: PPs, PP vertices, TP vertices before dedup, TP vertices.
+ */
+int tpg_graph_capture(tpg_cfg *g);
+int tpg_graph_launch(tpg_cfg *g, tpg_paths **pp, tpg_paths **tp);
+int tpg_set_output_capacity(tpg_cfg *g, int64_t prime_paths, int64_t pp_vertices,
+                            int64_t tp_vertices_raw, int64_t tp_vertices);
 
 /* Statistics of the handle's last calls. */
 int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);

@@ -193,7 +193,24 @@ struct tpg_cfg {
     bool pp_valid = false;
 
     tpg_stats stats{};
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[8] = {};
+    long long last_tv0 = 0;  // TP vertices before dedup in the last tpg_test_paths
+
+    // graph mode: the whole hot path captured in one CUDA graph
+    struct GraphPlan {
+        bool ready = false;
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t own_stream = nullptr;
+        DevBuf seg, ppseg, tfl[2], tvis[2], status;
+        DevBuf lvl_pp_off, keys[2], refs[2], len, scan_tmp, pp_graph, tp_len, run_start, run_rank, tp_graph0,
+            run_base, nruns, bounds0, tp_off0, tp_vert0, perm[2], keep, keep_off, keep_rank, tp_graph, counts;
+        Block *pp_off = nullptr, *pp_vert = nullptr, *pp_gptr = nullptr;
+        Block *tp_off = nullptr, *tp_vert = nullptr, *tp_gptr = nullptr;
+        long long seg_cap = 0, pp_cap = 0, lvl_cap = 0, status_cap = 0;
+        long long P_cap = 0, V_cap = 0, TV0_cap = 0, TV_cap = 0;
+        long long kernels_per_replay = 0;
+    } gp;
+    long long out_cap[4] = {0, 0, 0, 0};  // explicit output capacities P, V, TV0, TV (0 = last run)
     std::vector<LevelRec> h_levels;
     int *h_small = nullptr;  // pinned staging for small read-backs (4 KB)
 };
@@ -228,9 +245,30 @@ void drop_cache(tpg_cfg *g) {
     g->pp_valid = false;
 }
 
+void release_plan(tpg_cfg *g) {
+    auto &p = g->gp;
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    p.exec = nullptr;
+    DevBuf *all[] = {&p.seg, &p.ppseg, &p.tfl[0], &p.tfl[1], &p.tvis[0], &p.tvis[1], &p.status, &p.lvl_pp_off,
+                     &p.keys[0], &p.keys[1], &p.refs[0], &p.refs[1], &p.len, &p.scan_tmp, &p.pp_graph, &p.tp_len,
+                     &p.run_start, &p.run_rank, &p.tp_graph0, &p.run_base, &p.nruns, &p.bounds0, &p.tp_off0,
+                     &p.tp_vert0, &p.perm[0], &p.perm[1], &p.keep, &p.keep_off, &p.keep_rank, &p.tp_graph,
+                     &p.counts};
+    for (DevBuf *b : all) release(g, *b);
+    Block *bl[] = {p.pp_off, p.pp_vert, p.pp_gptr, p.tp_off, p.tp_vert, p.tp_gptr};
+    for (Block *b : bl) block_unref(b);
+    p.pp_off = p.pp_vert = p.pp_gptr = p.tp_off = p.tp_vert = p.tp_gptr = nullptr;
+    p.ready = false;
+}
+
 void destroy_cfg(tpg_cfg *g) {
     cudaStreamSynchronize(g->stream);
     drop_cache(g);
+    release_plan(g);
+    if (g->gp.own_stream) {
+        cudaStreamSynchronize(g->gp.own_stream);
+        cudaStreamDestroy(g->gp.own_stream);
+    }
     DevBuf *all[] = {&g->rp, &g->col, &g->prp, &g->pcol, &g->vgraph, &g->vbase, &g->entry, &g->exitv,
                      &g->tbl_base, &g->dist, &g->pred, &g->pre_len, &g->suf_len, &g->pre_off, &g->suf_off,
                      &g->pre_seq, &g->suf_seq, &g->tfl[0], &g->tfl[1], &g->tvis[0], &g->tvis[1],
@@ -279,7 +317,8 @@ int new_cfg(void *stream, tpg_cfg **out) {
         cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess ||
         cudaHostAlloc((void **)&g->h_small, 4096, cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreate(&g->ev[0]) || cudaEventCreate(&g->ev[1]) || cudaEventCreate(&g->ev[2]) ||
-        cudaEventCreate(&g->ev[3]) || cudaEventCreate(&g->ev[4]) || cudaEventCreate(&g->ev[5])) {
+        cudaEventCreate(&g->ev[3]) || cudaEventCreate(&g->ev[4]) || cudaEventCreate(&g->ev[5]) ||
+        cudaEventCreate(&g->ev[6]) || cudaEventCreate(&g->ev[7])) {
         cudaGetLastError();
         delete g;
         return TPG_ECUDA;
@@ -736,6 +775,7 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = TPG_ECUDA; break; }
         TV = h[0];
         R = h[1];
+        g->last_tv0 = TV;
         if (((int *)(h + 2))[0] & ERR_UNREACH) { rc = TPG_EUNREACH; break; }
         tp_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
         if (!tp_vert) { rc = TPG_ENOMEM; break; }
@@ -843,6 +883,174 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
     *oTV = FTV;
     g->stats.test_paths = T;
     g->stats.tp_vertices = FTV;
+    return TPG_OK;
+}
+
+// Size and allocate the plan, then capture it (stream capture) into one graph.
+int capture_plan(tpg_cfg *g) {
+    auto &p = g->gp;
+    release_plan(g);
+    if (!p.own_stream && !g->stream) {
+        if (cudaStreamCreateWithFlags(&p.own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return TPG_ECUDA;
+        }
+    }
+    cudaStream_t s = g->stream ? g->stream : p.own_stream;
+    // capacities: explicit ones win, otherwise the exact sizes of the last run
+    const bool have_run = g->pp_valid && g->stats.simple_paths > 0;
+    p.seg_cap = std::max<long long>(have_run ? g->stats.simple_paths : g->node_cap, g->N);
+    p.lvl_cap = std::max<long long>(have_run ? g->stats.peak_level_nodes : g->lvl_cap, g->N);
+    p.pp_cap = std::max<long long>(have_run ? g->stats.prime_paths : g->pp_cap, 1);
+    p.P_cap = std::max<long long>(g->out_cap[0] ? g->out_cap[0] : g->stats.prime_paths, 1);
+    p.V_cap = std::max<long long>(g->out_cap[1] ? g->out_cap[1] : g->stats.pp_vertices, 1);
+    p.TV0_cap = std::max<long long>(g->out_cap[2] ? g->out_cap[2] : g->last_tv0, 1);
+    p.TV_cap = std::max<long long>(g->out_cap[3] ? g->out_cap[3] : g->stats.tp_vertices, 1);
+    if (g->out_cap[0] == 0 && !have_run) return TPG_EINVAL;  // nothing to size from
+    p.pp_cap = std::max(p.pp_cap, p.P_cap);
+    p.status_cap = p.seg_cap / ENUM_MIN_TILE + 2LL * g->max_levels + 64;
+    const long long Pc = p.P_cap;
+    const int W = g->W;
+    RC(ensure(g, p.seg, sizeof(int2) * p.seg_cap));
+    RC(ensure(g, p.ppseg, sizeof(int) * p.pp_cap));
+    for (int b = 0; b < 2; ++b) {
+        RC(ensure(g, p.tfl[b], sizeof(int2) * p.lvl_cap));
+        RC(ensure(g, p.tvis[b], sizeof(unsigned) * (size_t)W * p.lvl_cap));
+        RC(ensure(g, p.keys[b], sizeof(int) * Pc));
+        RC(ensure(g, p.refs[b], sizeof(long long) * Pc));
+        RC(ensure(g, p.perm[b], sizeof(long long) * Pc));
+    }
+    RC(ensure(g, p.status, sizeof(unsigned long long) * p.status_cap));
+    RC(ensure(g, p.lvl_pp_off, sizeof(long long) * (g->max_levels + 1)));
+    RC(ensure(g, p.len, sizeof(long long) * Pc));
+    RC(ensure(g, p.scan_tmp, sizeof(long long) * gm_scan_tmp_elems(Pc + 1)));
+    RC(ensure(g, p.pp_graph, sizeof(int) * Pc));
+    RC(ensure(g, p.tp_len, sizeof(long long) * Pc));
+    RC(ensure(g, p.run_start, sizeof(int) * Pc));
+    RC(ensure(g, p.run_rank, sizeof(long long) * (Pc + 1)));
+    RC(ensure(g, p.tp_graph0, sizeof(int) * Pc));
+    RC(ensure(g, p.run_base, sizeof(long long) * g->G));
+    RC(ensure(g, p.nruns, sizeof(long long) * g->G));
+    RC(ensure(g, p.bounds0, sizeof(long long) * (Pc + 1)));
+    RC(ensure(g, p.tp_off0, sizeof(long long) * (Pc + 1)));
+    RC(ensure(g, p.tp_vert0, sizeof(int) * p.TV0_cap));
+    RC(ensure(g, p.keep, sizeof(int) * Pc));
+    RC(ensure(g, p.keep_off, sizeof(long long) * (Pc + 1)));
+    RC(ensure(g, p.keep_rank, sizeof(long long) * (Pc + 1)));
+    RC(ensure(g, p.tp_graph, sizeof(int) * Pc));
+    RC(ensure(g, p.counts, sizeof(GmCounts)));
+    RC(alloc_fixed_workspace(g));
+    p.pp_off = block_new(g->fns, sizeof(long long) * (Pc + 1), s);
+    p.pp_vert = block_new(g->fns, sizeof(int) * p.V_cap, s);
+    p.pp_gptr = block_new(g->fns, sizeof(long long) * (g->G + 1), s);
+    p.tp_off = block_new(g->fns, sizeof(long long) * (Pc + 1), s);
+    p.tp_vert = block_new(g->fns, sizeof(int) * p.TV_cap, s);
+    p.tp_gptr = block_new(g->fns, sizeof(long long) * (g->G + 1), s);
+    if (!p.pp_off || !p.pp_vert || !p.pp_gptr || !p.tp_off || !p.tp_vert || !p.tp_gptr) return TPG_ENOMEM;
+    if (!enum_shape_supported(g->W, g->shape)) g->shape = default_enum_shape(g->W);
+
+    EnumArgs a{};
+    a.g = g->gd;
+    a.seg = p.seg.as<int2>();
+    a.seg_cap = p.seg_cap;
+    a.next_nodes = nullptr;
+    a.pp_seg = p.ppseg.as<int>();
+    a.pp_seg_cap = p.pp_cap;
+    a.tfl[0] = p.tfl[0].as<int2>();
+    a.tfl[1] = p.tfl[1].as<int2>();
+    a.tvis[0] = p.tvis[0].as<unsigned>();
+    a.tvis[1] = p.tvis[1].as<unsigned>();
+    a.lvl_cap = p.lvl_cap;
+    a.levels = g->levels.as<LevelRec>();
+    a.max_levels = g->max_levels;
+    a.start_level = 1;
+    a.seed_level1 = 1;
+    a.status = p.status.as<unsigned long long>();
+    a.status_cap = p.status_cap;
+    a.tile_ctr = g->tile_ctr.as<int>();
+    a.err = g->ctl.as<int>();
+    a.stop_level = g->ctl.as<int>() + 1;
+    a.bar = (unsigned *)(g->ctl.as<char>() + 64);
+
+    GmArgs m{};
+    m.g = g->gd;
+    m.levels = g->levels.as<LevelRec>();
+    m.max_levels = g->max_levels;
+    m.enum_err = g->ctl.as<int>();
+    m.P_cap = Pc;
+    m.V_cap = p.V_cap;
+    m.TV0_cap = p.TV0_cap;
+    m.TV_cap = p.TV_cap;
+    m.num_sms = g->num_sms;
+    m.bar = (unsigned *)(g->ctl.as<char>() + 128);
+    m.tp_rounds = gm_tp_rounds(g->maxn);
+    m.lvl_pp_off = p.lvl_pp_off.as<long long>();
+    for (int b = 0; b < 2; ++b) {
+        m.keys[b] = p.keys[b].as<int>();
+        m.refs[b] = p.refs[b].as<long long>();
+        m.perm[b] = p.perm[b].as<long long>();
+    }
+    m.len = p.len.as<long long>();
+    m.scan_tmp = p.scan_tmp.as<long long>();
+    m.pp_off = (long long *)p.pp_off->p;
+    m.pp_vert = (int *)p.pp_vert->p;
+    m.pp_graph = p.pp_graph.as<int>();
+    m.pp_gptr = (long long *)p.pp_gptr->p;
+    m.tp_len = p.tp_len.as<long long>();
+    m.run_start = p.run_start.as<int>();
+    m.run_rank = p.run_rank.as<long long>();
+    m.tp_graph0 = p.tp_graph0.as<int>();
+    m.run_base = p.run_base.as<long long>();
+    m.nruns = p.nruns.as<long long>();
+    m.bounds0 = p.bounds0.as<long long>();
+    m.tp_off0 = p.tp_off0.as<long long>();
+    m.tp_vert0 = p.tp_vert0.as<int>();
+    m.keep = p.keep.as<int>();
+    m.keep_off = p.keep_off.as<long long>();
+    m.keep_rank = p.keep_rank.as<long long>();
+    m.tp_off = (long long *)p.tp_off->p;
+    m.tp_vert = (int *)p.tp_vert->p;
+    m.tp_graph = p.tp_graph.as<int>();
+    m.tp_gptr = (long long *)p.tp_gptr->p;
+    m.counts = p.counts.as<GmCounts>();
+    CK(cudaStreamSynchronize(s));
+
+    cudaGraph_t graph = nullptr;
+    const long long launches0 = g_kernel_launches.load();
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int grid = 0;
+    do {
+        if ((e = cudaMemsetAsync(g->levels.p, 0, sizeof(LevelRec) * g->max_levels, s))) break;
+        if ((e = cudaMemsetAsync(p.status.p, 0, sizeof(unsigned long long) * p.status_cap, s))) break;
+        if ((e = cudaMemsetAsync(g->tile_ctr.p, 0, sizeof(int) * g->max_levels, s))) break;
+        if ((e = cudaMemsetAsync(g->ctl.p, 0, 256, s))) break;
+        if ((e = cudaMemsetAsync(p.counts.p, 0, sizeof(GmCounts), s))) break;
+        if ((e = launch_enumerate(a, g->shape, g->num_sms, s, &grid))) break;
+        if ((e = gm_enqueue_pp(m, s))) break;
+        if ((e = gm_enqueue_tp(m, s))) break;
+        if ((e = cudaMemcpyAsync(g->h_small + 512, p.counts.p, sizeof(GmCounts), cudaMemcpyDeviceToHost, s))) break;
+        e = cudaMemcpyAsync(g->h_small + 600, g->ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    } while (false);
+    cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    p.kernels_per_replay = g_kernel_launches.load() - launches0;
+    g_kernel_launches.fetch_sub(p.kernels_per_replay);  // counted when replayed
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return TPG_ECUDA;
+    }
+    e = cudaGraphInstantiate(&p.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p.exec = nullptr;
+        return TPG_ECUDA;
+    }
+    g->stats.enumerate_grid = grid;
+    g->stats.tile_block = g->shape.block;
+    g->stats.tile_items = g->shape.items;
+    p.ready = true;
     return TPG_OK;
 }
 
@@ -1082,6 +1290,85 @@ int tpg_test_paths(tpg_cfg *g, tpg_paths **out) {
     return rc;
 }
 
+int tpg_set_output_capacity(tpg_cfg *g, int64_t prime_paths, int64_t pp_vertices, int64_t tp_vertices_raw,
+                            int64_t tp_vertices) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (prime_paths < 0 || pp_vertices < 0 || tp_vertices_raw < 0 || tp_vertices < 0) return TPG_EINVAL;
+    g->out_cap[0] = prime_paths;
+    g->out_cap[1] = pp_vertices;
+    g->out_cap[2] = tp_vertices_raw;
+    g->out_cap[3] = tp_vertices;
+    return TPG_OK;
+}
+
+int tpg_graph_capture(tpg_cfg *g) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (!g->pp_valid && g->out_cap[0] == 0) {
+        // size from one exact run of the host-driven path
+        RC(run_prime_paths(g));
+        Block *o = nullptr, *v = nullptr, *gp = nullptr;
+        long long T = 0, TV = 0;
+        RC(run_test_paths(g, &o, &v, &gp, &T, &TV));
+        block_unref(o);
+        block_unref(v);
+        block_unref(gp);
+    }
+    return capture_plan(g);
+}
+
+int tpg_graph_launch(tpg_cfg *g, tpg_paths **pp, tpg_paths **tp) {
+    if (!pp || !tp) return TPG_EINVAL;
+    *pp = nullptr;
+    *tp = nullptr;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    auto &p = g->gp;
+    if (!p.ready) RC(tpg_graph_capture(g));
+    cudaStream_t s = g->stream ? g->stream : p.own_stream;
+    CK(cudaEventRecord(g->ev[6], s));
+    CK(cudaGraphLaunch(p.exec, s));
+    g_kernel_launches.fetch_add(p.kernels_per_replay);
+    CK(cudaEventRecord(g->ev[7], s));
+    CK(cudaStreamSynchronize(s));
+    cudaEventElapsedTime(&g->stats.t_graph_ms, g->ev[6], g->ev[7]);
+    g->stats.graph_launches += 1;
+    const GmCounts c = *(const GmCounts *)(g->h_small + 512);
+    g->stats.graph_flags = c.flags;
+    g->stats.graph_enum_error = g->h_small[600];
+    if (c.flags & GM_UNREACH) return TPG_EUNREACH;
+    if (c.flags & GM_TIMEOUT) return TPG_ETIMEOUT;
+    if (c.flags) {
+        // a capacity was too small: exact host-driven path, and re-capture next time
+        g->stats.graph_fallbacks += 1;
+        p.ready = false;
+        drop_cache(g);
+        RC(run_prime_paths(g));
+        RC(make_result(g, g->pp_off, g->pp_vert, g->pp_gptr, g->P, g->V, pp));
+        Block *o = nullptr, *v = nullptr, *gp = nullptr;
+        long long T = 0, TV = 0;
+        int rc = run_test_paths(g, &o, &v, &gp, &T, &TV);
+        if (rc == TPG_OK) rc = make_result(g, o, v, gp, T, TV, tp);
+        block_unref(o);
+        block_unref(v);
+        block_unref(gp);
+        if (rc != TPG_OK) {
+            tpg_free(*pp);
+            *pp = nullptr;
+        }
+        return rc;
+    }
+    g->stats.prime_paths = c.P;
+    g->stats.pp_vertices = c.V;
+    g->stats.test_paths = c.T;
+    g->stats.tp_vertices = c.TV;
+    RC(make_result(g, p.pp_off, p.pp_vert, p.pp_gptr, c.P, c.V, pp));
+    const int rc = make_result(g, p.tp_off, p.tp_vert, p.tp_gptr, c.T, c.TV, tp);
+    if (rc != TPG_OK) {
+        tpg_free(*pp);
+        *pp = nullptr;
+    }
+    return rc;
+}
+
 void tpg_free(void *handle) {
     if (!handle) return;
     const uint32_t magic = *(const uint32_t *)handle;
@@ -1104,6 +1391,7 @@ int tpg_set_stream(tpg_cfg *g, void *stream) {
         cudaGetLastError();
         return TPG_ECUDA;
     }
+    if (g->stream != (cudaStream_t)stream) g->gp.ready = false;  // a capture is tied to its stream
     g->stream = (cudaStream_t)stream;
     return TPG_OK;
 }

@@ -71,6 +71,61 @@ cudaError_t pp_materialize(const long long *refs, const int *single_refs, int si
                            int *out_vertices, int *out_graph, cudaStream_t s);
 cudaError_t graph_ptr_from_ids(const int *ids, long long n, int G, long long *ptr, cudaStream_t s);
 
+// graphmode.cu: the device-driven pipeline captured into a CUDA graph
+enum : int {
+    GM_ENUM_FAILED = 1,  // the frontier launch stopped (capacity) or failed
+    GM_OVF_PP = 2,       // more PPs than P_cap
+    GM_OVF_PPV = 4,      // more PP vertices than V_cap
+    GM_UNREACH = 8,      // a PP cannot be toured
+    GM_TIMEOUT = ERR_TIMEOUT,  // a bounded grid barrier ran out (the barrier ORs this bit)
+    GM_OVF_TPV0 = 32,    // more TP vertices (before dedup) than TV0_cap
+    GM_OVF_TPV = 64,     // more TP vertices (after dedup) than TV_cap
+};
+static_assert(GM_TIMEOUT == 16, "flag bits must stay distinct");
+struct GmCounts {
+    long long P, V, TV0, R, T, TV;
+    int flags;
+    int pp_buf;  // which keys/refs buffer holds the ordered PPs
+};
+struct GmArgs {
+    GraphDev g;
+    const LevelRec *levels;
+    int max_levels;
+    const int *enum_err;
+    long long P_cap, V_cap, TV0_cap, TV_cap;
+    int num_sms, tp_rounds;
+    unsigned *bar;          // grid barrier of the ordering kernel (zeroed)
+    long long *lvl_pp_off;  // [max_levels+1]
+    int *keys[2];
+    long long *refs[2];
+    long long *len;         // [P_cap]
+    long long *scan_tmp;    // gm_scan_tmp_elems(P_cap)
+    long long *pp_off;      // [P_cap+1]
+    int *pp_vert;           // [V_cap]
+    int *pp_graph;          // [P_cap] (batches)
+    long long *pp_gptr;     // [G+1]
+    long long *tp_len;      // [P_cap]
+    int *run_start;         // [P_cap]
+    long long *run_rank;    // [P_cap+1]
+    int *tp_graph0;         // [P_cap]
+    long long *run_base, *nruns;  // [G]
+    long long *bounds0;     // [P_cap+1]
+    long long *tp_off0;     // [P_cap+1]
+    int *tp_vert0;          // [TV0_cap]
+    long long *perm[2];     // [P_cap]
+    int *keep;              // [P_cap]
+    long long *keep_off, *keep_rank;  // [P_cap+1]
+    long long *tp_off;      // [P_cap+1]
+    int *tp_vert;           // [TV_cap]
+    int *tp_graph;          // [P_cap]
+    long long *tp_gptr;     // [G+1]
+    GmCounts *counts;
+};
+int gm_tp_rounds(int maxn);
+size_t gm_scan_tmp_elems(long long n_cap);
+cudaError_t gm_enqueue_pp(const GmArgs &a, cudaStream_t s);
+cudaError_t gm_enqueue_tp(const GmArgs &a, cudaStream_t s);
+
 // preprocess.cu
 cudaError_t build_union_csr(const int *unused, const long long *rp_base_dev,
                             const long long *arc_base_dev, const int *rp_cat, const int *col_cat,

@@ -11,6 +11,7 @@
 // with that level's own PPs by key.  Keys of the two inputs never tie.
 #include "common.cuh"
 #include "kernels.h"
+#include "paths_dev.cuh"
 
 namespace tpg {
 
@@ -121,56 +122,14 @@ cudaError_t pp_offsets_single_level(long long *off, long long n, int level, cuda
     return cudaGetLastError();
 }
 
-// One warp materialises 32 consecutive PPs: each lane walks its path's parent
-// links from the last vertex back to the first, writing into a per-warp
-// shared-memory window; the warp then stores the window contiguously.  If
-// the window does not fit, lanes store directly.
 constexpr int MAT_WARPS = 8;
-constexpr int MAT_BUF = 2048;  // int32 per warp (8 KB)
 
 __global__ void __launch_bounds__(MAT_WARPS * 32)
     pp_materialize_kernel(const long long *refs, const int *single_refs, int single_level, long long n,
                           const long long *offsets, const LevelRec *levels, GraphDev g, int *out,
                           int *out_graph) {
     __shared__ int buf[MAT_WARPS][MAT_BUF];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const long long nwarps = (long long)gridDim.x * MAT_WARPS;
-    for (long long w0 = (blockIdx.x * (long long)MAT_WARPS + wid) * 32; w0 < n; w0 += nwarps * 32) {
-        const long long idx = w0 + lane;
-        const bool valid = idx < n;
-        int level = 0, rel = 0;
-        if (valid) {
-            if (refs) {
-                const long long r = refs[idx];
-                level = (int)(r >> 32);
-                rel = (int)(r & 0xffffffffll);
-            } else {
-                level = single_level;
-                rel = single_refs[idx];
-            }
-        }
-        const long long w_end_idx = (w0 + 32 < n) ? w0 + 32 : n;
-        const long long start = offsets[w0];
-        const long long span = offsets[w_end_idx] - start;
-        const long long off = valid ? offsets[idx] : 0;
-        const bool staged = span <= MAT_BUF;
-        int node = rel, root = 0;
-        for (int j = level; j >= 1; --j) {
-            const int2 rec = levels[j].nodes[node];
-            const int v = rec.x;
-            const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
-            if (staged) buf[wid][off - start + (j - 1)] = loc;
-            else out[off + (j - 1)] = loc;
-            root = v;
-            node = rec.y;
-        }
-        if (valid && out_graph) out_graph[idx] = g.vgraph ? g.vgraph[root] : 0;
-        if (staged) {
-            __syncwarp();
-            for (long long t = lane; t < span; t += 32) out[start + t] = buf[wid][t];
-            __syncwarp();
-        }
-    }
+    materialize_warps(refs, single_refs, single_level, n, offsets, levels, g, out, out_graph, buf);
 }
 
 cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,

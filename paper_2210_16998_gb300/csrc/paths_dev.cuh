@@ -1,0 +1,78 @@
+// Device helpers shared by the host-driven and the graph-captured pipelines.
+#pragma once
+#include "common.cuh"
+
+namespace tpg {
+
+// (graph, sequence) order: graph id first, then lexicographic on the vertex
+// sequences, a proper prefix first.
+__device__ __forceinline__ int tp_cmp(long long a, long long b, const long long *off, const int *vert,
+                                      const int *graph) {
+    const int ga = graph[a], gb = graph[b];
+    if (ga != gb) return ga < gb ? -1 : 1;
+    const long long a0 = off[a], la = off[a + 1] - a0;
+    const long long b0 = off[b], lb = off[b + 1] - b0;
+    const long long l = la < lb ? la : lb;
+    for (long long t = 0; t < l; ++t) {
+        const int x = vert[a0 + t], y = vert[b0 + t];
+        if (x != y) return x < y ? -1 : 1;
+    }
+    if (la == lb) return 0;
+    return la < lb ? -1 : 1;
+}
+
+// Materialise PPs [0, n): one warp handles 32 consecutive PPs; each lane
+// walks its path's parent links from the last vertex back to the first,
+// writing into a per-warp shared-memory window that the warp then stores
+// contiguously (lanes store directly when the window does not fit).  A PP is
+// refs[i] = (level << 32 | index in level), or, with refs == nullptr, index
+// single_refs[i] in level single_level.  out_graph (optional) receives the
+// graph id of each PP.
+constexpr int MAT_BUF = 2048;  // int32 per warp (8 KB)
+
+template <int NWARPS>
+__device__ __forceinline__ void materialize_warps(const long long *refs, const int *single_refs, int single_level,
+                                                  long long n, const long long *offsets, const LevelRec *levels,
+                                                  const GraphDev &g, int *out, int *out_graph,
+                                                  int (&buf)[NWARPS][MAT_BUF]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long nwarps = (long long)gridDim.x * NWARPS;
+    for (long long w0 = (blockIdx.x * (long long)NWARPS + wid) * 32; w0 < n; w0 += nwarps * 32) {
+        const long long idx = w0 + lane;
+        const bool valid = idx < n;
+        int level = 0, rel = 0;
+        if (valid) {
+            if (refs) {
+                const long long r = refs[idx];
+                level = (int)(r >> 32);
+                rel = (int)(r & 0xffffffffll);
+            } else {
+                level = single_level;
+                rel = single_refs[idx];
+            }
+        }
+        const long long w_end_idx = (w0 + 32 < n) ? w0 + 32 : n;
+        const long long start = offsets[w0];
+        const long long span = offsets[w_end_idx] - start;
+        const long long off = valid ? offsets[idx] : 0;
+        const bool staged = span <= MAT_BUF;
+        int node = rel, root = 0;
+        for (int j = level; j >= 1; --j) {
+            const int2 rec = levels[j].nodes[node];
+            const int v = rec.x;
+            const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
+            if (staged) buf[wid][off - start + (j - 1)] = loc;
+            else out[off + (j - 1)] = loc;
+            root = v;
+            node = rec.y;
+        }
+        if (valid && out_graph) out_graph[idx] = g.vgraph ? g.vgraph[root] : 0;
+        if (staged) {
+            __syncwarp();
+            for (long long t = lane; t < span; t += 32) out[start + t] = buf[wid][t];
+            __syncwarp();
+        }
+    }
+}
+
+}  // namespace tpg

@@ -12,6 +12,7 @@
 // are dropped after the final round.
 #include "common.cuh"
 #include "kernels.h"
+#include "paths_dev.cuh"
 
 namespace tpg {
 
@@ -115,22 +116,6 @@ cudaError_t tp_iota(long long *perm, long long P, cudaStream_t s) {
     iota_kernel<<<grid_for(P), 256, 0, s>>>(perm, P);
     note_launch();
     return cudaGetLastError();
-}
-
-// (graph, sequence) order: graph id first, then lexicographic, proper prefix first
-__device__ __forceinline__ int tp_cmp(long long a, long long b, const long long *off, const int *vert,
-                                      const int *graph) {
-    const int ga = graph[a], gb = graph[b];
-    if (ga != gb) return ga < gb ? -1 : 1;
-    const long long a0 = off[a], la = off[a + 1] - a0;
-    const long long b0 = off[b], lb = off[b + 1] - b0;
-    const long long l = la < lb ? la : lb;
-    for (long long t = 0; t < l; ++t) {
-        const int x = vert[a0 + t], y = vert[b0 + t];
-        if (x != y) return x < y ? -1 : 1;
-    }
-    if (la == lb) return 0;
-    return la < lb ? -1 : 1;
 }
 
 constexpr int TPM_ITEMS = 4;

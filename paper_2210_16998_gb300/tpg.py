@@ -77,6 +77,11 @@ class _Stats(ctypes.Structure):
         ("enumerate_grid", ctypes.c_int32),
         ("tile_block", ctypes.c_int32),
         ("tile_items", ctypes.c_int32),
+        ("t_graph_ms", ctypes.c_float),
+        ("graph_launches", ctypes.c_int32),
+        ("graph_fallbacks", ctypes.c_int32),
+        ("graph_flags", ctypes.c_int32),
+        ("graph_enum_error", ctypes.c_int32),
     ]
 
 
@@ -126,6 +131,10 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_set_result_location.argtypes = [P, ctypes.c_int32]
         lib.tpg_set_tile_shape.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
         lib.tpg_set_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        lib.tpg_set_output_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        lib.tpg_graph_capture.argtypes = [P]
+        lib.tpg_graph_launch.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths)),
+                                         ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_set_allocator.argtypes = [_ALLOC_FN, _RELEASE_FN, P]
         lib.tpg_get_stats.argtypes = [P, ctypes.POINTER(_Stats)]
         lib.tpg_strerror.argtypes = [ctypes.c_int]
@@ -138,7 +147,8 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_prime_paths_noalloc.restype = ctypes.c_int
         for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
                      "tpg_test_paths", "tpg_set_stream", "tpg_set_result_location", "tpg_set_allocator",
-                     "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_capacity"):
+                     "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_capacity", "tpg_set_output_capacity",
+                     "tpg_graph_capture", "tpg_graph_launch"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     if install_torch_allocator:
@@ -376,6 +386,23 @@ def tpg_set_tile_shape(cfg: Cfg, block: int, items: int):
 def tpg_set_capacity(cfg: Cfg, nodes: int, level_nodes: int, prime_paths: int):
     _check(load_library().tpg_set_capacity(cfg.handle, int(nodes), int(level_nodes), int(prime_paths)),
            "tpg_set_capacity")
+
+
+def tpg_set_output_capacity(cfg: Cfg, prime_paths: int, pp_vertices: int, tp_vertices_raw: int, tp_vertices: int):
+    _check(load_library().tpg_set_output_capacity(cfg.handle, int(prime_paths), int(pp_vertices),
+                                                  int(tp_vertices_raw), int(tp_vertices)), "tpg_set_output_capacity")
+
+
+def tpg_graph_capture(cfg: Cfg):
+    _check(load_library().tpg_graph_capture(cfg.handle), "tpg_graph_capture")
+
+
+def tpg_graph_launch(cfg: Cfg):
+    """Replay the captured hot path; returns (prime paths, test paths)."""
+    pp = ctypes.POINTER(_Paths)()
+    tp = ctypes.POINTER(_Paths)()
+    _check(load_library().tpg_graph_launch(cfg.handle, ctypes.byref(pp), ctypes.byref(tp)), "tpg_graph_launch")
+    return Paths(pp), Paths(tp)
 
 
 def tpg_set_allocator(alloc=None, release=None):
