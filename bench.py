@@ -339,7 +339,10 @@ def run_batch(args, rank, world, local_rank):
     tpg.load_library(build=True)
     cfgs = cfggen.batch_cfgs(4096)
     ns, rp, col, ent, ext = cfggen.concat_batch(cfgs)
-    shape, tuned = autotune.tune()
+    if args.tile:
+        shape, tuned = tuple(int(x) for x in args.tile.split(",")), {"fixed": args.tile}
+    else:
+        shape, tuned = autotune.tune()
     h = tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE)
     tpg.tpg_set_tile_shape(h, *shape)
     # host-driven batched run: exact sizes for the capture, and its own timing
@@ -391,31 +394,36 @@ def run_batch(args, rank, world, local_rank):
     h.close()
 
     # per-graph plain launches over the same 4096 graphs (inputs resident)
-    dev_inputs = [(torch.as_tensor(c.row_ptr, device="cuda"), torch.as_tensor(c.col, device="cuda")) for c in cfgs]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    plain_pp = 0
-    for c, (r_, c_) in zip(cfgs, dev_inputs):
-        hh = tpg.tpg_load_cfg_device(c.n, c.m, r_, c_, c.entry, c.exit)
-        a = tpg.tpg_prime_paths(hh)
-        b = tpg.tpg_test_paths(hh)
-        plain_pp += a.num_paths
-        a.free()
-        b.free()
-        hh.close()
-    torch.cuda.synchronize()
-    plain_s = time.perf_counter() - t0
-    assert plain_pp == P
+    plain_s = float("nan")
+    if not args.no_plain:
+        dev_inputs = [(torch.as_tensor(c.row_ptr, device="cuda"), torch.as_tensor(c.col, device="cuda"))
+                      for c in cfgs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plain_pp = 0
+        for c, (r_, c_) in zip(cfgs, dev_inputs):
+            hh = tpg.tpg_load_cfg_device(c.n, c.m, r_, c_, c.entry, c.exit)
+            a = tpg.tpg_prime_paths(hh)
+            b = tpg.tpg_test_paths(hh)
+            plain_pp += a.num_paths
+            a.free()
+            b.free()
+            hh.close()
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
+        assert plain_pp == P
 
     # e2e through the C ABI with host buffers
     t0 = time.perf_counter()
+    bo = 0
     he = tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_HOST)
     tpg.tpg_set_tile_shape(he, *shape)
-    a = tpg.tpg_prime_paths(he)
-    b = tpg.tpg_test_paths(he)
-    bo = sum(x.nbytes for r in (a, b) for x in (r.graph_path_ptr, r.offsets, r.vertices))
-    a.free()
-    b.free()
+    if not args.no_e2e:
+        a = tpg.tpg_prime_paths(he)
+        b = tpg.tpg_test_paths(he)
+        bo = sum(x.nbytes for r in (a, b) for x in (r.graph_path_ptr, r.offsets, r.vertices))
+        a.free()
+        b.free()
     he.close()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -439,8 +447,12 @@ def run_batch(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "compare": {"host_driven_batched_pp_per_s": P / (min(host_ms) / 1000.0),
                     "host_driven_batched_ms": min(host_ms),
+                    "host_driven_phases_ms": {"enumerate": st_host["t_enumerate_ms"],
+                                              "order_materialise": st_host["t_order_ms"],
+                                              "test_paths": st_host["t_test_paths_ms"]},
                     "per_graph_plain_pp_per_s": P / plain_s, "per_graph_plain_s": plain_s},
-        "e2e": {"value": P / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": int(bo)},
+        "e2e": {"value": (P / e2e_s) if not args.no_e2e else None, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": int(bo)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "enumerate_kernel", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
@@ -503,6 +515,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k", type=int, default=K_DIAMONDS, help="diamonds in the chain (22 = the benchmark workload)")
     ap.add_argument("--workload", choices=["chain", "batch"], default="chain")
+    ap.add_argument("--no-plain", action="store_true", help="batch: skip the per-graph plain launches")
+    ap.add_argument("--tile", default="", help="batch: fixed tile shape 'block,items' instead of the autotuner")
     args = ap.parse_args()
     K_DIAMONDS = args.k
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -203,7 +203,8 @@ struct tpg_cfg {
         cudaStream_t own_stream = nullptr;
         DevBuf seg, ppseg, tfl[2], tvis[2], status;
         DevBuf lvl_pp_off, keys[2], refs[2], len, scan_tmp, pp_graph, tp_len, run_start, run_rank, tp_graph0,
-            run_base, nruns, bounds0, tp_off0, tp_vert0, perm[2], keep, keep_off, keep_rank, tp_graph, counts;
+            run_base, nruns, bounds0, tp_off0, tp_vert0, perm[2], keep, keep_off, keep_rank, tp_graph, counts,
+            key_off, key;
         Block *pp_off = nullptr, *pp_vert = nullptr, *pp_gptr = nullptr;
         Block *tp_off = nullptr, *tp_vert = nullptr, *tp_gptr = nullptr;
         long long seg_cap = 0, pp_cap = 0, lvl_cap = 0, status_cap = 0;
@@ -253,7 +254,7 @@ void release_plan(tpg_cfg *g) {
                      &p.keys[0], &p.keys[1], &p.refs[0], &p.refs[1], &p.len, &p.scan_tmp, &p.pp_graph, &p.tp_len,
                      &p.run_start, &p.run_rank, &p.tp_graph0, &p.run_base, &p.nruns, &p.bounds0, &p.tp_off0,
                      &p.tp_vert0, &p.perm[0], &p.perm[1], &p.keep, &p.keep_off, &p.keep_rank, &p.tp_graph,
-                     &p.counts};
+                     &p.counts, &p.key_off, &p.key};
     for (DevBuf *b : all) release(g, *b);
     Block *bl[] = {p.pp_off, p.pp_vert, p.pp_gptr, p.tp_off, p.tp_vert, p.tp_gptr};
     for (Block *b : bl) block_unref(b);
@@ -616,7 +617,7 @@ int run_prime_paths(tpg_cfg *g) {
         const int k = pp_levels[0];
         const int *refs = g->h_levels[k].pp;
         CK(pp_offsets_single_level((long long *)off->p, P, k, s));
-        CK(pp_materialize(nullptr, refs, k, P, (const long long *)off->p, dlev, g->gd, (int *)vert->p,
+        CK(pp_materialize(nullptr, refs, k, P, (const long long *)off->p, dlev, g->max_levels, g->gd, (int *)vert->p,
                           pgraph ? (int *)pgraph->p : nullptr, s));
     } else {
         for (int b = 0; b < 2; ++b) {
@@ -636,9 +637,9 @@ int run_prime_paths(tpg_cfg *g) {
                 CK(order_init_run(lref, k, L.pp_count, g->s_keys[cur].as<int>(), g->s_refs[cur].as<long long>(), s));
                 na = L.pp_count;
             } else {
-                CK(order_ascend(g->s_keys[cur].as<int>(), na, dlev, cur_level, k, s));
                 CK(order_merge(g->s_keys[cur].as<int>(), g->s_refs[cur].as<long long>(), na, lref, k, L.pp_count,
-                               g->s_keys[cur ^ 1].as<int>(), g->s_refs[cur ^ 1].as<long long>(), s));
+                               g->s_keys[cur ^ 1].as<int>(), g->s_refs[cur ^ 1].as<long long>(), dlev, cur_level,
+                               s));
                 cur ^= 1;
                 na += L.pp_count;
             }
@@ -647,7 +648,7 @@ int run_prime_paths(tpg_cfg *g) {
         const long long *refs = g->s_refs[cur].as<long long>();
         CK(pp_lengths(refs, P, g->s_len.as<long long>(), s));
         CK(scan_i64(g->s_len.as<long long>(), (long long *)off->p, P, g->s_tmp.as<long long>(), s));
-        CK(pp_materialize(refs, nullptr, 0, P, (const long long *)off->p, dlev, g->gd, (int *)vert->p,
+        CK(pp_materialize(refs, nullptr, 0, P, (const long long *)off->p, dlev, g->max_levels, g->gd, (int *)vert->p,
                           pgraph ? (int *)pgraph->p : nullptr, s));
     }
     if (g->G > 1) {
@@ -939,6 +940,10 @@ int capture_plan(tpg_cfg *g) {
     RC(ensure(g, p.keep_rank, sizeof(long long) * (Pc + 1)));
     RC(ensure(g, p.tp_graph, sizeof(int) * Pc));
     RC(ensure(g, p.counts, sizeof(GmCounts)));
+    const int key_bits = g->maxn <= 255 ? 8 : 16;
+    const long long K_cap = p.TV0_cap / (64 / key_bits) + Pc + 1;
+    RC(ensure(g, p.key_off, sizeof(long long) * (Pc + 1)));
+    RC(ensure(g, p.key, sizeof(unsigned long long) * K_cap));
     RC(alloc_fixed_workspace(g));
     p.pp_off = block_new(g->fns, sizeof(long long) * (Pc + 1), s);
     p.pp_vert = block_new(g->fns, sizeof(int) * p.V_cap, s);
@@ -1005,6 +1010,10 @@ int capture_plan(tpg_cfg *g) {
     m.bounds0 = p.bounds0.as<long long>();
     m.tp_off0 = p.tp_off0.as<long long>();
     m.tp_vert0 = p.tp_vert0.as<int>();
+    m.key_off = p.key_off.as<long long>();
+    m.key = p.key.as<unsigned long long>();
+    m.K_cap = K_cap;
+    m.key_bits = key_bits;
     m.keep = p.keep.as<int>();
     m.keep_off = p.keep_off.as<long long>();
     m.keep_rank = p.keep_rank.as<long long>();
@@ -1337,9 +1346,11 @@ int tpg_graph_launch(tpg_cfg *g, tpg_paths **pp, tpg_paths **tp) {
     if (c.flags & GM_UNREACH) return TPG_EUNREACH;
     if (c.flags & GM_TIMEOUT) return TPG_ETIMEOUT;
     if (c.flags) {
-        // a capacity was too small: exact host-driven path, and re-capture next time
+        // a capacity was too small: exact host-driven path, and re-capture next
+        // time with the exact sizes that run measures
         g->stats.graph_fallbacks += 1;
         p.ready = false;
+        for (long long &oc : g->out_cap) oc = 0;
         drop_cache(g);
         RC(run_prime_paths(g));
         RC(make_result(g, g->pp_off, g->pp_vert, g->pp_gptr, g->P, g->V, pp));

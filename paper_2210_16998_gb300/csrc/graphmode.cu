@@ -23,7 +23,8 @@ namespace tpg {
 namespace {
 
 constexpr int GMB = 256;      // threads per block of the streaming kernels
-constexpr int GM_ITEMS = 4;   // outputs per thread of the merge kernels
+constexpr int GM_ITEMS = 4;   // outputs per thread of the PP merge
+constexpr int TPM_ITEMS = 16; // outputs per thread of the TP run merge
 constexpr int GM_SCAN_ITEMS = 8;
 constexpr long long GM_SCAN_TILE = (long long)GMB * GM_SCAN_ITEMS;
 
@@ -173,30 +174,34 @@ __global__ void __launch_bounds__(GMB) gm_order_kernel(GmArgs a) {
                 a.refs[cur][i] = ((long long)k << 32) | (unsigned)rl;
             }
         } else {
-            int *ka = a.keys[cur];
-            for (long long i = tid; i < na; i += nthr) {
-                int key = ka[i];
-                for (int j = cur_level; j > k; --j) key = a.levels[j].nodes[key].y;
-                ka[i] = key;
-            }
-            if (!grid_barrier(a.bar, &a.counts->flags)) { ok = false; break; }
+            // merge the accumulated run (keys at cur_level, lifted to level k
+            // on the fly) with level k's PPs
+            const int *ka = a.keys[cur];
             const long long *ra = a.refs[cur];
             int *kc = a.keys[cur ^ 1];
             long long *rc = a.refs[cur ^ 1];
             const long long total = na + nb;
+            const int up = cur_level;
+            auto lift = [&](long long i) {
+                int key = ka[i];
+                for (int j = up; j > k; --j) key = a.levels[j].nodes[key].y;
+                return key;
+            };
             for (long long d0 = tid * GM_ITEMS; d0 < total; d0 += nthr * GM_ITEMS) {
                 long long lo2 = d0 > nb ? d0 - nb : 0, hi2 = d0 < na ? d0 : na;
                 while (lo2 < hi2) {
                     const long long mid = (lo2 + hi2) >> 1;
-                    if (ka[mid] <= lref[d0 - mid - 1]) lo2 = mid + 1;
+                    if (lift(mid) <= lref[d0 - mid - 1]) lo2 = mid + 1;
                     else hi2 = mid;
                 }
                 long long i = lo2, j = d0 - lo2;
+                int ki = (i < na) ? lift(i) : 0;
                 for (int t = 0; t < GM_ITEMS && d0 + t < total; ++t) {
-                    if (i < na && (j >= nb || ka[i] <= lref[j])) {
-                        kc[d0 + t] = ka[i];
+                    if (i < na && (j >= nb || ki <= lref[j])) {
+                        kc[d0 + t] = ki;
                         rc[d0 + t] = ra[i];
                         ++i;
+                        if (i < na) ki = lift(i);
                     } else {
                         const int rl = lref[j];
                         kc[d0 + t] = rl;
@@ -225,9 +230,11 @@ constexpr int GM_MAT_WARPS = 8;
 
 __global__ void __launch_bounds__(GM_MAT_WARPS * 32) gm_materialize(GmArgs a) {
     __shared__ int sbuf[GM_MAT_WARPS][MAT_BUF];
+    __shared__ int2 *s_nodes[MAT_MAX_LV];
+    int2 *const *lv = cache_level_nodes(a.levels, a.max_levels, s_nodes);
     const long long P = gm_P(a);
     materialize_warps<GM_MAT_WARPS>(a.refs[a.counts->pp_buf], nullptr, 0, P, a.pp_off, a.levels, a.g, a.pp_vert,
-                                    a.g.G > 1 ? a.pp_graph : nullptr, sbuf);
+                                    a.g.G > 1 ? a.pp_graph : nullptr, sbuf, lv);
 }
 
 // graph_path_ptr from sorted graph ids (ids == nullptr: one graph)
@@ -257,6 +264,8 @@ __global__ void __launch_bounds__(GMB) gm_tp_len(GmArgs a) {
         if (pl == 0 || sl == 0) atomicOr(&a.counts->flags, GM_UNREACH);
         else len = (long long)(pl - 1) + (o1 - o0) + (sl - 1);
         a.tp_len[i] = len;
+        const int vpw = 64 / a.key_bits;
+        a.len[i] = (len + vpw - 1) / vpw;
         a.tp_graph0[i] = gid;
         int start = 1;
         if (i > 0) {
@@ -277,7 +286,7 @@ __global__ void gm_tp_check(GmArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         GmCounts *c = a.counts;
         c->TV0 = a.tp_off0[clampc(c->P, a.P_cap)];
-        if (c->TV0 > a.TV0_cap) atomicOr(&c->flags, GM_OVF_TPV0);
+        if (c->TV0 > a.TV0_cap || a.key_off[clampc(c->P, a.P_cap)] > a.K_cap) atomicOr(&c->flags, GM_OVF_TPV0);
         c->R = a.run_rank[clampc(c->P, a.P_cap)];
     }
 }
@@ -301,27 +310,48 @@ __global__ void __launch_bounds__(GMB) gm_bounds0(GmArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.bounds0[P ? a.counts->R : 0] = P;
 }
 
+// TP vertex at position p of TP i: prefix, PP, suffix
+struct TpParts {
+    const int *pre, *pp, *suf;
+    long long pl, plen;
+    __device__ __forceinline__ int at(long long p) const {
+        if (p < pl) return pre[p];
+        if (p < pl + plen) return pp[p - pl];
+        return suf[p - pl - plen];
+    }
+};
+
+constexpr int TP_LANES = 8;  // lanes per TP in the write and gather kernels
+
 __global__ void __launch_bounds__(GMB) gm_tp_write(GmArgs a) {
     const long long P = gm_P_tp(a);
     const GraphDev &g = a.g;
-    const int lane = threadIdx.x & 31;
-    const long long nw = (long long)gridDim.x * (GMB / 32);
-    for (long long i = blockIdx.x * (long long)(GMB / 32) + (threadIdx.x >> 5); i < P; i += nw) {
+    const int sub = threadIdx.x & (TP_LANES - 1);
+    const long long ngroups = (long long)gridDim.x * (GMB / TP_LANES);
+    const int bits = a.key_bits, vpw = 64 / bits;
+    for (long long i = blockIdx.x * (long long)(GMB / TP_LANES) + (threadIdx.x / TP_LANES); i < P; i += ngroups) {
         const long long o0 = a.pp_off[i], o1 = a.pp_off[i + 1];
         const int gid = g.G > 1 ? a.pp_graph[i] : 0;
         const int vb = g.vgraph ? g.vbase[gid] : 0;
         const int f = a.pp_vert[o0] + vb, l = a.pp_vert[o1 - 1] + vb;
-        const long long pl = g.pre_len[f] - 1, plen = o1 - o0;
-        const long long total = a.tp_off0[i + 1] - a.tp_off0[i];
-        const int *pre = g.pre_seq + g.pre_off[f];
-        const int *suf = g.suf_seq + g.suf_off[l] + 1;
-        int *dst = a.tp_vert0 + a.tp_off0[i];
-        for (long long p = lane; p < total; p += 32) {
-            int v;
-            if (p < pl) v = pre[p];
-            else if (p < pl + plen) v = a.pp_vert[o0 + (p - pl)];
-            else v = suf[p - pl - plen];
-            dst[p] = v;
+        TpParts t;
+        t.pl = g.pre_len[f] - 1;
+        t.plen = o1 - o0;
+        t.pre = g.pre_seq + g.pre_off[f];
+        t.pp = a.pp_vert + o0;
+        t.suf = g.suf_seq + g.suf_off[l] + 1;
+        const long long d0 = a.tp_off0[i], total = a.tp_off0[i + 1] - d0;
+        int *dst = a.tp_vert0 + d0;
+        for (long long p = sub; p < total; p += TP_LANES) dst[p] = t.at(p);
+        const long long k0 = a.key_off[i], nw = a.key_off[i + 1] - k0;
+        for (long long w = sub; w < nw; w += TP_LANES) {
+            unsigned long long word = 0;
+            for (int q = 0; q < vpw; ++q) {
+                const long long p = w * vpw + q;
+                const unsigned long long v = p < total ? (unsigned long long)(t.at(p) + 1) : 0ull;
+                word = (word << bits) | v;
+            }
+            a.key[k0 + w] = word;
         }
     }
 }
@@ -333,9 +363,9 @@ __global__ void __launch_bounds__(GMB) gm_tp_merge_round(GmArgs a, int r, int bu
     long long *pout = a.perm[buf ^ 1];
     const int G = a.g.G;
     const long long nthreads = (long long)gridDim.x * GMB;
-    for (long long d0 = (blockIdx.x * (long long)GMB + threadIdx.x) * GM_ITEMS; d0 < P; d0 += nthreads * GM_ITEMS) {
+    for (long long d0 = (blockIdx.x * (long long)GMB + threadIdx.x) * TPM_ITEMS; d0 < P; d0 += nthreads * TPM_ITEMS) {
         long long a_hi = 0, b_hi = -1, i = 0, j = 0;
-        for (int t = 0; t < GM_ITEMS; ++t) {
+        for (int t = 0; t < TPM_ITEMS; ++t) {
             const long long d = d0 + t;
             if (d >= P) break;
             if (d >= b_hi) {
@@ -351,7 +381,7 @@ __global__ void __launch_bounds__(GMB) gm_tp_merge_round(GmArgs a, int r, int bu
                 long long lo = diag > nb ? diag - nb : 0, hi = diag < na ? diag : na;
                 while (lo < hi) {
                     const long long mid = (lo + hi) >> 1;
-                    if (tp_cmp(pin[a_lo + mid], pin[a_hi + diag - mid - 1], a.tp_off0, a.tp_vert0, a.tp_graph0) <= 0)
+                    if (key_cmp(pin[a_lo + mid], pin[a_hi + diag - mid - 1], a.key_off, a.key, a.tp_graph0) <= 0)
                         lo = mid + 1;
                     else
                         hi = mid;
@@ -362,7 +392,7 @@ __global__ void __launch_bounds__(GMB) gm_tp_merge_round(GmArgs a, int r, int bu
             bool take_a;
             if (i >= a_hi) take_a = false;
             else if (j >= b_hi) take_a = true;
-            else take_a = tp_cmp(pin[i], pin[j], a.tp_off0, a.tp_vert0, a.tp_graph0) <= 0;
+            else take_a = key_cmp(pin[i], pin[j], a.key_off, a.key, a.tp_graph0) <= 0;
             pout[d] = take_a ? pin[i++] : pin[j++];
         }
     }
@@ -373,7 +403,7 @@ __global__ void __launch_bounds__(GMB) gm_tp_dedup(GmArgs a, int buf) {
     const long long *perm = a.perm[buf];
     for (long long i = blockIdx.x * (long long)GMB + threadIdx.x; i < P; i += (long long)gridDim.x * GMB) {
         const long long x = perm[i];
-        const int k = (i == 0) || tp_cmp(perm[i - 1], x, a.tp_off0, a.tp_vert0, a.tp_graph0) != 0;
+        const int k = (i == 0) || key_cmp(perm[i - 1], x, a.key_off, a.key, a.tp_graph0) != 0;
         a.keep[i] = k;
         a.tp_len[i] = k ? a.tp_off0[x + 1] - a.tp_off0[x] : 0;
     }
@@ -397,14 +427,14 @@ __device__ __forceinline__ long long gm_P_final(const GmArgs &a) {
 __global__ void __launch_bounds__(GMB) gm_tp_gather(GmArgs a, int buf) {
     const long long P = gm_P_final(a);
     const long long *perm = a.perm[buf];
-    const int lane = threadIdx.x & 31;
-    const long long nw = (long long)gridDim.x * (GMB / 32);
-    for (long long i = blockIdx.x * (long long)(GMB / 32) + (threadIdx.x >> 5); i < P; i += nw) {
+    const int sub = threadIdx.x & (TP_LANES - 1);
+    const long long ngroups = (long long)gridDim.x * (GMB / TP_LANES);
+    for (long long i = blockIdx.x * (long long)(GMB / TP_LANES) + (threadIdx.x / TP_LANES); i < P; i += ngroups) {
         if (!a.keep[i]) continue;
         const long long x = perm[i], rk = a.keep_rank[i];
         const long long s0 = a.tp_off0[x], len = a.tp_off0[x + 1] - s0, d0 = a.keep_off[i];
-        for (long long p = lane; p < len; p += 32) a.tp_vert[d0 + p] = a.tp_vert0[s0 + p];
-        if (lane == 0) {
+        for (long long p = sub; p < len; p += TP_LANES) a.tp_vert[d0 + p] = a.tp_vert0[s0 + p];
+        if (sub == 0) {
             a.tp_graph[rk] = a.tp_graph0[x];
             a.tp_off[rk] = d0;
         }
@@ -474,6 +504,8 @@ cudaError_t gm_enqueue_tp(const GmArgs &a, cudaStream_t s) {
     if ((e = gm_scan<long long>(a.tp_len, a.tp_off0, &a.counts->P, a.P_cap, a.scan_tmp, nullptr, a.num_sms, s)))
         return e;
     if ((e = gm_scan<int>(a.run_start, a.run_rank, &a.counts->P, a.P_cap, a.scan_tmp, nullptr, a.num_sms, s)))
+        return e;
+    if ((e = gm_scan<long long>(a.len, a.key_off, &a.counts->P, a.P_cap, a.scan_tmp, nullptr, a.num_sms, s)))
         return e;
     gm_tp_check<<<1, 32, 0, s>>>(a);
     gm_run_bases<<<grid, GMB, 0, s>>>(a);

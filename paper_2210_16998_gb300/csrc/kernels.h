@@ -63,11 +63,12 @@ cudaError_t order_init_run(const int *pp_refs_level, int level, long long n, int
 cudaError_t order_ascend(int *keys, long long n, const LevelRec *levels, int from_level, int to_level,
                          cudaStream_t s);
 cudaError_t order_merge(const int *ka, const long long *ra, long long na, const int *kb, int level_b,
-                        long long nb, int *kc, long long *rc, cudaStream_t s);
+                        long long nb, int *kc, long long *rc, const LevelRec *levels, int from_level,
+                        cudaStream_t s);
 cudaError_t pp_lengths(const long long *refs, long long n, long long *len_out, cudaStream_t s);
 cudaError_t pp_offsets_single_level(long long *off, long long n, int level, cudaStream_t s);
 cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,
-                           const long long *offsets, const LevelRec *levels, const GraphDev &g,
+                           const long long *offsets, const LevelRec *levels, int max_levels, const GraphDev &g,
                            int *out_vertices, int *out_graph, cudaStream_t s);
 cudaError_t graph_ptr_from_ids(const int *ids, long long n, int G, long long *ptr, cudaStream_t s);
 
@@ -112,6 +113,10 @@ struct GmArgs {
     long long *bounds0;     // [P_cap+1]
     long long *tp_off0;     // [P_cap+1]
     int *tp_vert0;          // [TV0_cap]
+    long long *key_off;     // [P_cap+1] word offsets of the packed TP keys
+    unsigned long long *key;  // [K_cap] packed TP keys
+    long long K_cap;
+    int key_bits;           // 8 (graphs of <= 255 vertices) or 16
     long long *perm[2];     // [P_cap]
     int *keep;              // [P_cap]
     long long *keep_off, *keep_rank;  // [P_cap+1]

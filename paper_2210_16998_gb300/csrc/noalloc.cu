@@ -243,7 +243,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     } else if (npl == 1) {
         const int k = pp_levels[0];
         NA_CK(pp_offsets_single_level((long long *)offsets_dev, P, k, s));
-        NA_CK(pp_materialize(nullptr, lv[k].pp, k, P, (const long long *)offsets_dev, dlev, d, vertices_dev,
+        NA_CK(pp_materialize(nullptr, lv[k].pp, k, P, (const long long *)offsets_dev, dlev, a.max_levels, d, vertices_dev,
                              nullptr, s));
     } else {
         int *keys[2] = {(int *)(S + NA.keys0), (int *)(S + NA.keys1)};
@@ -257,8 +257,8 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
                 NA_CK(order_init_run(lref, k, lv[k].pp_count, keys[cur], refs[cur], s));
                 na = lv[k].pp_count;
             } else {
-                NA_CK(order_ascend(keys[cur], na, dlev, cur_level, k, s));
-                NA_CK(order_merge(keys[cur], refs[cur], na, lref, k, lv[k].pp_count, keys[cur ^ 1], refs[cur ^ 1], s));
+                NA_CK(order_merge(keys[cur], refs[cur], na, lref, k, lv[k].pp_count, keys[cur ^ 1], refs[cur ^ 1],
+                                  dlev, cur_level, s));
                 cur ^= 1;
                 na += lv[k].pp_count;
             }
@@ -266,7 +266,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
         }
         NA_CK(pp_lengths(refs[cur], P, (long long *)(S + NA.len), s));
         NA_CK(scan_i64((long long *)(S + NA.len), (long long *)offsets_dev, P, (long long *)(S + NA.ltmp), s));
-        NA_CK(pp_materialize(refs[cur], nullptr, 0, P, (const long long *)offsets_dev, dlev, d, vertices_dev,
+        NA_CK(pp_materialize(refs[cur], nullptr, 0, P, (const long long *)offsets_dev, dlev, a.max_levels, d, vertices_dev,
                              nullptr, s));
     }
     NA_CK(cudaStreamSynchronize(s));

@@ -54,28 +54,36 @@ cudaError_t order_ascend(int *keys, long long n, const LevelRec *levels, int fro
 
 constexpr int MERGE_ITEMS = 8;
 
-// Merge path: thread t produces outputs [t*ITEMS, t*ITEMS + ITEMS).  On equal
-// keys A goes first (cannot happen between A and B here, but keeps the merge
-// stable in general).
+// Merge path: thread t produces outputs [t*ITEMS, t*ITEMS + ITEMS).  The
+// keys of run A are stored at level from_level and lifted to level
+// to_level (the level of run B) on the fly.  On equal keys A goes first
+// (cannot happen between A and B here, but keeps the merge stable).
 __global__ void order_merge_kernel(const int *ka, const long long *ra, long long na, const int *kb,
-                                   int level_b, long long nb, int *kc, long long *rc) {
+                                   int level_b, long long nb, int *kc, long long *rc, const LevelRec *levels,
+                                   int from_level) {
     const long long total = na + nb;
     const long long diag = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * MERGE_ITEMS;
     if (diag >= total) return;
+    auto lift = [&](long long i) {
+        int key = ka[i];
+        for (int j = from_level; j > level_b; --j) key = levels[j].nodes[key].y;
+        return key;
+    };
     long long lo = diag > nb ? diag - nb : 0;
     long long hi = diag < na ? diag : na;
     while (lo < hi) {
         const long long mid = (lo + hi) >> 1;
-        if (ka[mid] <= kb[diag - mid - 1]) lo = mid + 1;
+        if (lift(mid) <= kb[diag - mid - 1]) lo = mid + 1;
         else hi = mid;
     }
     long long i = lo, j = diag - lo;
+    int ki = (i < na) ? lift(i) : 0;
     for (int t = 0; t < MERGE_ITEMS && diag + t < total; ++t) {
-        const bool take_a = (i < na) && (j >= nb || ka[i] <= kb[j]);
-        if (take_a) {
-            kc[diag + t] = ka[i];
+        if (i < na && (j >= nb || ki <= kb[j])) {
+            kc[diag + t] = ki;
             rc[diag + t] = ra[i];
             ++i;
+            if (i < na) ki = lift(i);
         } else {
             const int r = kb[j];
             kc[diag + t] = r;
@@ -86,11 +94,12 @@ __global__ void order_merge_kernel(const int *ka, const long long *ra, long long
 }
 
 cudaError_t order_merge(const int *ka, const long long *ra, long long na, const int *kb, int level_b, long long nb,
-                        int *kc, long long *rc, cudaStream_t s) {
+                        int *kc, long long *rc, const LevelRec *levels, int from_level, cudaStream_t s) {
     const long long total = na + nb;
     if (total <= 0) return cudaSuccess;
     const long long threads = (total + MERGE_ITEMS - 1) / MERGE_ITEMS;
-    order_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ka, ra, na, kb, level_b, nb, kc, rc);
+    order_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ka, ra, na, kb, level_b, nb, kc, rc, levels,
+                                                                        from_level);
     note_launch();
     return cudaGetLastError();
 }
@@ -126,21 +135,23 @@ constexpr int MAT_WARPS = 8;
 
 __global__ void __launch_bounds__(MAT_WARPS * 32)
     pp_materialize_kernel(const long long *refs, const int *single_refs, int single_level, long long n,
-                          const long long *offsets, const LevelRec *levels, GraphDev g, int *out,
-                          int *out_graph) {
+                          const long long *offsets, const LevelRec *levels, int max_levels, GraphDev g,
+                          int *out, int *out_graph) {
     __shared__ int buf[MAT_WARPS][MAT_BUF];
-    materialize_warps(refs, single_refs, single_level, n, offsets, levels, g, out, out_graph, buf);
+    __shared__ int2 *s_nodes[MAT_MAX_LV];
+    int2 *const *lv = cache_level_nodes(levels, max_levels, s_nodes);
+    materialize_warps(refs, single_refs, single_level, n, offsets, levels, g, out, out_graph, buf, lv);
 }
 
 cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,
-                           const long long *offsets, const LevelRec *levels, const GraphDev &g, int *out_vertices,
-                           int *out_graph, cudaStream_t s) {
+                           const long long *offsets, const LevelRec *levels, int max_levels, const GraphDev &g,
+                           int *out_vertices, int *out_graph, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const long long warps = (n + 31) / 32;
     long long blocks = (warps + MAT_WARPS - 1) / MAT_WARPS;
     if (blocks > 152 * 64) blocks = 152 * 64;
     pp_materialize_kernel<<<(unsigned)blocks, MAT_WARPS * 32, 0, s>>>(refs, single_refs, single_level, n, offsets,
-                                                                     levels, g, out_vertices, out_graph);
+                                                                     levels, max_levels, g, out_vertices, out_graph);
     note_launch();
     return cudaGetLastError();
 }

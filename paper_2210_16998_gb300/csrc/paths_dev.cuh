@@ -21,6 +21,26 @@ __device__ __forceinline__ int tp_cmp(long long a, long long b, const long long 
     return la < lb ? -1 : 1;
 }
 
+// Packed comparison keys of vertex sequences: vertex v is stored as v + 1
+// in `bits` (8 or 16) bits, most significant first, vpw = 64 / bits vertices
+// per 64-bit word, the last word zero-padded.  Comparing word by word (a
+// missing word reads as 0) orders the sequences lexicographically with a
+// proper prefix first, and equal keys mean equal sequences.
+__device__ __forceinline__ int key_cmp(long long a, long long b, const long long *koff,
+                                       const unsigned long long *key, const int *graph) {
+    const int ga = graph[a], gb = graph[b];
+    if (ga != gb) return ga < gb ? -1 : 1;
+    const long long a0 = koff[a], wa = koff[a + 1] - a0;
+    const long long b0 = koff[b], wb = koff[b + 1] - b0;
+    const long long w = wa > wb ? wa : wb;
+    for (long long t = 0; t < w; ++t) {
+        const unsigned long long x = t < wa ? key[a0 + t] : 0ull;
+        const unsigned long long y = t < wb ? key[b0 + t] : 0ull;
+        if (x != y) return x < y ? -1 : 1;
+    }
+    return 0;
+}
+
 // Materialise PPs [0, n): one warp handles 32 consecutive PPs; each lane
 // walks its path's parent links from the last vertex back to the first,
 // writing into a per-warp shared-memory window that the warp then stores
@@ -29,12 +49,23 @@ __device__ __forceinline__ int tp_cmp(long long a, long long b, const long long 
 // single_refs[i] in level single_level.  out_graph (optional) receives the
 // graph id of each PP.
 constexpr int MAT_BUF = 2048;  // int32 per warp (8 KB)
+constexpr int MAT_MAX_LV = 512; // level-pointer table cached in shared memory up to this many levels
+
+// Copy the levels' node pointers to shared memory (one dependent load per
+// parent-link step instead of two); returns nullptr when there are too many.
+__device__ __forceinline__ int2 *const *cache_level_nodes(const LevelRec *levels, int max_levels,
+                                                          int2 **s_nodes) {
+    if (max_levels > MAT_MAX_LV) return nullptr;
+    for (int k = threadIdx.x; k < max_levels; k += blockDim.x) s_nodes[k] = levels[k].nodes;
+    __syncthreads();
+    return s_nodes;
+}
 
 template <int NWARPS>
 __device__ __forceinline__ void materialize_warps(const long long *refs, const int *single_refs, int single_level,
                                                   long long n, const long long *offsets, const LevelRec *levels,
                                                   const GraphDev &g, int *out, int *out_graph,
-                                                  int (&buf)[NWARPS][MAT_BUF]) {
+                                                  int (&buf)[NWARPS][MAT_BUF], int2 *const *lvl_nodes) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long nwarps = (long long)gridDim.x * NWARPS;
     for (long long w0 = (blockIdx.x * (long long)NWARPS + wid) * 32; w0 < n; w0 += nwarps * 32) {
@@ -58,7 +89,7 @@ __device__ __forceinline__ void materialize_warps(const long long *refs, const i
         const bool staged = span <= MAT_BUF;
         int node = rel, root = 0;
         for (int j = level; j >= 1; --j) {
-            const int2 rec = levels[j].nodes[node];
+            const int2 rec = lvl_nodes ? lvl_nodes[j][node] : levels[j].nodes[node];
             const int v = rec.x;
             const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
             if (staged) buf[wid][off - start + (j - 1)] = loc;
