@@ -167,7 +167,7 @@ int tpg_prime_paths(tpg_cfg *g, tpg_paths **out);
  */
 int tpg_test_paths(tpg_cfg *g, tpg_paths **out);
 
-/* Release a tpg_cfg* or tpg_paths* (tag-checked).  NULL is a no-op. */
+/* Release a tpg_cfg*, tpg_paths* or tpg_sizer* (tag-checked).  NULL is a no-op. */
 void tpg_free(void *handle);
 
 /* Issue the handle's work on `stream` (a cudaStream_t; NULL = default). */
@@ -229,6 +229,69 @@ int tpg_graph_capture(tpg_cfg *g);
 int tpg_graph_launch(tpg_cfg *g, tpg_paths **pp, tpg_paths **tp);
 int tpg_set_output_capacity(tpg_cfg *g, int64_t prime_paths, int64_t pp_vertices,
                             int64_t tp_vertices_raw, int64_t tp_vertices);
+
+/*
+ * tpg_root_counts -- exact per-root volumes of the enumeration.
+ *
+ * counts_host[3*v + 0..2] (v a global vertex id; for a batch, graph g's
+ * vertices follow each other in graph order) receive, over the simple paths
+ * whose first vertex is v: their number (closed cycles included), the
+ * number of those that are prime, and the total vertices of those prime
+ * paths.  These are the training labels of the learned sizer.  Runs the
+ * frontier kernel in counting mode (no ordering, no outputs).
+ */
+int tpg_root_counts(tpg_cfg *g, int64_t *counts_host);
+
+/*
+ * Learned sizer (no counterpart in the paper; it addresses the storage cost
+ * the paper attributes to copying predecessor paths, Sec. 4.3).
+ *
+ * A message-passing network over the CFG (8 vertex features, three layers
+ * of width 64, BF16 weights and activations, FP32 accumulation and FP32
+ * master weights trained with Adam) predicts for every vertex r the log1p
+ * of three enumeration volumes rooted at r: simple paths, prime paths and
+ * prime-path vertices.  Summed over a handle, they pre-size its graph-mode
+ * capture (tpg_sizer_presize), so a new batch can be captured and replayed
+ * without an exact sizing run; a replay whose capacities prove too small
+ * falls back to the exact path, so results never depend on the network.
+ *
+ * tpg_sizer_create      new network, weights initialised from `seed`.
+ * tpg_sizer_add_batch   keep a training batch: the handle's graph, its
+ *                       features and exact per-root labels (tpg_root_counts)
+ *                       and its whole-batch volumes; volumes_out (optional,
+ *                       6 values): simple paths, peak level, PPs, PP
+ *                       vertices, TP vertices before and after dedup.
+ * tpg_sizer_train       `epochs` passes over the kept batches (one Adam step
+ *                       per batch, rate cosine-decayed from lr to lr/10);
+ *                       loss_per_epoch (optional) receives the mean loss.
+ * tpg_sizer_predict     per-vertex predictions pred_host[3*N] (optional) and
+ *                       their expm1 sums totals_host[3] (optional).
+ * tpg_sizer_presize     capacities of the handle's next graph capture from
+ *                       the predicted totals times `margin` (>= 1); caps_out
+ *                       (optional, 7 values) receives them.
+ * tpg_sizer_features    the 8 features of every vertex (x_host[8*N]).
+ * tpg_sizer_get_params / tpg_sizer_set_params   FP32 master weights
+ *                       (tpg_sizer_num_params() floats).
+ * tpg_sizer_loss_grad   loss and gradient on kept batch `batch` at the
+ *                       current weights, without an update.
+ * tpg_sizer_batch_targets  the labels of kept batch `batch` (targets[3*N]).
+ * tpg_sizer_save / tpg_sizer_load   weights and volume ratios to a file.
+ * A tpg_sizer* is released with tpg_free.
+ */
+typedef struct tpg_sizer tpg_sizer;
+int tpg_sizer_num_params(void);
+int tpg_sizer_create(uint64_t seed, tpg_sizer **out);
+int tpg_sizer_add_batch(tpg_sizer *z, tpg_cfg *g, int64_t *volumes_out);
+int tpg_sizer_train(tpg_sizer *z, int32_t epochs, float lr, float *loss_per_epoch);
+int tpg_sizer_predict(tpg_sizer *z, tpg_cfg *g, float *pred_host, double *totals_host);
+int tpg_sizer_presize(tpg_sizer *z, tpg_cfg *g, double margin, int64_t *caps_out);
+int tpg_sizer_features(tpg_cfg *g, float *x_host);
+int tpg_sizer_get_params(const tpg_sizer *z, float *host);
+int tpg_sizer_set_params(tpg_sizer *z, const float *host);
+int tpg_sizer_loss_grad(tpg_sizer *z, int32_t batch, double *loss, float *grad_host);
+int tpg_sizer_batch_targets(tpg_sizer *z, int32_t batch, float *targets_host);
+int tpg_sizer_save(const tpg_sizer *z, const char *path);
+int tpg_sizer_load(tpg_sizer *z, const char *path);
 
 /* Statistics of the handle's last calls. */
 int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);

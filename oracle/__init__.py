@@ -67,7 +67,7 @@ def _load():
             getattr(lib, name).restype = ctypes.c_int64
             getattr(lib, name).argtypes = [P]
         for name in ("orc_pp_offsets", "orc_tp_offsets", "orc_len_counts",
-                     "orc_pp_len_counts", "orc_root_paths", "orc_root_pp_ints"):
+                     "orc_pp_len_counts", "orc_root_paths", "orc_root_pp_ints", "orc_root_pps"):
             getattr(lib, name).restype = ctypes.POINTER(ctypes.c_int64)
             getattr(lib, name).argtypes = [P]
         for name in ("orc_pp_vertices", "orc_tp_vertices"):
@@ -100,6 +100,7 @@ class OracleResult:
     pp_len_counts: np.ndarray   # PPs by vertex count
     root_paths: np.ndarray      # simple paths per first vertex
     root_pp_ints: np.ndarray    # PP vertices per first vertex
+    root_pps: np.ndarray        # PPs per first vertex
     pp_offsets: np.ndarray | None = None
     pp_vertices: np.ndarray | None = None
     tp_offsets: np.ndarray | None = None
@@ -139,6 +140,7 @@ def run(n, row_ptr, col, entry=None, exit=None, want_paths=True, limit=0,
             pp_len_counts=_copy(lib.orc_pp_len_counts(h), n + 3, np.int64),
             root_paths=_copy(lib.orc_root_paths(h), n, np.int64),
             root_pp_ints=_copy(lib.orc_root_pp_ints(h), n, np.int64),
+            root_pps=_copy(lib.orc_root_pps(h), n, np.int64),
         )
         if want_paths or test_paths:
             cnt = int(lib.orc_pp_count(h))

@@ -59,6 +59,7 @@ typedef struct orc_result {
     int64_t *pp_len_counts; /* [n+2] PPs by vertex count */
     int64_t *root_paths;    /* [n] simple paths per first vertex */
     int64_t *root_pp_ints;  /* [n] total PP vertices per first vertex */
+    int64_t *root_pps;      /* [n] PPs per first vertex */
     int32_t *bfs_dist;      /* [n*n] or NULL */
     int32_t *bfs_pred;      /* [n*n] or NULL */
     int err;
@@ -209,8 +210,9 @@ orc_result *orc_prime_paths(int n, const int32_t *row_ptr, const int32_t *col,
     r->pp_len_counts = (int64_t *)calloc((size_t)n + 3, sizeof(int64_t));
     r->root_paths = (int64_t *)calloc((size_t)n, sizeof(int64_t));
     r->root_pp_ints = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    r->root_pps = (int64_t *)calloc((size_t)n, sizeof(int64_t));
     if (!path || !it || !onpath || !mark || !ext || !r->len_counts || !r->pp_len_counts ||
-        !r->root_paths || !r->root_pp_ints || build_pred(&g) || sl_init(&r->pp)) {
+        !r->root_paths || !r->root_pp_ints || !r->root_pps || build_pred(&g) || sl_init(&r->pp)) {
         r->err = ORC_ENOMEM;
         goto done;
     }
@@ -242,6 +244,7 @@ orc_result *orc_prime_paths(int n, const int32_t *row_ptr, const int32_t *col,
                 }
                 if (!extendable) {
                     r->pp_len_counts[len]++;
+                    r->root_pps[root]++;
                     r->root_pp_ints[root] += len;
                     if (want_paths && sl_push(&r->pp, path, len, -1)) { r->err = ORC_ENOMEM; break; }
                 }
@@ -271,6 +274,7 @@ orc_result *orc_prime_paths(int n, const int32_t *row_ptr, const int32_t *col,
                     }
                     if (!extendable) {
                         r->pp_len_counts[len + 1]++;
+                        r->root_pps[root]++;
                         r->root_pp_ints[root] += len + 1;
                         if (want_paths && sl_push(&r->pp, path, len, w)) { r->err = ORC_ENOMEM; break; }
                     }
@@ -391,13 +395,14 @@ const int64_t *orc_len_counts(const orc_result *r) { return r->len_counts; }
 const int64_t *orc_pp_len_counts(const orc_result *r) { return r->pp_len_counts; }
 const int64_t *orc_root_paths(const orc_result *r) { return r->root_paths; }
 const int64_t *orc_root_pp_ints(const orc_result *r) { return r->root_pp_ints; }
+const int64_t *orc_root_pps(const orc_result *r) { return r->root_pps; }
 
 void orc_free(orc_result *r) {
     if (!r) return;
     sl_free(&r->pp);
     sl_free(&r->tp);
     free(r->len_counts); free(r->pp_len_counts);
-    free(r->root_paths); free(r->root_pp_ints);
+    free(r->root_paths); free(r->root_pp_ints); free(r->root_pps);
     free(r->bfs_dist); free(r->bfs_pred);
     free(r);
 }

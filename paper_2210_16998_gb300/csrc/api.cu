@@ -17,12 +17,13 @@ using namespace tpg;
 
 namespace tpg {
 std::atomic<long long> g_kernel_launches{0};
-}
+}  // namespace tpg
 
 namespace {
 
 constexpr uint32_t MAGIC_CFG = 0x54504743u;    // "TPGC"
 constexpr uint32_t MAGIC_PATHS = 0x54504750u;  // "TPGP"
+constexpr uint32_t MAGIC_SIZER = 0x5450475au;  // "TPGZ"
 constexpr uint32_t MAGIC_DEAD = 0xDEADBEEFu;
 
 struct AllocFns {
@@ -153,6 +154,25 @@ int cuda_err(cudaError_t e) {
 
 }  // namespace
 
+namespace tpg {
+void *lib_dev_alloc(size_t bytes, cudaStream_t s) {
+    AllocFns f;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        f = g_alloc;
+    }
+    return dev_alloc(f, bytes, s);
+}
+void lib_dev_free(void *p, cudaStream_t s) {
+    AllocFns f;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        f = g_alloc;
+    }
+    dev_release(f, p, s);
+}
+}  // namespace tpg
+
 // ---------------------------------------------------------------------------
 // handle and result objects
 // ---------------------------------------------------------------------------
@@ -212,8 +232,28 @@ struct tpg_cfg {
         long long kernels_per_replay = 0;
     } gp;
     long long out_cap[4] = {0, 0, 0, 0};  // explicit output capacities P, V, TV0, TV (0 = last run)
+    unsigned long long *root_counts = nullptr;  // set while a counting run is in progress
     std::vector<LevelRec> h_levels;
     int *h_small = nullptr;  // pinned staging for small read-backs (4 KB)
+};
+
+// one training batch of the learned sizer: a copy of a handle's graph,
+// its features, exact labels and whole-batch volumes
+struct SizerBatch {
+    long long N = 0;
+    DevBuf rp, col, prp, pcol, X, T;
+    double nodes = 0, peak = 0, P = 0, V = 0, TV0 = 0, TV = 0;
+};
+
+struct tpg_sizer {
+    uint32_t magic = MAGIC_SIZER;
+    SizerNet *net = nullptr;
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    AllocFns fns;
+    std::vector<SizerBatch> batches;
+    double r_peak = 0, r_tv0 = 0, r_tv = 0;  // largest volume ratios seen in training
+    unsigned long long seed = 0;
 };
 
 namespace {
@@ -484,6 +524,7 @@ int enumerate_levels(tpg_cfg *g) {
         a.err = g->ctl.as<int>();
         a.stop_level = g->ctl.as<int>() + 1;
         a.bar = (unsigned *)(g->ctl.as<char>() + 64);
+        a.root_counts = g->root_counts;
         int grid = 0;
         CK(cudaEventRecord(g->ev[0], s));
         CK(launch_enumerate(a, g->shape, g->num_sms, s, &grid));
@@ -549,7 +590,10 @@ int enumerate_levels(tpg_cfg *g) {
             release(g, g->status);
             RC(ensure(g, g->status, sizeof(unsigned long long) * g->status_cap));
         }
-        // level k restarts its look-back from an empty status array
+        // level k restarts its look-back from an empty status array; its
+        // per-root counts are taken again, so subtract nothing: the counting
+        // run repeats from a clean slate instead (see run_root_counts)
+        if (g->root_counts) return TPG_ENOMEM;
         long long zero = 0;
         CK(cudaMemsetAsync(g->status.p, 0, sizeof(unsigned long long) * g->status_cap, s));
         CK(cudaMemcpyAsync((char *)g->levels.p + sizeof(LevelRec) * k + offsetof(LevelRec, status_base), &zero,
@@ -1063,6 +1107,35 @@ int capture_plan(tpg_cfg *g) {
     return TPG_OK;
 }
 
+// Exact per-root counts by one counting run of the frontier launch.  A
+// resumed launch would count its restarted level twice, so a counting run
+// that needs more room grows the capacities and starts over.
+int run_root_counts(tpg_cfg *g, DevBuf &buf) {
+    RC(ensure(g, buf, sizeof(unsigned long long) * 3 * (size_t)g->N));
+    for (int attempt = 0; attempt < 32; ++attempt) {
+        CK(cudaMemsetAsync(buf.p, 0, sizeof(unsigned long long) * 3 * (size_t)g->N, g->stream));
+        g->root_counts = buf.as<unsigned long long>();
+        const int rc = enumerate_levels(g);
+        g->root_counts = nullptr;
+        if (rc == TPG_OK) return TPG_OK;
+        if (rc != TPG_ENOMEM) return rc;
+        // grow from what this attempt saw and start again
+        long long seen = 0, peak = 0, pps = 0;
+        for (int k = 1; k < g->max_levels; ++k) {
+            const LevelRec &L = g->h_levels[k];
+            if (L.count <= 0) break;
+            seen += L.count + L.children;
+            peak = std::max(peak, std::max(L.count, L.children));
+            pps += L.pp_count;
+        }
+        g->node_cap = std::max(g->node_cap * 4, 2 * seen);
+        g->lvl_cap = std::min<long long>(std::max(g->lvl_cap * 2, 2 * peak), (long long)MAX31 - 1);
+        g->pp_cap = std::max(g->pp_cap * 4, 2 * pps + 1);
+        g->status_cap = 0;
+    }
+    return TPG_ENOMEM;
+}
+
 bool is_cfg(const void *p) { return p && ((const tpg_cfg *)p)->magic == MAGIC_CFG; }
 
 }  // namespace
@@ -1299,6 +1372,22 @@ int tpg_test_paths(tpg_cfg *g, tpg_paths **out) {
     return rc;
 }
 
+int tpg_root_counts(tpg_cfg *g, int64_t *counts_host) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (!counts_host) return TPG_EINVAL;
+    DevBuf buf;
+    int rc = run_root_counts(g, buf);
+    if (rc == TPG_OK) {
+        if (cudaMemcpyAsync(counts_host, buf.p, sizeof(long long) * 3 * (size_t)g->N, cudaMemcpyDeviceToHost,
+                            g->stream) ||
+            cudaStreamSynchronize(g->stream))
+            rc = cuda_err(cudaGetLastError());
+    }
+    release(g, buf);
+    g->pp_valid = false;  // the arena now holds the counting run
+    return rc;
+}
+
 int tpg_set_output_capacity(tpg_cfg *g, int64_t prime_paths, int64_t pp_vertices, int64_t tp_vertices_raw,
                             int64_t tp_vertices) {
     if (!is_cfg(g)) return TPG_EHANDLE;
@@ -1380,11 +1469,284 @@ int tpg_graph_launch(tpg_cfg *g, tpg_paths **pp, tpg_paths **tp) {
     return rc;
 }
 
+// ---------------------------------------------------------------------------
+// learned sizer
+// ---------------------------------------------------------------------------
+int tpg_sizer_num_params(void) { return sz_param_count(); }
+
+int tpg_sizer_create(uint64_t seed, tpg_sizer **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    tpg_sizer *z = new tpg_sizer();
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        z->fns = g_alloc;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&z->num_sms, cudaDevAttrMultiProcessorCount, dev)) {
+        cudaGetLastError();
+        delete z;
+        return TPG_ECUDA;
+    }
+    z->seed = seed;
+    z->net = sz_create(seed, z->stream, z->num_sms);
+    if (!z->net) {
+        delete z;
+        return TPG_ENOMEM;
+    }
+    *out = z;
+    return TPG_OK;
+}
+
+static bool is_sizer(const void *p) { return p && ((const tpg_sizer *)p)->magic == MAGIC_SIZER; }
+
+static void free_sizer_batch(tpg_sizer *z, SizerBatch &b) {
+    DevBuf *all[] = {&b.rp, &b.col, &b.prp, &b.pcol, &b.X, &b.T};
+    for (DevBuf *d : all) {
+        dev_release(z->fns, d->p, z->stream);
+        d->p = nullptr;
+        d->bytes = 0;
+    }
+}
+
+static int sz_buf(tpg_sizer *z, DevBuf &b, size_t bytes) {
+    b.p = dev_alloc(z->fns, bytes ? bytes : 16, z->stream);
+    b.bytes = bytes;
+    return b.p ? TPG_OK : TPG_ENOMEM;
+}
+
+static SzGraph view_of(const SizerBatch &b) {
+    SzGraph v;
+    v.N = b.N;
+    v.rp = b.rp.as<int>();
+    v.col = b.col.as<int>();
+    v.prp = b.prp.as<int>();
+    v.pcol = b.pcol.as<int>();
+    v.X = b.X.as<float>();
+    v.T = b.T.as<float>();
+    return v;
+}
+
+// copy of the handle's graph and its features (no labels)
+static int sizer_snapshot(tpg_sizer *z, tpg_cfg *g, SizerBatch &b) {
+    b.N = g->N;
+    cudaStream_t s = g->stream;
+    RC(sz_buf(z, b.rp, sizeof(int) * (g->N + 1)));
+    RC(sz_buf(z, b.col, sizeof(int) * std::max<long long>(g->M, 1)));
+    RC(sz_buf(z, b.prp, sizeof(int) * (g->N + 1)));
+    RC(sz_buf(z, b.pcol, sizeof(int) * std::max<long long>(g->M, 1)));
+    RC(sz_buf(z, b.X, sizeof(float) * sz_features_per_vertex() * g->N));
+    CK(cudaMemcpyAsync(b.rp.p, g->gd.rp, sizeof(int) * (g->N + 1), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(b.prp.p, g->gd.prp, sizeof(int) * (g->N + 1), cudaMemcpyDeviceToDevice, s));
+    if (g->M > 0) {
+        CK(cudaMemcpyAsync(b.col.p, g->gd.col, sizeof(int) * g->M, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(b.pcol.p, g->gd.pcol, sizeof(int) * g->M, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(sz_features(g->gd, b.X.as<float>(), s, z->num_sms));
+    CK(cudaStreamSynchronize(s));
+    return TPG_OK;
+}
+
+int tpg_sizer_add_batch(tpg_sizer *z, tpg_cfg *g, int64_t *volumes_out) {
+    if (!is_sizer(z)) return TPG_EHANDLE;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    SizerBatch b;
+    int rc = sizer_snapshot(z, g, b);
+    DevBuf counts;
+    if (rc == TPG_OK) rc = run_root_counts(g, counts);
+    if (rc == TPG_OK) rc = sz_buf(z, b.T, sizeof(float) * sz_targets() * g->N);
+    if (rc == TPG_OK) rc = cuda_err(sz_labels(counts.as<unsigned long long>(), g->N, b.T.as<float>(), g->stream,
+                                              z->num_sms));
+    if (rc == TPG_OK) rc = cuda_err(cudaStreamSynchronize(g->stream));
+    release(g, counts);
+    // whole-batch volumes (exact run) for the ratios used in pre-sizing
+    if (rc == TPG_OK) rc = run_prime_paths(g);
+    if (rc == TPG_OK) {
+        Block *o = nullptr, *v = nullptr, *gp = nullptr;
+        long long T = 0, TV = 0;
+        rc = run_test_paths(g, &o, &v, &gp, &T, &TV);
+        block_unref(o);
+        block_unref(v);
+        block_unref(gp);
+    }
+    if (rc != TPG_OK) {
+        free_sizer_batch(z, b);
+        return rc;
+    }
+    b.nodes = (double)g->stats.simple_paths;
+    b.peak = (double)g->stats.peak_level_nodes;
+    b.P = (double)g->stats.prime_paths;
+    b.V = (double)g->stats.pp_vertices;
+    b.TV0 = (double)g->last_tv0;
+    b.TV = (double)g->stats.tp_vertices;
+    if (b.nodes > 0) z->r_peak = std::max(z->r_peak, b.peak / b.nodes);
+    if (b.V > 0) {
+        z->r_tv0 = std::max(z->r_tv0, b.TV0 / b.V);
+        z->r_tv = std::max(z->r_tv, b.TV / b.V);
+    }
+    if (volumes_out) {
+        const double v6[6] = {b.nodes, b.peak, b.P, b.V, b.TV0, b.TV};
+        for (int i = 0; i < 6; ++i) volumes_out[i] = (int64_t)v6[i];
+    }
+    z->batches.push_back(b);
+    return TPG_OK;
+}
+
+int tpg_sizer_train(tpg_sizer *z, int32_t epochs, float lr, float *loss_per_epoch) {
+    if (!is_sizer(z)) return TPG_EHANDLE;
+    if (epochs < 0 || !(lr > 0.f) || z->batches.empty()) return TPG_EINVAL;
+    unsigned long long x = z->seed ^ 0xA5A5A5A5ull;
+    std::vector<int> order(z->batches.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    for (int ep = 0; ep < epochs; ++ep) {
+        // Fisher-Yates with splitmix64 steps; cosine decay of the rate to 10%
+        for (size_t i = order.size(); i > 1; --i) {
+            x += 0x9E3779B97F4A7C15ull;
+            unsigned long long r = x;
+            r = (r ^ (r >> 30)) * 0xBF58476D1CE4E5B9ull;
+            r = (r ^ (r >> 27)) * 0x94D049BB133111EBull;
+            r ^= r >> 31;
+            std::swap(order[i - 1], order[r % i]);
+        }
+        const float rate = lr * (0.1f + 0.9f * 0.5f * (1.f + cosf(3.14159265f * ep / std::max(1, epochs))));
+        double sum = 0.0;
+        for (int bi : order) {
+            double loss = 0.0;
+            CK(sz_loss_backward(z->net, view_of(z->batches[bi]), &loss));
+            CK(sz_adam_step(z->net, rate));
+            sum += loss;
+        }
+        if (loss_per_epoch) loss_per_epoch[ep] = (float)(sum / order.size());
+    }
+    CK(cudaStreamSynchronize(z->stream));
+    return TPG_OK;
+}
+
+int tpg_sizer_predict(tpg_sizer *z, tpg_cfg *g, float *pred_host, double *totals_host) {
+    if (!is_sizer(z) || !is_cfg(g)) return TPG_EHANDLE;
+    SizerBatch b;
+    int rc = sizer_snapshot(z, g, b);
+    if (rc == TPG_OK) rc = cuda_err(sz_predict(z->net, view_of(b), pred_host, totals_host));
+    free_sizer_batch(z, b);
+    return rc;
+}
+
+int tpg_sizer_presize(tpg_sizer *z, tpg_cfg *g, double margin, int64_t *caps_out) {
+    if (!is_sizer(z) || !is_cfg(g)) return TPG_EHANDLE;
+    if (!(margin >= 1.0)) return TPG_EINVAL;
+    double tot[3] = {0, 0, 0};
+    RC(tpg_sizer_predict(z, g, nullptr, tot));
+    const double nodes = tot[0] * margin + g->N, P = tot[1] * margin + 1, V = tot[2] * margin + 1;
+    const double rp = z->r_peak > 0 ? z->r_peak : 1.0;
+    g->node_cap = (long long)nodes;
+    g->lvl_cap = std::max<long long>((long long)(nodes * std::min(1.0, rp * margin)), g->N);
+    g->pp_cap = (long long)P;
+    g->out_cap[0] = (long long)P;
+    g->out_cap[1] = (long long)V;
+    g->out_cap[2] = (long long)(V * (z->r_tv0 > 0 ? z->r_tv0 : 2.0) * margin) + 1;
+    g->out_cap[3] = (long long)(V * (z->r_tv > 0 ? z->r_tv : 2.0) * margin) + 1;
+    g->gp.ready = false;
+    if (caps_out) {
+        const long long c[7] = {g->node_cap, g->lvl_cap, g->pp_cap, g->out_cap[0], g->out_cap[1], g->out_cap[2],
+                                g->out_cap[3]};
+        for (int i = 0; i < 7; ++i) caps_out[i] = c[i];
+    }
+    return TPG_OK;
+}
+
+int tpg_sizer_features(tpg_cfg *g, float *x_host) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (!x_host) return TPG_EINVAL;
+    DevBuf X;
+    RC(ensure(g, X, sizeof(float) * sz_features_per_vertex() * g->N));
+    int rc = cuda_err(sz_features(g->gd, X.as<float>(), g->stream, g->num_sms));
+    if (rc == TPG_OK &&
+        (cudaMemcpyAsync(x_host, X.p, sizeof(float) * sz_features_per_vertex() * g->N, cudaMemcpyDeviceToHost,
+                         g->stream) ||
+         cudaStreamSynchronize(g->stream)))
+        rc = cuda_err(cudaGetLastError());
+    release(g, X);
+    return rc;
+}
+
+int tpg_sizer_get_params(const tpg_sizer *z, float *host) {
+    if (!is_sizer(z)) return TPG_EHANDLE;
+    if (!host) return TPG_EINVAL;
+    return cuda_err(sz_get_params(z->net, host));
+}
+
+int tpg_sizer_set_params(tpg_sizer *z, const float *host) {
+    if (!is_sizer(z)) return TPG_EHANDLE;
+    if (!host) return TPG_EINVAL;
+    return cuda_err(sz_set_params(z->net, host));
+}
+
+int tpg_sizer_loss_grad(tpg_sizer *z, int32_t batch, double *loss, float *grad_host) {
+    if (!is_sizer(z)) return TPG_EHANDLE;
+    if (batch < 0 || batch >= (int)z->batches.size()) return TPG_EINVAL;
+    double l = 0.0;
+    CK(sz_loss_backward(z->net, view_of(z->batches[batch]), &l));
+    if (loss) *loss = l;
+    if (grad_host) CK(sz_get_grads(z->net, grad_host));
+    return TPG_OK;
+}
+
+int tpg_sizer_batch_targets(tpg_sizer *z, int32_t batch, float *targets_host) {
+    if (!is_sizer(z)) return TPG_EHANDLE;
+    if (batch < 0 || batch >= (int)z->batches.size() || !targets_host) return TPG_EINVAL;
+    const SizerBatch &b = z->batches[batch];
+    CK(cudaMemcpyAsync(targets_host, b.T.p, sizeof(float) * sz_targets() * b.N, cudaMemcpyDeviceToHost, z->stream));
+    CK(cudaStreamSynchronize(z->stream));
+    return TPG_OK;
+}
+
+int tpg_sizer_save(const tpg_sizer *z, const char *path) {
+    if (!is_sizer(z)) return TPG_EHANDLE;
+    if (!path) return TPG_EINVAL;
+    std::vector<float> p(sz_param_count());
+    CK(sz_get_params(z->net, p.data()));
+    FILE *f = fopen(path, "wb");
+    if (!f) return TPG_EINVAL;
+    const char magic[8] = {'T', 'P', 'G', 'S', 'Z', '0', '0', '1'};
+    const int32_t np = (int32_t)p.size();
+    const double r[3] = {z->r_peak, z->r_tv0, z->r_tv};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(&np, sizeof(np), 1, f) == 1 && fwrite(r, sizeof(double), 3, f) == 3 &&
+              fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? TPG_OK : TPG_EINVAL;
+}
+
+int tpg_sizer_load(tpg_sizer *z, const char *path) {
+    if (!is_sizer(z)) return TPG_EHANDLE;
+    if (!path) return TPG_EINVAL;
+    FILE *f = fopen(path, "rb");
+    if (!f) return TPG_EINVAL;
+    char magic[8];
+    int32_t np = 0;
+    double r[3];
+    std::vector<float> p(sz_param_count());
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "TPGSZ001", 8) == 0 && fread(&np, sizeof(np), 1, f) == 1 &&
+              np == (int32_t)p.size() && fread(r, sizeof(double), 3, f) == 3 &&
+              fread(p.data(), sizeof(float), p.size(), f) == p.size();
+    fclose(f);
+    if (!ok) return TPG_EINVAL;
+    z->r_peak = r[0];
+    z->r_tv0 = r[1];
+    z->r_tv = r[2];
+    return cuda_err(sz_set_params(z->net, p.data()));
+}
+
 void tpg_free(void *handle) {
     if (!handle) return;
     const uint32_t magic = *(const uint32_t *)handle;
     if (magic == MAGIC_CFG) {
         destroy_cfg((tpg_cfg *)handle);
+    } else if (magic == MAGIC_SIZER) {
+        tpg_sizer *z = (tpg_sizer *)handle;
+        for (auto &b : z->batches) free_sizer_batch(z, b);
+        sz_destroy(z->net);
+        z->magic = MAGIC_DEAD;
+        delete z;
     } else if (magic == MAGIC_PATHS) {
         PathsImpl *r = (PathsImpl *)handle;
         for (int i = 0; i < 3; ++i) {

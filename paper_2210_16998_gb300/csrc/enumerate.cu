@@ -165,6 +165,25 @@ __global__ void __launch_bounds__(BLOCK) enumerate_kernel(EnumArgs a) {
                     pp[j] = lm;
                 }
             }
+            if (a.root_counts) {
+                // per-root totals: paths arrive sorted by first vertex, so a
+                // warp's lanes mostly share one root; one atomic per group
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) {
+                    const unsigned grp = __match_any_sync(0xffffffffu, first[j]);
+                    const unsigned one = first[j] >= 0 ? 1u : 0u;
+                    const unsigned isp = (first[j] >= 0 && pp[j]) ? 1u : 0u;
+                    const unsigned c0 = __reduce_add_sync(grp, one);
+                    const unsigned c1 = __reduce_add_sync(grp, isp);
+                    const unsigned c2 = __reduce_add_sync(grp, isp * (unsigned)k);
+                    if (first[j] >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) {
+                        unsigned long long *rc = a.root_counts + 3ll * first[j];
+                        atomicAdd(rc, (unsigned long long)c0);
+                        if (c1) atomicAdd(rc + 1, (unsigned long long)c1);
+                        if (c2) atomicAdd(rc + 2, (unsigned long long)c2);
+                    }
+                }
+            }
             // exclusive scan of (children, PP) in path order
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j)

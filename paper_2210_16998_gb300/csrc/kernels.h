@@ -34,6 +34,7 @@ struct EnumArgs {
     int *err;                // error flags (zeroed)
     int *stop_level;         // level whose next level did not fit (written with the flags)
     unsigned *bar;           // grid barrier {count, generation} (zeroed)
+    unsigned long long *root_counts;  // optional [3*N]: per first vertex, simple paths, PPs, PP vertices
 };
 
 // enumerate.cu
@@ -130,6 +131,32 @@ int gm_tp_rounds(int maxn);
 size_t gm_scan_tmp_elems(long long n_cap);
 cudaError_t gm_enqueue_pp(const GmArgs &a, cudaStream_t s);
 cudaError_t gm_enqueue_tp(const GmArgs &a, cudaStream_t s);
+
+// sizer.cu: the learned sizer's network
+struct SizerNet;
+struct SzGraph {
+    long long N;
+    const int *rp, *col, *prp, *pcol;  // successor / predecessor CSR (global ids)
+    const float *X;                    // [N][8] features
+    const float *T;                    // [N][3] targets (training only)
+};
+int sz_param_count();
+int sz_features_per_vertex();
+int sz_targets();
+SizerNet *sz_create(unsigned long long seed, cudaStream_t s, int num_sms);
+void sz_destroy(SizerNet *n);
+cudaError_t sz_set_params(SizerNet *n, const float *host);
+cudaError_t sz_get_params(SizerNet *n, float *host);
+cudaError_t sz_get_grads(SizerNet *n, float *host);
+cudaError_t sz_features(const GraphDev &g, float *X, cudaStream_t s, int num_sms);
+cudaError_t sz_labels(const unsigned long long *counts, long long N, float *T, cudaStream_t s, int num_sms);
+cudaError_t sz_forward(SizerNet *n, const SzGraph &b);
+cudaError_t sz_loss_backward(SizerNet *n, const SzGraph &b, double *loss_host);
+cudaError_t sz_adam_step(SizerNet *n, float lr);
+cudaError_t sz_predict(SizerNet *n, const SzGraph &b, float *Y_host, double *totals_host);
+// device allocator of the library (api.cu)
+void *lib_dev_alloc(size_t bytes, cudaStream_t s);
+void lib_dev_free(void *p, cudaStream_t s);
 
 // preprocess.cu
 cudaError_t build_union_csr(const int *unused, const long long *rp_base_dev,

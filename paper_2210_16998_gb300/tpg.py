@@ -133,6 +133,28 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_set_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         lib.tpg_set_output_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         lib.tpg_graph_capture.argtypes = [P]
+        lib.tpg_root_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        lib.tpg_root_counts.restype = ctypes.c_int
+        fp = ctypes.POINTER(ctypes.c_float)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.tpg_sizer_num_params.restype = ctypes.c_int
+        lib.tpg_sizer_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
+        lib.tpg_sizer_add_batch.argtypes = [P, P, i64p]
+        lib.tpg_sizer_train.argtypes = [P, ctypes.c_int32, ctypes.c_float, fp]
+        lib.tpg_sizer_predict.argtypes = [P, P, fp, dp]
+        lib.tpg_sizer_presize.argtypes = [P, P, ctypes.c_double, i64p]
+        lib.tpg_sizer_features.argtypes = [P, fp]
+        lib.tpg_sizer_get_params.argtypes = [P, fp]
+        lib.tpg_sizer_set_params.argtypes = [P, fp]
+        lib.tpg_sizer_loss_grad.argtypes = [P, ctypes.c_int32, dp, fp]
+        lib.tpg_sizer_batch_targets.argtypes = [P, ctypes.c_int32, fp]
+        lib.tpg_sizer_save.argtypes = [P, ctypes.c_char_p]
+        lib.tpg_sizer_load.argtypes = [P, ctypes.c_char_p]
+        for name in ("tpg_sizer_create", "tpg_sizer_add_batch", "tpg_sizer_train", "tpg_sizer_predict",
+                     "tpg_sizer_presize", "tpg_sizer_features", "tpg_sizer_get_params", "tpg_sizer_set_params",
+                     "tpg_sizer_loss_grad", "tpg_sizer_batch_targets", "tpg_sizer_save", "tpg_sizer_load"):
+            getattr(lib, name).restype = ctypes.c_int
         lib.tpg_graph_launch.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths)),
                                          ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_set_allocator.argtypes = [_ALLOC_FN, _RELEASE_FN, P]
@@ -364,7 +386,7 @@ def tpg_test_paths(cfg: Cfg) -> Paths:
 
 
 def tpg_free(obj):
-    if isinstance(obj, (Cfg,)):
+    if isinstance(obj, (Cfg, Sizer)):
         obj.close()
     elif isinstance(obj, Paths):
         obj.free()
@@ -391,6 +413,14 @@ def tpg_set_capacity(cfg: Cfg, nodes: int, level_nodes: int, prime_paths: int):
 def tpg_set_output_capacity(cfg: Cfg, prime_paths: int, pp_vertices: int, tp_vertices_raw: int, tp_vertices: int):
     _check(load_library().tpg_set_output_capacity(cfg.handle, int(prime_paths), int(pp_vertices),
                                                   int(tp_vertices_raw), int(tp_vertices)), "tpg_set_output_capacity")
+
+
+def tpg_root_counts(cfg: Cfg, num_vertices: int):
+    """Per first vertex: (simple paths, prime paths, prime-path vertices), int64 [N, 3]."""
+    out = np.zeros((num_vertices, 3), dtype=np.int64)
+    _check(load_library().tpg_root_counts(cfg.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+           "tpg_root_counts")
+    return out
 
 
 def tpg_graph_capture(cfg: Cfg):
@@ -440,6 +470,114 @@ def tpg_prime_paths_noalloc(n, m, row_ptr_dev, col_dev, offsets_dev, vertices_de
                                      int(offsets_dev.numel()) - 1, ctypes.c_void_p(vertices_dev.data_ptr()),
                                      int(vertices_dev.numel()), s, ctypes.byref(npaths), ctypes.byref(nverts))
     return int(rc), int(npaths.value), int(nverts.value)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Sizer:
+    """The learned sizer (owns a tpg_sizer*)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    def close(self):
+        if self.handle:
+            load_library().tpg_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def tpg_sizer_num_params() -> int:
+    return int(load_library().tpg_sizer_num_params())
+
+
+def tpg_sizer_create(seed: int = 0) -> Sizer:
+    h = ctypes.c_void_p()
+    _check(load_library().tpg_sizer_create(int(seed), ctypes.byref(h)), "tpg_sizer_create")
+    return Sizer(h.value)
+
+
+def tpg_sizer_add_batch(z: Sizer, cfg: Cfg):
+    """Keep (graph, features, exact labels) of a handle; returns its volumes
+    (simple paths, peak level, PPs, PP vertices, TP vertices raw, TP vertices)."""
+    vol = np.zeros(6, np.int64)
+    _check(load_library().tpg_sizer_add_batch(z.handle, cfg.handle, vol.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+           "tpg_sizer_add_batch")
+    return vol
+
+
+def tpg_sizer_train(z: Sizer, epochs: int, lr: float):
+    losses = np.zeros(max(epochs, 1), np.float32)
+    _check(load_library().tpg_sizer_train(z.handle, int(epochs), float(lr), _fptr(losses)), "tpg_sizer_train")
+    return losses[:epochs]
+
+
+def tpg_sizer_predict(z: Sizer, cfg: Cfg, num_vertices: int):
+    pred = np.zeros((num_vertices, 3), np.float32)
+    tot = np.zeros(3, np.float64)
+    _check(load_library().tpg_sizer_predict(z.handle, cfg.handle, _fptr(pred),
+                                           tot.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "tpg_sizer_predict")
+    return pred, tot
+
+
+def tpg_sizer_presize(z: Sizer, cfg: Cfg, margin: float):
+    caps = np.zeros(7, np.int64)
+    _check(load_library().tpg_sizer_presize(z.handle, cfg.handle, float(margin),
+                                           caps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "tpg_sizer_presize")
+    return caps
+
+
+def tpg_sizer_features(cfg: Cfg, num_vertices: int):
+    x = np.zeros((num_vertices, 8), np.float32)
+    _check(load_library().tpg_sizer_features(cfg.handle, _fptr(x)), "tpg_sizer_features")
+    return x
+
+
+def tpg_sizer_get_params(z: Sizer):
+    p = np.zeros(tpg_sizer_num_params(), np.float32)
+    _check(load_library().tpg_sizer_get_params(z.handle, _fptr(p)), "tpg_sizer_get_params")
+    return p
+
+
+def tpg_sizer_set_params(z: Sizer, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == tpg_sizer_num_params()
+    _check(load_library().tpg_sizer_set_params(z.handle, _fptr(p)), "tpg_sizer_set_params")
+
+
+def tpg_sizer_loss_grad(z: Sizer, batch: int):
+    g = np.zeros(tpg_sizer_num_params(), np.float32)
+    loss = ctypes.c_double(0.0)
+    _check(load_library().tpg_sizer_loss_grad(z.handle, int(batch), ctypes.byref(loss), _fptr(g)),
+           "tpg_sizer_loss_grad")
+    return float(loss.value), g
+
+
+def tpg_sizer_batch_targets(z: Sizer, batch: int, num_vertices: int):
+    t = np.zeros((num_vertices, 3), np.float32)
+    _check(load_library().tpg_sizer_batch_targets(z.handle, int(batch), _fptr(t)), "tpg_sizer_batch_targets")
+    return t
+
+
+def tpg_sizer_save(z: Sizer, path: str):
+    _check(load_library().tpg_sizer_save(z.handle, path.encode()), "tpg_sizer_save")
+
+
+def tpg_sizer_load(z: Sizer, path: str):
+    _check(load_library().tpg_sizer_load(z.handle, path.encode()), "tpg_sizer_load")
 
 
 def tpg_kernel_launches() -> int:
