@@ -475,6 +475,159 @@ def run_batch(args, rank, world, local_rank):
     return line
 
 
+def lpt_groups(weights, k):
+    """Longest-processing-time packing: heaviest first, into the lightest group."""
+    order = np.argsort(-np.asarray(weights), kind="stable")
+    loads = np.zeros(k)
+    groups = [[] for _ in range(k)]
+    for i in order:
+        j = int(np.argmin(loads))
+        groups[j].append(int(i))
+        loads[j] += weights[i]
+    return [sorted(g) for g in groups], loads
+
+
+def run_sizer(args, rank, world, local_rank):
+    import torch
+
+    from paper_2210_16998_gb300 import cfggen, tpg
+
+    torch.cuda.set_device(local_rank)
+    tpg.load_library(build=True)
+    n_train = args.train_graphs
+    t0 = time.perf_counter()
+    train = [cfggen.random_cfg(cfggen.TRAIN_SEED0 + i) for i in range(n_train)]
+    held = cfggen.batch_cfgs(4096, cfggen.HELDOUT_SEED0)
+    gen_s = time.perf_counter() - t0
+    z = tpg.tpg_sizer_create(seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b0 in range(0, n_train, 4096):
+        ns, rp, col, ent, ext = cfggen.concat_batch(train[b0:b0 + 4096])
+        with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext) as h:
+            tpg.tpg_sizer_add_batch(z, h)
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = tpg.tpg_sizer_train(z, args.epochs, 3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    ns, rp, col, ent, ext = cfggen.concat_batch(held)
+    N = int(ns.sum())
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, out
+
+    # exact per-graph volumes of the held-out batch (exact counting mode)
+    with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext) as h:
+        counts = tpg.tpg_root_counts(h, N)
+    bounds = np.concatenate([[0], np.cumsum(ns)])
+    truth = np.array([counts[bounds[i]:bounds[i + 1]].sum(0) for i in range(len(held))], np.float64)
+
+    # (a) plain host-driven enumerator, cold handle
+    def plain_host():
+        with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE) as h:
+            tpg.tpg_set_tile_shape(h, *shape)
+            a, b = tpg.tpg_prime_paths(h), tpg.tpg_test_paths(h)
+            st = tpg.tpg_get_stats(h)
+            P = a.num_paths
+            a.free()
+            b.free()
+        return P, st
+
+    # (b) graph mode sized by an exact run, cold handle
+    def plain_graph():
+        with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE) as h:
+            tpg.tpg_set_tile_shape(h, *shape)
+            tpg.tpg_graph_capture(h)
+            a, b = tpg.tpg_graph_launch(h)
+            P = a.num_paths
+            a.free()
+            b.free()
+        return P
+
+    # (c) graph mode pre-sized by the sizer, cold handle
+    def sized_graph(idx=None, margin=args.margin):
+        sub = held if idx is None else [held[i] for i in idx]
+        n_, r_, c_, e_, x_ = cfggen.concat_batch(sub)
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        with tpg.tpg_load_cfg_batch(n_, r_, c_, e_, x_, location=tpg.TPG_RESULT_DEVICE) as h:
+            tpg.tpg_set_tile_shape(h, *shape)
+            caps = tpg.tpg_sizer_presize(z, h, margin)
+            tpg.tpg_graph_capture(h)
+            a, b = tpg.tpg_graph_launch(h)
+            st = tpg.tpg_get_stats(h)
+            P = a.num_paths
+            a.free()
+            b.free()
+            torch.cuda.synchronize()
+            t_first = time.perf_counter() - t_start
+            # steady-state replay of the same capture
+            t = time.perf_counter()
+            a, b = tpg.tpg_graph_launch(h)
+            torch.cuda.synchronize()
+            rep = time.perf_counter() - t
+            a.free()
+            b.free()
+        return P, st, caps, rep, t_first
+
+    shape = (512, 2)
+    plain_host()
+    plain_graph()
+    sized_graph()  # warm-up (allocator, module loading)
+    ta, (Pa, sta) = timed(plain_host)
+    tb, Pb = timed(plain_graph)
+    Pc, stc, caps, rep_s, tc = sized_graph()
+    assert Pa == Pb == Pc
+    with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext) as h:
+        pred, _ = tpg.tpg_sizer_predict(z, h, N)
+    vol = np.expm1(np.maximum(pred.astype(np.float64), 0))
+    est = np.array([vol[bounds[i]:bounds[i + 1]].sum(0) for i in range(len(held))])
+    err = np.abs(np.log1p(est) - np.log1p(truth))
+    # LPT launch groups by predicted volume (the same sums the pre-sizing uses):
+    # retry rate per graph
+    groups, loads = lpt_groups(est[:, 0], args.groups)
+    retried, tg = 0, 0.0
+    for gidx in groups:
+        Pg, stg, _, _, t_ = sized_graph(gidx)
+        tg += t_
+        if stg["graph_fallbacks"]:
+            retried += len(gidx)
+    used = truth[:, 0].sum() * 8
+    line = {
+        "metric": METRIC, "value": Pc / tc, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
+        "ms_per_step": 1000 * tc, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32 (sizer: bf16 weights, fp32 accumulate)", "data": "synthetic (seeded structured CFGs)",
+        "config": {"workload": "learned sizer: train on 50k seeded CFGs (10-150 vertices), evaluate on a held-out "
+                               "batch of 4096", "train_graphs": n_train, "epochs": args.epochs, "margin": args.margin,
+                   "held_out_graphs": len(held), "vertices": N, "prime_paths": Pc,
+                   "step": "cold start of a new batch: load + (predict + presize) + capture + one replay"},
+        "sizer": {"generate_s": gen_s, "label_s": label_s, "train_s": train_s,
+                  "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                  "per_graph_abs_log_err_mean": [float(x) for x in err.mean(0)],
+                  "per_graph_abs_log_err_p90": [float(x) for x in np.percentile(err, 90, axis=0)]},
+        "compare": {
+            "plain_host_driven": {"pp_per_s": Pa / ta, "s": ta, "arena_alloc_bytes": sta["arena_bytes_alloc"],
+                                  "arena_waste": 1 - used / max(sta["arena_bytes_alloc"], 1),
+                                  "frontier_launches": sta["attempts"]},
+            "plain_graph_exact_sizing": {"pp_per_s": Pb / tb, "s": tb},
+            "sizer_graph": {"pp_per_s": Pc / tc, "s": tc, "arena_alloc_bytes": int(caps[0]) * 8,
+                            "arena_waste": 1 - used / max(int(caps[0]) * 8, 1),
+                            "fallback": bool(stc["graph_fallbacks"]), "replay_pp_per_s": Pc / rep_s},
+            "sizer_lpt_groups": {"groups": args.groups, "retry_rate": retried / len(held), "s": tg,
+                                 "pp_per_s": Pc / tg, "predicted_loads": [float(x) for x in loads]},
+        },
+    }
+    z.close()
+    return line
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -514,7 +667,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k", type=int, default=K_DIAMONDS, help="diamonds in the chain (22 = the benchmark workload)")
-    ap.add_argument("--workload", choices=["chain", "batch"], default="chain")
+    ap.add_argument("--workload", choices=["chain", "batch", "sizer"], default="chain")
+    ap.add_argument("--train-graphs", type=int, default=50000, help="sizer: training graphs")
+    ap.add_argument("--epochs", type=int, default=40, help="sizer: training epochs")
+    ap.add_argument("--margin", type=float, default=1.25, help="sizer: capacity margin over predictions")
+    ap.add_argument("--groups", type=int, default=8, help="sizer: LPT launch groups")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the per-graph plain launches")
     ap.add_argument("--tile", default="", help="batch: fixed tile shape 'block,items' instead of the autotuner")
     args = ap.parse_args()
@@ -531,7 +688,7 @@ def main():
 
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-        line = (run_batch if args.workload == "batch" else run_ours)(args, rank, world, local_rank)
+        line = {"batch": run_batch, "sizer": run_sizer}.get(args.workload, run_ours)(args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist
 

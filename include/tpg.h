@@ -264,10 +264,13 @@ int tpg_root_counts(tpg_cfg *g, int64_t *counts_host);
  * tpg_sizer_train       `epochs` passes over the kept batches (one Adam step
  *                       per batch, rate cosine-decayed from lr to lr/10);
  *                       loss_per_epoch (optional) receives the mean loss.
+ *                       Afterwards each target's predicted batch total is
+ *                       calibrated: the largest exact/predicted ratio over
+ *                       the kept batches scales later pre-sizing.
  * tpg_sizer_predict     per-vertex predictions pred_host[3*N] (optional) and
  *                       their expm1 sums totals_host[3] (optional).
  * tpg_sizer_presize     capacities of the handle's next graph capture from
- *                       the predicted totals times `margin` (>= 1); caps_out
+ *                       the calibrated predicted totals times `margin` (>= 1); caps_out
  *                       (optional, 7 values) receives them.
  * tpg_sizer_features    the 8 features of every vertex (x_host[8*N]).
  * tpg_sizer_get_params / tpg_sizer_set_params   FP32 master weights
@@ -275,7 +278,8 @@ int tpg_root_counts(tpg_cfg *g, int64_t *counts_host);
  * tpg_sizer_loss_grad   loss and gradient on kept batch `batch` at the
  *                       current weights, without an update.
  * tpg_sizer_batch_targets  the labels of kept batch `batch` (targets[3*N]).
- * tpg_sizer_save / tpg_sizer_load   weights and volume ratios to a file.
+ * tpg_sizer_save / tpg_sizer_load   weights, volume ratios and calibration
+ *                       to a file.
  * A tpg_sizer* is released with tpg_free.
  */
 typedef struct tpg_sizer tpg_sizer;

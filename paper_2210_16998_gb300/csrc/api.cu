@@ -253,6 +253,7 @@ struct tpg_sizer {
     AllocFns fns;
     std::vector<SizerBatch> batches;
     double r_peak = 0, r_tv0 = 0, r_tv = 0;  // largest volume ratios seen in training
+    double calib[3] = {1.0, 1.0, 1.0};      // exact / predicted totals, largest over the training batches
     unsigned long long seed = 0;
 };
 
@@ -1618,6 +1619,17 @@ int tpg_sizer_train(tpg_sizer *z, int32_t epochs, float lr, float *loss_per_epoc
         }
         if (loss_per_epoch) loss_per_epoch[ep] = (float)(sum / order.size());
     }
+    // Calibration: the network fits log volumes, so the sum of exp of its
+    // predictions tracks a median rather than a total; per target, keep the
+    // largest ratio of exact to predicted batch totals seen in training.
+    for (int t = 0; t < 3; ++t) z->calib[t] = 1.0;
+    for (auto &b : z->batches) {
+        double pred[3] = {0, 0, 0}, exact[3] = {0, 0, 0};
+        CK(sz_predict(z->net, view_of(b), nullptr, pred));
+        CK(sz_log_totals(z->net, b.T.as<float>(), b.N, exact));
+        for (int t = 0; t < 3; ++t)
+            if (pred[t] > 0) z->calib[t] = std::max(z->calib[t], exact[t] / pred[t]);
+    }
     CK(cudaStreamSynchronize(z->stream));
     return TPG_OK;
 }
@@ -1636,7 +1648,8 @@ int tpg_sizer_presize(tpg_sizer *z, tpg_cfg *g, double margin, int64_t *caps_out
     if (!(margin >= 1.0)) return TPG_EINVAL;
     double tot[3] = {0, 0, 0};
     RC(tpg_sizer_predict(z, g, nullptr, tot));
-    const double nodes = tot[0] * margin + g->N, P = tot[1] * margin + 1, V = tot[2] * margin + 1;
+    const double nodes = tot[0] * z->calib[0] * margin + g->N, P = tot[1] * z->calib[1] * margin + 1,
+                 V = tot[2] * z->calib[2] * margin + 1;
     const double rp = z->r_peak > 0 ? z->r_peak : 1.0;
     g->node_cap = (long long)nodes;
     g->lvl_cap = std::max<long long>((long long)(nodes * std::min(1.0, rp * margin)), g->N);
@@ -1707,10 +1720,10 @@ int tpg_sizer_save(const tpg_sizer *z, const char *path) {
     CK(sz_get_params(z->net, p.data()));
     FILE *f = fopen(path, "wb");
     if (!f) return TPG_EINVAL;
-    const char magic[8] = {'T', 'P', 'G', 'S', 'Z', '0', '0', '1'};
+    const char magic[8] = {'T', 'P', 'G', 'S', 'Z', '0', '0', '2'};
     const int32_t np = (int32_t)p.size();
-    const double r[3] = {z->r_peak, z->r_tv0, z->r_tv};
-    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(&np, sizeof(np), 1, f) == 1 && fwrite(r, sizeof(double), 3, f) == 3 &&
+    const double r[6] = {z->r_peak, z->r_tv0, z->r_tv, z->calib[0], z->calib[1], z->calib[2]};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(&np, sizeof(np), 1, f) == 1 && fwrite(r, sizeof(double), 6, f) == 6 &&
               fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
     ok = (fclose(f) == 0) && ok;
     return ok ? TPG_OK : TPG_EINVAL;
@@ -1723,16 +1736,17 @@ int tpg_sizer_load(tpg_sizer *z, const char *path) {
     if (!f) return TPG_EINVAL;
     char magic[8];
     int32_t np = 0;
-    double r[3];
+    double r[6];
     std::vector<float> p(sz_param_count());
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "TPGSZ001", 8) == 0 && fread(&np, sizeof(np), 1, f) == 1 &&
-              np == (int32_t)p.size() && fread(r, sizeof(double), 3, f) == 3 &&
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "TPGSZ002", 8) == 0 && fread(&np, sizeof(np), 1, f) == 1 &&
+              np == (int32_t)p.size() && fread(r, sizeof(double), 6, f) == 6 &&
               fread(p.data(), sizeof(float), p.size(), f) == p.size();
     fclose(f);
     if (!ok) return TPG_EINVAL;
     z->r_peak = r[0];
     z->r_tv0 = r[1];
     z->r_tv = r[2];
+    for (int t = 0; t < 3; ++t) z->calib[t] = r[3 + t];
     return cuda_err(sz_set_params(z->net, p.data()));
 }
 

@@ -154,6 +154,7 @@ cudaError_t sz_forward(SizerNet *n, const SzGraph &b);
 cudaError_t sz_loss_backward(SizerNet *n, const SzGraph &b, double *loss_host);
 cudaError_t sz_adam_step(SizerNet *n, float lr);
 cudaError_t sz_predict(SizerNet *n, const SzGraph &b, float *Y_host, double *totals_host);
+cudaError_t sz_log_totals(SizerNet *n, const float *Y, long long N, double *totals_host);
 // device allocator of the library (api.cu)
 void *lib_dev_alloc(size_t bytes, cudaStream_t s);
 void lib_dev_free(void *p, cudaStream_t s);

@@ -614,6 +614,16 @@ cudaError_t sz_adam_step(SizerNet *n, float lr) {
     return cudaGetLastError();
 }
 
+// expm1 sums of a [N][3] log1p array (labels or predictions) into totals_host[3]
+cudaError_t sz_log_totals(SizerNet *n, const float *Y, long long N, double *totals_host) {
+    cudaError_t e = cudaMemsetAsync(n->tot, 0, sizeof(double) * SZ_T, n->s);
+    if (e != cudaSuccess) return e;
+    sz_sum_pred<<<grid_of(N, 256, n->num_sms), 256, 0, n->s>>>(Y, N, n->tot);
+    note_launch();
+    if ((e = cudaMemcpyAsync(totals_host, n->tot, sizeof(double) * SZ_T, cudaMemcpyDeviceToHost, n->s))) return e;
+    return cudaStreamSynchronize(n->s);
+}
+
 cudaError_t sz_predict(SizerNet *n, const SzGraph &b, float *Y_host, double *totals_host) {
     cudaError_t e = sz_forward(n, b);
     if (e != cudaSuccess) return e;
