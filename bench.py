@@ -174,6 +174,16 @@ def closed_form_check(pp):
         assert list(seq) == exp, (j, seq, exp)
 
 
+def parse_tile(text):
+    """'block,items' -> tuple, or None for the library default."""
+    if not text:
+        return None
+    v = tuple(int(x) for x in text.split(","))
+    if len(v) != 2:
+        raise SystemExit(f"--tile wants block,items, got {text!r}")
+    return v
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -186,8 +196,12 @@ def run_ours(args, rank, world, local_rank):
     rp = torch.as_tensor(cfg.row_ptr, device="cuda")
     col = torch.as_tensor(cfg.col, device="cuda")
 
+    shape = parse_tile(args.tile)
+
     def step(check=False):
         h = tpg.tpg_load_cfg_device(cfg.n, cfg.m, rp, col, cfg.entry, cfg.exit)
+        if shape:
+            tpg.tpg_set_tile_shape(h, *shape)
         pp = tpg.tpg_prime_paths(h)
         if check:
             closed_form_check(pp)
@@ -240,6 +254,8 @@ def run_ours(args, rank, world, local_rank):
 
     def e2e_step():
         h = tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=tpg.TPG_RESULT_HOST)
+        if shape:
+            tpg.tpg_set_tile_shape(h, *shape)
         pp = tpg.tpg_prime_paths(h)
         tp = tpg.tpg_test_paths(h)
         nbytes = 0
@@ -279,7 +295,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded diamond-chain CFG)",
-        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                               "tile": [stats[-1]["tile_block"], stats[-1]["tile_items"]]}),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": int(bo),
                 "steps": e2e_steps},
         "gpu_launches": int(launches),
@@ -340,7 +357,7 @@ def run_batch(args, rank, world, local_rank):
     cfgs = cfggen.batch_cfgs(4096)
     ns, rp, col, ent, ext = cfggen.concat_batch(cfgs)
     if args.tile:
-        shape, tuned = tuple(int(x) for x in args.tile.split(",")), {"fixed": args.tile}
+        shape, tuned = parse_tile(args.tile), {"fixed": args.tile}
     else:
         shape, tuned = autotune.tune()
     h = tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE)
@@ -673,7 +690,8 @@ def main():
     ap.add_argument("--margin", type=float, default=1.25, help="sizer: capacity margin over predictions")
     ap.add_argument("--groups", type=int, default=8, help="sizer: LPT launch groups")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the per-graph plain launches")
-    ap.add_argument("--tile", default="", help="batch: fixed tile shape 'block,items' instead of the autotuner")
+    ap.add_argument("--tile", default="",
+                    help="fixed frontier tile 'block,items' (batch: instead of the autotuner)")
     args = ap.parse_args()
     K_DIAMONDS = args.k
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -311,7 +311,7 @@ int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);
  * in advance, and hosts whose framework owns every allocation.  The call
  * runs the same kernels as tpg_load_cfg + tpg_prime_paths, keeps every
  * temporary in one fixed-size device array built into the library (about
- * 29 MB, held by every GPU that loads the library until the process exits),
+ * 31 MB, held by every GPU that loads the library until the process exits),
  * and writes into buffers the caller owns.  It calls no cudaMalloc,
  * cudaFree, cudaHostAlloc or other allocating routine.
  *

@@ -201,8 +201,8 @@ struct tpg_cfg {
 
     // enumeration workspace
     std::vector<DevBuf> node_segs, pp_segs;  // the arena: chains of segments
-    DevBuf tfl[2], tvis[2], levels, status, tile_ctr, ctl;
-    long long node_cap = 0, lvl_cap = 0, pp_cap = 0, status_cap = 0;
+    DevBuf tfl[2], tvis[2], tcnt[2], levels, agg, ctl;
+    long long node_cap = 0, lvl_cap = 0, pp_cap = 0;
     EnumShape shape{0, 0};
     // generic scratch
     DevBuf s_keys[2], s_refs[2], s_len, s_tmp, s_i32[3], s_i64[4];
@@ -221,13 +221,13 @@ struct tpg_cfg {
         bool ready = false;
         cudaGraphExec_t exec = nullptr;
         cudaStream_t own_stream = nullptr;
-        DevBuf seg, ppseg, tfl[2], tvis[2], status;
+        DevBuf seg, ppseg, tfl[2], tvis[2], tcnt[2];
         DevBuf lvl_pp_off, keys[2], refs[2], len, scan_tmp, pp_graph, tp_len, run_start, run_rank, tp_graph0,
             run_base, nruns, bounds0, tp_off0, tp_vert0, perm[2], keep, keep_off, keep_rank, tp_graph, counts,
             key_off, key;
         Block *pp_off = nullptr, *pp_vert = nullptr, *pp_gptr = nullptr;
         Block *tp_off = nullptr, *tp_vert = nullptr, *tp_gptr = nullptr;
-        long long seg_cap = 0, pp_cap = 0, lvl_cap = 0, status_cap = 0;
+        long long seg_cap = 0, pp_cap = 0, lvl_cap = 0;
         long long P_cap = 0, V_cap = 0, TV0_cap = 0, TV_cap = 0;
         long long kernels_per_replay = 0;
     } gp;
@@ -291,7 +291,7 @@ void release_plan(tpg_cfg *g) {
     auto &p = g->gp;
     if (p.exec) cudaGraphExecDestroy(p.exec);
     p.exec = nullptr;
-    DevBuf *all[] = {&p.seg, &p.ppseg, &p.tfl[0], &p.tfl[1], &p.tvis[0], &p.tvis[1], &p.status, &p.lvl_pp_off,
+    DevBuf *all[] = {&p.seg, &p.ppseg, &p.tfl[0], &p.tfl[1], &p.tvis[0], &p.tvis[1], &p.tcnt[0], &p.tcnt[1], &p.lvl_pp_off,
                      &p.keys[0], &p.keys[1], &p.refs[0], &p.refs[1], &p.len, &p.scan_tmp, &p.pp_graph, &p.tp_len,
                      &p.run_start, &p.run_rank, &p.tp_graph0, &p.run_base, &p.nruns, &p.bounds0, &p.tp_off0,
                      &p.tp_vert0, &p.perm[0], &p.perm[1], &p.keep, &p.keep_off, &p.keep_rank, &p.tp_graph,
@@ -313,8 +313,8 @@ void destroy_cfg(tpg_cfg *g) {
     }
     DevBuf *all[] = {&g->rp, &g->col, &g->prp, &g->pcol, &g->vgraph, &g->vbase, &g->entry, &g->exitv,
                      &g->tbl_base, &g->dist, &g->pred, &g->pre_len, &g->suf_len, &g->pre_off, &g->suf_off,
-                     &g->pre_seq, &g->suf_seq, &g->tfl[0], &g->tfl[1], &g->tvis[0], &g->tvis[1],
-                     &g->levels, &g->status, &g->tile_ctr, &g->ctl, &g->s_keys[0], &g->s_keys[1],
+                     &g->pre_seq, &g->suf_seq, &g->tfl[0], &g->tfl[1], &g->tvis[0], &g->tvis[1], &g->tcnt[0], &g->tcnt[1],
+                     &g->levels, &g->agg, &g->ctl, &g->s_keys[0], &g->s_keys[1],
                      &g->s_refs[0], &g->s_refs[1], &g->s_len, &g->s_tmp, &g->s_i32[0], &g->s_i32[1],
                      &g->s_i32[2], &g->s_i64[0], &g->s_i64[1], &g->s_i64[2], &g->s_i64[3]};
     for (DevBuf *b : all) release(g, *b);
@@ -436,13 +436,12 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h) {
 // ---------------------------------------------------------------------------
 // prime paths
 // ---------------------------------------------------------------------------
-// Fixed-size parts of the enumeration workspace (level table, tile
-// counters, control words, look-back status).
+// Fixed-size parts of the enumeration workspace (level table, control
+// words, per-block level counts).
 int alloc_fixed_workspace(tpg_cfg *g) {
     RC(ensure(g, g->levels, sizeof(LevelRec) * g->max_levels));
-    RC(ensure(g, g->tile_ctr, sizeof(int) * g->max_levels));
-    RC(ensure(g, g->ctl, 256));
-    RC(ensure(g, g->status, sizeof(unsigned long long) * g->status_cap));
+    RC(ensure(g, g->ctl, CTL_BYTES));
+    RC(ensure(g, g->agg, sizeof(long long) * ENUM_AGG_WORDS));
     return TPG_OK;
 }
 
@@ -451,6 +450,7 @@ int alloc_frontier(tpg_cfg *g) {
     for (int b = 0; b < 2; ++b) {
         RC(ensure(g, g->tfl[b], sizeof(int2) * g->lvl_cap));
         RC(ensure(g, g->tvis[b], sizeof(unsigned) * (size_t)g->W * g->lvl_cap));
+        RC(ensure(g, g->tcnt[b], sizeof(unsigned short) * g->lvl_cap));
     }
     return TPG_OK;
 }
@@ -484,19 +484,15 @@ int enumerate_levels(tpg_cfg *g) {
         g->lvl_cap = std::max<long long>(g->N, 1LL << 22);
         g->pp_cap = 1LL << 22;
     }
-    g->lvl_cap = std::min<long long>(std::max<long long>(g->lvl_cap, g->N), (long long)MAX31 - 1);
+    g->lvl_cap = round_frontier_cap(std::max<long long>(g->lvl_cap, g->N));
     g->node_cap = std::max(g->node_cap, (long long)g->N);
-    if (g->status_cap < g->node_cap / ENUM_MIN_TILE + 2LL * g->max_levels + 64)
-        g->status_cap = g->node_cap / ENUM_MIN_TILE + 2LL * g->max_levels + 64;
     RC(prepare_segments(g, g->node_segs, sizeof(int2), g->node_cap));
     RC(prepare_segments(g, g->pp_segs, sizeof(int), g->pp_cap));
     RC(alloc_frontier(g));
     RC(alloc_fixed_workspace(g));
     if (!enum_shape_supported(g->W, g->shape)) g->shape = default_enum_shape(g->W);
     CK(cudaMemsetAsync(g->levels.p, 0, sizeof(LevelRec) * g->max_levels, s));
-    CK(cudaMemsetAsync(g->status.p, 0, sizeof(unsigned long long) * g->status_cap, s));
-    CK(cudaMemsetAsync(g->tile_ctr.p, 0, sizeof(int) * g->max_levels, s));
-    CK(cudaMemsetAsync(g->ctl.p, 0, 256, s));
+    CK(cudaMemsetAsync(g->ctl.p, 0, CTL_BYTES, s));
     int start_level = 1;
     int2 *next_override = nullptr;
     float total_ms = 0.f;
@@ -514,17 +510,18 @@ int enumerate_levels(tpg_cfg *g) {
         a.tfl[1] = g->tfl[1].as<int2>();
         a.tvis[0] = g->tvis[0].as<unsigned>();
         a.tvis[1] = g->tvis[1].as<unsigned>();
+        a.tcnt[0] = g->tcnt[0].as<unsigned short>();
+        a.tcnt[1] = g->tcnt[1].as<unsigned short>();
         a.lvl_cap = g->lvl_cap;
         a.levels = g->levels.as<LevelRec>();
         a.max_levels = g->max_levels;
         a.start_level = start_level;
         a.seed_level1 = (launch == 1) ? 1 : 0;
-        a.status = g->status.as<unsigned long long>();
-        a.status_cap = g->status_cap;
-        a.tile_ctr = g->tile_ctr.as<int>();
+        a.agg = g->agg.as<long long>();
+        a.agg_cap = ENUM_AGG_WORDS;
         a.err = g->ctl.as<int>();
         a.stop_level = g->ctl.as<int>() + 1;
-        a.bar = (unsigned *)(g->ctl.as<char>() + 64);
+        a.bar = (unsigned *)(g->ctl.as<char>() + CTL_BAR_OFFSET);
         a.root_counts = g->root_counts;
         int grid = 0;
         CK(cudaEventRecord(g->ev[0], s));
@@ -545,6 +542,7 @@ int enumerate_levels(tpg_cfg *g) {
         g->stats.attempts = launch;
         const int err = g->h_small[0];
         if (err & ERR_TIMEOUT) return TPG_ETIMEOUT;
+        if (err & ERR_INVAL) return TPG_ECUDA;  // a chunk's output disagreed with its count
         if (err & (ERR_OVF_COUNT | ERR_OVF_LEVELS)) return TPG_ETOOBIG;
         if (!(err & ERR_OVERFLOW_MASK)) return TPG_OK;
         if (launch >= 64) return TPG_ENOMEM;
@@ -568,8 +566,7 @@ int enumerate_levels(tpg_cfg *g) {
                                sizeof(int *), cudaMemcpyHostToDevice, s));
         }
         if (err & ERR_OVF_LEVEL) {
-            const long long cap_new = std::min<long long>(std::max(L.children + L.children / 4, 2 * g->lvl_cap),
-                                                          (long long)MAX31 - 1);
+            const long long cap_new = round_frontier_cap(std::max(L.children + L.children / 4, 2 * g->lvl_cap));
             DevBuf nfl, nvis;
             const int b = k & 1;
             RC(ensure(g, nfl, sizeof(int2) * cap_new));
@@ -585,22 +582,15 @@ int enumerate_levels(tpg_cfg *g) {
             g->lvl_cap = cap_new;
             RC(ensure(g, g->tfl[b ^ 1], sizeof(int2) * cap_new));
             RC(ensure(g, g->tvis[b ^ 1], sizeof(unsigned) * (size_t)g->W * cap_new));
+            // count words are recomputed by the relaunch's counting pass
+            for (int c = 0; c < 2; ++c) {
+                release(g, g->tcnt[c]);
+                RC(ensure(g, g->tcnt[c], sizeof(unsigned short) * cap_new));
+            }
         }
-        if (err & ERR_OVF_STATUS) {
-            g->status_cap *= 2;
-            release(g, g->status);
-            RC(ensure(g, g->status, sizeof(unsigned long long) * g->status_cap));
-        }
-        // level k restarts its look-back from an empty status array; its
-        // per-root counts are taken again, so subtract nothing: the counting
-        // run repeats from a clean slate instead (see run_root_counts)
-        if (g->root_counts) return TPG_ENOMEM;
-        long long zero = 0;
-        CK(cudaMemsetAsync(g->status.p, 0, sizeof(unsigned long long) * g->status_cap, s));
-        CK(cudaMemcpyAsync((char *)g->levels.p + sizeof(LevelRec) * k + offsetof(LevelRec, status_base), &zero,
-                           sizeof(long long), cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(g->tile_ctr.p, 0, sizeof(int) * g->max_levels, s));
-        CK(cudaMemsetAsync(g->ctl.p, 0, 256, s));
+        // level k was stopped before any of its output (or per-root count)
+        // was written; the relaunch counts it again and carries on
+        CK(cudaMemsetAsync(g->ctl.p, 0, CTL_BYTES, s));
         CK(cudaStreamSynchronize(s));  // the host-side values above must be consumed first
         start_level = k;
     }
@@ -798,7 +788,7 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
     RC(ensure(g, g->s_i32[0], sizeof(int) * (P + 1)));         // run_start
     RC(ensure(g, g->s_i32[1], sizeof(int) * (P + 1)));         // tp_graph
     RC(ensure(g, g->s_tmp, sizeof(long long) * scan_tmp_elems(P + 1)));
-    RC(ensure(g, g->ctl, 256));
+    RC(ensure(g, g->ctl, CTL_BYTES));
     CK(cudaEventRecord(g->ev[4], s));
     CK(cudaMemsetAsync(g->ctl.p, 0, sizeof(int), s));
     long long *tp_len = g->s_i64[0].as<long long>();
@@ -946,7 +936,7 @@ int capture_plan(tpg_cfg *g) {
     // capacities: explicit ones win, otherwise the exact sizes of the last run
     const bool have_run = g->pp_valid && g->stats.simple_paths > 0;
     p.seg_cap = std::max<long long>(have_run ? g->stats.simple_paths : g->node_cap, g->N);
-    p.lvl_cap = std::max<long long>(have_run ? g->stats.peak_level_nodes : g->lvl_cap, g->N);
+    p.lvl_cap = round_frontier_cap(std::max<long long>(have_run ? g->stats.peak_level_nodes : g->lvl_cap, g->N));
     p.pp_cap = std::max<long long>(have_run ? g->stats.prime_paths : g->pp_cap, 1);
     p.P_cap = std::max<long long>(g->out_cap[0] ? g->out_cap[0] : g->stats.prime_paths, 1);
     p.V_cap = std::max<long long>(g->out_cap[1] ? g->out_cap[1] : g->stats.pp_vertices, 1);
@@ -954,7 +944,6 @@ int capture_plan(tpg_cfg *g) {
     p.TV_cap = std::max<long long>(g->out_cap[3] ? g->out_cap[3] : g->stats.tp_vertices, 1);
     if (g->out_cap[0] == 0 && !have_run) return TPG_EINVAL;  // nothing to size from
     p.pp_cap = std::max(p.pp_cap, p.P_cap);
-    p.status_cap = p.seg_cap / ENUM_MIN_TILE + 2LL * g->max_levels + 64;
     const long long Pc = p.P_cap;
     const int W = g->W;
     RC(ensure(g, p.seg, sizeof(int2) * p.seg_cap));
@@ -962,11 +951,11 @@ int capture_plan(tpg_cfg *g) {
     for (int b = 0; b < 2; ++b) {
         RC(ensure(g, p.tfl[b], sizeof(int2) * p.lvl_cap));
         RC(ensure(g, p.tvis[b], sizeof(unsigned) * (size_t)W * p.lvl_cap));
+        RC(ensure(g, p.tcnt[b], sizeof(unsigned short) * p.lvl_cap));
         RC(ensure(g, p.keys[b], sizeof(int) * Pc));
         RC(ensure(g, p.refs[b], sizeof(long long) * Pc));
         RC(ensure(g, p.perm[b], sizeof(long long) * Pc));
     }
-    RC(ensure(g, p.status, sizeof(unsigned long long) * p.status_cap));
     RC(ensure(g, p.lvl_pp_off, sizeof(long long) * (g->max_levels + 1)));
     RC(ensure(g, p.len, sizeof(long long) * Pc));
     RC(ensure(g, p.scan_tmp, sizeof(long long) * gm_scan_tmp_elems(Pc + 1)));
@@ -1010,17 +999,18 @@ int capture_plan(tpg_cfg *g) {
     a.tfl[1] = p.tfl[1].as<int2>();
     a.tvis[0] = p.tvis[0].as<unsigned>();
     a.tvis[1] = p.tvis[1].as<unsigned>();
+    a.tcnt[0] = p.tcnt[0].as<unsigned short>();
+    a.tcnt[1] = p.tcnt[1].as<unsigned short>();
     a.lvl_cap = p.lvl_cap;
     a.levels = g->levels.as<LevelRec>();
     a.max_levels = g->max_levels;
     a.start_level = 1;
     a.seed_level1 = 1;
-    a.status = p.status.as<unsigned long long>();
-    a.status_cap = p.status_cap;
-    a.tile_ctr = g->tile_ctr.as<int>();
+    a.agg = g->agg.as<long long>();
+    a.agg_cap = ENUM_AGG_WORDS;
     a.err = g->ctl.as<int>();
     a.stop_level = g->ctl.as<int>() + 1;
-    a.bar = (unsigned *)(g->ctl.as<char>() + 64);
+    a.bar = (unsigned *)(g->ctl.as<char>() + CTL_BAR_OFFSET);
 
     GmArgs m{};
     m.g = g->gd;
@@ -1076,9 +1066,7 @@ int capture_plan(tpg_cfg *g) {
     int grid = 0;
     do {
         if ((e = cudaMemsetAsync(g->levels.p, 0, sizeof(LevelRec) * g->max_levels, s))) break;
-        if ((e = cudaMemsetAsync(p.status.p, 0, sizeof(unsigned long long) * p.status_cap, s))) break;
-        if ((e = cudaMemsetAsync(g->tile_ctr.p, 0, sizeof(int) * g->max_levels, s))) break;
-        if ((e = cudaMemsetAsync(g->ctl.p, 0, 256, s))) break;
+        if ((e = cudaMemsetAsync(g->ctl.p, 0, CTL_BYTES, s))) break;
         if ((e = cudaMemsetAsync(p.counts.p, 0, sizeof(GmCounts), s))) break;
         if ((e = launch_enumerate(a, g->shape, g->num_sms, s, &grid))) break;
         if ((e = gm_enqueue_pp(m, s))) break;
@@ -1132,7 +1120,6 @@ int run_root_counts(tpg_cfg *g, DevBuf &buf) {
         g->node_cap = std::max(g->node_cap * 4, 2 * seen);
         g->lvl_cap = std::min<long long>(std::max(g->lvl_cap * 2, 2 * peak), (long long)MAX31 - 1);
         g->pp_cap = std::max(g->pp_cap * 4, 2 * pps + 1);
-        g->status_cap = 0;
     }
     return TPG_ENOMEM;
 }
@@ -1235,7 +1222,7 @@ int tpg_load_cfg_device(int32_t n, int32_t m, const int32_t *row_ptr_dev, const 
         if ((rc = ensure(g, g->vbase, sizeof(int) * 2))) break;
         if ((rc = ensure(g, g->entry, sizeof(int)))) break;
         if ((rc = ensure(g, g->exitv, sizeof(int)))) break;
-        if ((rc = ensure(g, g->ctl, 256))) break;
+        if ((rc = ensure(g, g->ctl, CTL_BYTES))) break;
         cudaStream_t s = g->stream;
         int *hs = g->h_small;
         hs[0] = entry;

@@ -14,31 +14,29 @@ enum : int {
     ERR_OVF_NODES = 1,    // persistent path arena full
     ERR_OVF_LEVEL = 2,    // ping-pong frontier full
     ERR_OVF_PP = 4,       // PP reference list full
-    ERR_OVF_STATUS = 8,   // look-back status array full
+    ERR_RESERVED_8 = 8,   // (unused)
     ERR_TIMEOUT = 16,     // a bounded wait ran out
     ERR_UNREACH = 32,     // TP: vertex not reachable / cannot reach exit
     ERR_INVAL = 64,       // device-side validation failed
     ERR_OVF_LEVELS = 128, // more levels than the level table holds
     ERR_OVF_COUNT = 256,  // a level count passed 2^31 - 1
 };
-constexpr int ERR_OVERFLOW_MASK = ERR_OVF_NODES | ERR_OVF_LEVEL | ERR_OVF_PP | ERR_OVF_STATUS;
+constexpr int ERR_OVERFLOW_MASK = ERR_OVF_NODES | ERR_OVF_LEVEL | ERR_OVF_PP;
 
 // wall-clock limit of every device-side spin (nanoseconds)
 constexpr unsigned long long SPIN_LIMIT_NS = 4ull * 1000 * 1000 * 1000;
 
 // One frontier level of the path arena.  The arena is a chain of segments;
 // a level lives inside one segment, so a level is addressed by a pointer.
-// Written by the last tile of the previous level (nodes, count, pp,
-// status_base) and by the last tile of this level (pp_count, children).
-// 64 bytes.
+// Written while the previous level is processed (nodes, count, pp) and when
+// this level's totals are known (pp_count, children).  64 bytes.
 struct LevelRec {
     int2 *nodes;            // the level's first node {last vertex, parent index}
     long long count;        // nodes in the level
     int *pp;                // the level's first PP reference
     long long pp_count;     // PPs found in the level
-    long long status_base;  // first look-back status word of the level
     long long children;     // nodes of the next level (exact, also on overflow)
-    long long pad[2];
+    long long pad[3];
 };
 
 // Device view of one handle's graph(s): the union of all graphs with global
@@ -116,79 +114,58 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
     return s_ok != 0;
 }
 
-// ---------------------------------------------------------------------------
-// look-back status words: flag(2) | a(31) | b(31), values saturate at 2^31-1
-// ---------------------------------------------------------------------------
-constexpr unsigned long long ST_AGG = 1ull, ST_PRE = 2ull;
+// Grid-wide barrier with tree arrival: a block arrives at one of
+// BAR_GROUPS group counters; the last block of a group arrives at the top
+// counter; the last group flips the generation that everyone else waits on.
+// bar[0] = top count, bar[1] = generation, bar[2 .. 2 + BAR_GROUPS) = group
+// counts (all zero at launch; each counter is reset by its last arrival).
+// Arrivals on one address are serialised by the L2, so splitting them over
+// groups shortens the barrier from ~G to ~G/BAR_GROUPS + BAR_GROUPS steps.
+// Every wait is bounded by SPIN_LIMIT_NS (ERR_TIMEOUT, false on expiry).
+constexpr int BAR_GROUPS = 32;
+constexpr int BAR_WORDS = 2 + BAR_GROUPS;
+__device__ __forceinline__ bool grid_barrier_tree(unsigned *bar, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned G = gridDim.x;
+        const unsigned grp = blockIdx.x % BAR_GROUPS;
+        const unsigned gsize = (G - grp + BAR_GROUPS - 1) / BAR_GROUPS;
+        const unsigned ngroups = G < (unsigned)BAR_GROUPS ? G : (unsigned)BAR_GROUPS;
+        const unsigned gen = ld_acquire_u32(bar + 1);
+        __threadfence();
+        bool released = false;
+        if (atomicAdd(bar + 2 + grp, 1u) == gsize - 1) {
+            atomicExch(bar + 2 + grp, 0u);
+            __threadfence();
+            if (atomicAdd(bar, 1u) == ngroups - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+                released = true;
+            }
+        }
+        if (!released) {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(bar + 1) == gen) {
+                __nanosleep(64);
+                if (global_ns() - t0 > SPIN_LIMIT_NS) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// counts of one level saturate here (int32 path indices)
 constexpr unsigned long long MAX31 = (1ull << 31) - 1;
-
-__device__ __forceinline__ unsigned long long st_pack(unsigned long long flag, unsigned long long a,
-                                                      unsigned long long b) {
-    a = a > MAX31 ? MAX31 : a;
-    b = b > MAX31 ? MAX31 : b;
-    return (flag << 62) | (a << 31) | b;
-}
-__device__ __forceinline__ unsigned long long st_flag(unsigned long long s) { return s >> 62; }
-__device__ __forceinline__ unsigned long long st_a(unsigned long long s) { return (s >> 31) & MAX31; }
-__device__ __forceinline__ unsigned long long st_b(unsigned long long s) { return s & MAX31; }
-
-// Decoupled look-back (single-pass prefix) of a tile's pair aggregate
-// (agg_a, agg_b); run by the FIRST WARP of the block.  Returns the exclusive
-// prefix of the tile in (pa, pb) on every lane of warp 0.  status[] must be
-// zero before the first tile of the scan publishes.  Tiles are claimed in
-// increasing order by running blocks, so every predecessor is resident or
-// finished and each wait ends; the wait is still bounded.
-__device__ __forceinline__ void lookback_pair(unsigned long long *status, long long tile,
-                                              unsigned long long agg_a, unsigned long long agg_b,
-                                              unsigned long long &pa, unsigned long long &pb,
-                                              int *err) {
-    const int lane = threadIdx.x & 31;
-    pa = 0;
-    pb = 0;
-    if (tile == 0) {
-        if (lane == 0) st_relaxed_u64(status, st_pack(ST_PRE, agg_a, agg_b));
-        return;
-    }
-    if (lane == 0) st_relaxed_u64(status + tile, st_pack(ST_AGG, agg_a, agg_b));
-    long long j = tile - 1;
-    unsigned long long t0 = global_ns();
-    bool timed_out = false;
-    while (true) {
-        long long idx = j - lane;
-        unsigned long long s = (idx >= 0) ? ld_relaxed_u64(status + idx) : st_pack(ST_PRE, 0, 0);
-        while (true) {
-            bool pending = st_flag(s) == 0;
-            if (!__any_sync(0xffffffffu, pending)) break;
-            if (pending) {
-                __nanosleep(32);
-                s = ld_relaxed_u64(status + idx);
-            }
-            bool late = global_ns() - t0 > SPIN_LIMIT_NS;
-            if (__shfl_sync(0xffffffffu, late, 0)) {
-                timed_out = true;
-                break;
-            }
-        }
-        if (timed_out) {
-            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
-            break;
-        }
-        unsigned pre_mask = __ballot_sync(0xffffffffu, st_flag(s) == ST_PRE);
-        int stop = pre_mask ? (__ffs(pre_mask) - 1) : 31;
-        unsigned long long va = (lane <= stop) ? st_a(s) : 0ull;
-        unsigned long long vb = (lane <= stop) ? st_b(s) : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            va += __shfl_xor_sync(0xffffffffu, va, o);
-            vb += __shfl_xor_sync(0xffffffffu, vb, o);
-        }
-        pa += va;
-        pb += vb;
-        if (pre_mask) break;
-        j -= 32;
-    }
-    if (lane == 0) st_relaxed_u64(status + tile, st_pack(ST_PRE, pa + agg_a, pb + agg_b));
-}
 
 // Block-wide exclusive scan of two 32-bit counters packed as (a << 32 | b);
 // the per-block sums must stay below 2^32.  Returns the exclusive prefix and

@@ -12,7 +12,17 @@ namespace tpg {
 extern std::atomic<long long> g_kernel_launches;
 inline void note_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
-constexpr int ENUM_MIN_TILE = 128;  // smallest tile (status words are sized for it)
+// per-chunk level counts of the frontier launch: 3 rotating slots of
+// {children, PPs} per warp and per block; the buffer holds ENUM_AGG_WORDS
+// int64 values, enough for grids of up to 8192 blocks and 16384 warps
+constexpr long long ENUM_AGG_WORDS = 3 * (2 * 16384 + 2 * 8192);
+// frontier count word: children (bits 0-12, at most TPG_MAX_N) and PP flag
+constexpr unsigned CNT_MASK = 0x1fffu;
+constexpr unsigned CNT_PP = 0x8000u;
+// control block of a launch (err, stop_level, ...); the frontier's grid
+// barrier lives at CTL_BAR_OFFSET, other cooperative kernels use offset 128
+constexpr int CTL_BYTES = 512;
+constexpr int CTL_BAR_OFFSET = 256;
 
 struct EnumArgs {
     GraphDev g;
@@ -23,17 +33,17 @@ struct EnumArgs {
     long long pp_seg_cap;
     int2 *tfl[2];            // ping-pong {first, last}
     unsigned *tvis[2];       // ping-pong bitsets, W word-arrays of lvl_cap each
+    unsigned short *tcnt[2]; // ping-pong count words (children | PP flag)
     long long lvl_cap;
     LevelRec *levels;        // [max_levels]
     int max_levels;
     int start_level;         // first level processed by this launch
     int seed_level1;         // 1 on a fresh run: level 1 is written first (never on a resume)
-    unsigned long long *status;  // look-back status words (zeroed)
-    long long status_cap;
-    int *tile_ctr;           // [max_levels] (zeroed from start_level on)
+    long long *agg;          // per-block level counts (no initialisation needed)
+    long long agg_cap;       // int64 values in agg (3 * (2 * warps + 2 * blocks) at least)
     int *err;                // error flags (zeroed)
     int *stop_level;         // level whose next level did not fit (written with the flags)
-    unsigned *bar;           // grid barrier {count, generation} (zeroed)
+    unsigned *bar;           // tree grid barrier, BAR_WORDS words (zeroed)
     unsigned long long *root_counts;  // optional [3*N]: per first vertex, simple paths, PPs, PP vertices
 };
 
@@ -45,7 +55,12 @@ struct EnumShape {
 int bitset_words_supported(int maxn);
 bool enum_shape_supported(int W, EnumShape shape);
 EnumShape default_enum_shape(int W);
+// level capacity of the ping-pong frontier: a multiple of 2048 paths (tiles
+// and bulk copies stay 16-byte aligned), at least x, below 2^31 - 1
+long long round_frontier_cap(long long x);
 cudaError_t launch_enumerate(const EnumArgs &args, EnumShape shape, int num_sms, cudaStream_t s, int *grid_out);
+// level 1 of a fresh run (one path per vertex)
+cudaError_t launch_seed_level1(const EnumArgs &args, cudaStream_t s);
 // copy the first `count` frontier records to buffers of another capacity
 cudaError_t relayout_frontier(const int2 *fl_old, const unsigned *vis_old, long long cap_old, int2 *fl_new,
                               unsigned *vis_new, long long cap_new, long long count, int W, cudaStream_t s);

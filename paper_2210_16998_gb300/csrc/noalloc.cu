@@ -11,7 +11,7 @@
 // ordering buffers) lives in one file-scope __device__ array of fixed size,
 // and the results go to buffers the caller already owns.
 //
-// The array (NA_SCRATCH_BYTES, about 29 MB) is part of the library image:
+// The array (NA_SCRATCH_BYTES, about 31 MB) is part of the library image:
 // every GPU that loads the library keeps it until the process exits.  All
 // calls share it and it keeps the last call's contents, so each call clears
 // what has to start at zero; two calls whose work overlaps on the GPU (for
@@ -37,8 +37,8 @@ constexpr int NA_MAX_LEVELS = NA_MAXN + 4;
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NaLayout {
-    size_t prp, pcol, indeg, scanbuf, scantmp, vbase, levels, tile, ctl, nodes, tfl0, tfl1, tvis0, tvis1, pprefs,
-        status, keys0, keys1, refs0, refs1, len, ltmp, total;
+    size_t prp, pcol, indeg, scanbuf, scantmp, vbase, levels, ctl, nodes, tfl0, tfl1, tvis0, tvis1, tcnt0, tcnt1, pprefs,
+        agg, keys0, keys1, refs0, refs1, len, ltmp, total;
 };
 
 constexpr NaLayout na_layout() {
@@ -51,15 +51,16 @@ constexpr NaLayout na_layout() {
     L.scantmp = o; o = align256(o + sizeof(long long) * 64);
     L.vbase = o;   o = align256(o + sizeof(int) * 2);
     L.levels = o;  o = align256(o + sizeof(LevelRec) * NA_MAX_LEVELS);
-    L.tile = o;    o = align256(o + sizeof(int) * NA_MAX_LEVELS);
-    L.ctl = o;     o = align256(o + 256);
+    L.ctl = o;     o = align256(o + CTL_BYTES);
     L.nodes = o;   o = align256(o + sizeof(int2) * NA_NODE_CAP);
     L.tfl0 = o;    o = align256(o + sizeof(int2) * NA_LVL_CAP);
     L.tfl1 = o;    o = align256(o + sizeof(int2) * NA_LVL_CAP);
     L.tvis0 = o;   o = align256(o + sizeof(unsigned) * NA_W * NA_LVL_CAP);
     L.tvis1 = o;   o = align256(o + sizeof(unsigned) * NA_W * NA_LVL_CAP);
+    L.tcnt0 = o;   o = align256(o + sizeof(unsigned short) * NA_LVL_CAP);
+    L.tcnt1 = o;   o = align256(o + sizeof(unsigned short) * NA_LVL_CAP);
     L.pprefs = o;  o = align256(o + sizeof(int) * NA_PP_CAP);
-    L.status = o;  o = align256(o + sizeof(unsigned long long) * (NA_NODE_CAP / NA_TILE + 2 * NA_MAX_LEVELS + 64));
+    L.agg = o;     o = align256(o + sizeof(long long) * ENUM_AGG_WORDS);
     L.keys0 = o;   o = align256(o + sizeof(int) * NA_PP_CAP);
     L.keys1 = o;   o = align256(o + sizeof(int) * NA_PP_CAP);
     L.refs0 = o;   o = align256(o + sizeof(long long) * NA_PP_CAP);
@@ -72,7 +73,7 @@ constexpr NaLayout na_layout() {
 
 constexpr NaLayout NA = na_layout();
 constexpr size_t NA_SCRATCH_BYTES = NA.total;
-static_assert(NA_SCRATCH_BYTES < (30u << 20), "no-allocation scratch stays under 30 MB");
+static_assert(NA_SCRATCH_BYTES < (32u << 20), "no-allocation scratch stays under 32 MB");
 
 // the scratch array shared by every call on a device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_SCRATCH_BYTES];
@@ -156,7 +157,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
 
     // 1. validate the CSR on the device
     int h_err = 0;
-    NA_CK(cudaMemsetAsync(err, 0, 256, s));
+    NA_CK(cudaMemsetAsync(err, 0, CTL_BYTES, s));
     na_validate_kernel<<<1, 128, 0, s>>>(row_ptr_dev, col_dev, n, m, err);
     note_launch();
     NA_CK(cudaGetLastError());
@@ -192,6 +193,8 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     a.tfl[1] = (int2 *)(S + NA.tfl1);
     a.tvis[0] = (unsigned *)(S + NA.tvis0);
     a.tvis[1] = (unsigned *)(S + NA.tvis1);
+    a.tcnt[0] = (unsigned short *)(S + NA.tcnt0);
+    a.tcnt[1] = (unsigned short *)(S + NA.tcnt1);
     a.lvl_cap = NA_LVL_CAP;
     a.pp_seg = (int *)(S + NA.pprefs);
     a.pp_seg_cap = NA_PP_CAP;
@@ -199,16 +202,13 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     a.max_levels = n + 4;
     a.start_level = 1;
     a.seed_level1 = 1;
-    a.status = (unsigned long long *)(S + NA.status);
-    a.status_cap = NA_NODE_CAP / NA_TILE + 2 * NA_MAX_LEVELS + 64;
-    a.tile_ctr = (int *)(S + NA.tile);
+    a.agg = (long long *)(S + NA.agg);
+    a.agg_cap = ENUM_AGG_WORDS;
     a.err = err;
     a.stop_level = err + 1;
-    a.bar = (unsigned *)(S + NA.ctl + 64);
+    a.bar = (unsigned *)(S + NA.ctl + CTL_BAR_OFFSET);
     NA_CK(cudaMemsetAsync(a.levels, 0, sizeof(LevelRec) * NA_MAX_LEVELS, s));
-    NA_CK(cudaMemsetAsync(a.status, 0, sizeof(unsigned long long) * a.status_cap, s));
-    NA_CK(cudaMemsetAsync(a.tile_ctr, 0, sizeof(int) * NA_MAX_LEVELS, s));
-    NA_CK(cudaMemsetAsync(err, 0, 256, s));
+    NA_CK(cudaMemsetAsync(err, 0, CTL_BYTES, s));
     int num_sms = 1, dev = 0, grid = 0;
     NA_CK(cudaGetDevice(&dev));
     NA_CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -218,6 +218,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     NA_CK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
     if (h_err & ERR_TIMEOUT) return TPG_ETIMEOUT;
+    if (h_err & ERR_INVAL) return TPG_ECUDA;
     if (h_err & (ERR_OVERFLOW_MASK | ERR_OVF_COUNT | ERR_OVF_LEVELS)) return TPG_ETOOBIG;
 
     // 4. sizes; the caller's buffers must hold them
