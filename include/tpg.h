@@ -188,8 +188,8 @@ int tpg_set_allocator(tpg_alloc_fn alloc, tpg_release_fn release, void *ctx);
 
 /*
  * Tile shape of the frontier kernel for this handle: `block` threads per
- * block, `items` paths per thread.  Supported: block 128 or 256 with items
- * 1, 2 or 4, block 512 with items 1 or 2 (bitsets of <= 8 words); block 256
+ * block, `items` paths per thread.  Supported: block 256 with items 1, 2
+ * or 4, block 512 with items 1 or 2 (bitsets of <= 8 words); block 256
  * items 1 for wider bitsets.  TPG_EINVAL otherwise.  Results never depend
  * on the shape; the autotuner uses this.
  */
@@ -311,7 +311,7 @@ int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);
  * in advance, and hosts whose framework owns every allocation.  The call
  * runs the same kernels as tpg_load_cfg + tpg_prime_paths, keeps every
  * temporary in one fixed-size device array built into the library (about
- * 31 MB, held by every GPU that loads the library until the process exits),
+ * 33 MB, held by every GPU that loads the library until the process exits),
  * and writes into buffers the caller owns.  It calls no cudaMalloc,
  * cudaFree, cudaHostAlloc or other allocating routine.
  *

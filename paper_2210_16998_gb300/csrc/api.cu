@@ -480,9 +480,14 @@ int prepare_segments(tpg_cfg *g, std::vector<DevBuf> &segs, size_t elem, long lo
 int enumerate_levels(tpg_cfg *g) {
     cudaStream_t s = g->stream;
     if (g->node_cap == 0) {
-        g->node_cap = std::max<long long>(4LL * g->N, 1LL << 24);
-        g->lvl_cap = std::max<long long>(g->N, 1LL << 22);
-        g->pp_cap = 1LL << 22;
+        // defaults sized for a GPU with hundreds of GB of HBM, so that most
+        // inputs finish in one launch: 1 GiB of arena (2^27 paths), a
+        // frontier of up to 2^24 paths per level within 1.5 GiB for both
+        // ping-pong halves, 2^24 PP references; larger needs grow the arena
+        const long long per_path = (long long)(sizeof(int2) + 4 * g->W + sizeof(unsigned short));
+        g->node_cap = std::max<long long>(4LL * g->N, 1LL << 27);
+        g->lvl_cap = std::max<long long>(g->N, std::min<long long>(1LL << 24, (3LL << 29) / (2 * per_path)));
+        g->pp_cap = 1LL << 24;
     }
     g->lvl_cap = round_frontier_cap(std::max<long long>(g->lvl_cap, g->N));
     g->node_cap = std::max(g->node_cap, (long long)g->N);

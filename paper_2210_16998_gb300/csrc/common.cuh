@@ -122,9 +122,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
 // Arrivals on one address are serialised by the L2, so splitting them over
 // groups shortens the barrier from ~G to ~G/BAR_GROUPS + BAR_GROUPS steps.
 // Every wait is bounded by SPIN_LIMIT_NS (ERR_TIMEOUT, false on expiry).
+// Also false, on every block alike, if an error flag in `stop` was raised
+// before the barrier.
 constexpr int BAR_GROUPS = 32;
 constexpr int BAR_WORDS = 2 + BAR_GROUPS;
-__device__ __forceinline__ bool grid_barrier_tree(unsigned *bar, int *err) {
+__device__ __forceinline__ bool grid_barrier_tree(unsigned *bar, int *err, int stop) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -158,6 +160,7 @@ __device__ __forceinline__ bool grid_barrier_tree(unsigned *bar, int *err) {
             }
         }
         __threadfence();
+        if (__ldcg(err) & stop) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

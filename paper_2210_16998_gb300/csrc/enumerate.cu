@@ -70,23 +70,33 @@ __global__ void init_level1_kernel(EnumArgs a) {
     }
 }
 
-// What a path of level k does next (Alg. 3 extension and prune steps): its
-// number of children (simple one-vertex extensions, closing arcs included)
-// and whether it is prime, packed as a count word (CNT_MASK | CNT_PP).  A
-// closed cycle (k >= 2, first == last) is never extended and always prime.
-// `extra` is a vertex on the path that is not in `vis` (-1 for none): a child
-// is evaluated as its parent's bitset plus the child's last vertex.
+// What a path of level k does next (Alg. 3 extension and prune steps): which
+// successors of its last vertex extend it (simple one-vertex extensions,
+// closing arcs included) and whether it is prime, packed as a count word
+// (see CNT_BITS).  A closed cycle (k >= 2, first == last) is never extended
+// and always prime.  `extra` is a vertex on the path that is not in `vis`
+// (-1 for none): a child is evaluated as its parent's bitset plus the
+// child's last vertex.
 template <int W>
 __device__ __forceinline__ unsigned eval_path(const GraphDev &g, int k, int first, int last, int vb,
                                               const unsigned (&vis)[W], int extra) {
     if (k >= 2 && first == last) return CNT_PP;
     const int e0 = __ldg(g.rp + last), e1 = __ldg(g.rp + last + 1);
-    unsigned c = 0;
-    for (int e = e0; e < e1; ++e) {
-        const int w = __ldg(g.col + e);
-        if (w == first || (w != extra && !test_bit<W>(vis, w - vb))) ++c;
+    if (e1 - e0 <= CNT_MASK_DEG) {
+        unsigned m = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int w = __ldg(g.col + e);
+            if (w == first || (w != extra && !test_bit<W>(vis, w - vb))) m |= 1u << (e - e0);
+        }
+        if (m) return m;
+    } else {
+        unsigned c = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int w = __ldg(g.col + e);
+            if (w == first || (w != extra && !test_bit<W>(vis, w - vb))) ++c;
+        }
+        if (c) return CNT_WIDE | c;
     }
-    if (c) return c;
     // right-maximal; left-maximal iff every predecessor u of the first vertex
     // is on the path and is not its last vertex (u.p would otherwise be simple)
     const int p0 = __ldg(g.prp + first), p1 = __ldg(g.prp + first + 1);
@@ -97,56 +107,47 @@ __device__ __forceinline__ unsigned eval_path(const GraphDev &g, int k, int firs
     return CNT_PP;
 }
 
-// paths per warp of a level of `count` paths: ceil(count / GW) rounded up to
-// a multiple of 32; warp w owns [w * chunk, (w + 1) * chunk) clipped to count
-__device__ __forceinline__ int warp_chunk(long long count, int GW) {
-    const long long q = (count + GW - 1) / GW;
+constexpr int CPG = ENUM_CPG;  // chunks per block: a level is cut into CPG * blocks chunks
+
+// paths per chunk of a level of `count` paths cut into nchk chunks:
+// ceil(count / nchk) rounded up to a multiple of 32
+__device__ __forceinline__ int level_chunk(long long count, int nchk) {
+    const long long q = (count + nchk - 1) / nchk;
     return (int)((q + 31) & ~31ll);
 }
 
-template <int BLOCK>
-__device__ __forceinline__ void block_sum4(long long (&v)[4]) {
-    __shared__ long long s_part[4][BLOCK / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-        if (lane == 0) s_part[i][wid] = v[i];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        long long t = 0;
-#pragma unroll
-        for (int w = 0; w < BLOCK / 32; ++w) t += s_part[i][w];
-        v[i] = t;
-    }
-    __syncthreads();
-}
-
-// Per-chunk counts of one level: slot s holds, for every warp chunk and for
-// every block (the sum of its warps' chunks), the children and the PPs the
-// chunk produces.
+// Per-chunk counts of one level.  Slot s holds, for every chunk and for every
+// group of CPG consecutive chunks, the children and the PPs it produces.
 struct AggSlots {
     long long *base;
-    int GW, G;
-    __device__ long long *wc(int s) const { return base + s * (2ll * GW + 2ll * G); }
-    __device__ long long *wp(int s) const { return wc(s) + GW; }
-    __device__ long long *bc(int s) const { return wc(s) + 2ll * GW; }
-    __device__ long long *bp(int s) const { return wc(s) + 2ll * GW + G; }
+    int NC, G;  // chunks, groups (= blocks)
+    __device__ long long *cc(int s) const { return base + s * (2ll * NC + 2ll * G); }
+    __device__ long long *cp(int s) const { return cc(s) + NC; }
+    __device__ long long *gc(int s) const { return cc(s) + 2ll * NC; }
+    __device__ long long *gp(int s) const { return cc(s) + 2ll * NC + G; }
 };
 
-// Add (c, p) to warp chunk `own` of slot s (and to its block).  Lanes with
-// nothing to add pass own = -1.  One set of atomics per warp when all lanes
-// share one owner (the usual case), per lane otherwise.
-template <int NW>
+__device__ __forceinline__ void add_counts(const AggSlots &A, int s, int own, unsigned long long c,
+                                           unsigned long long p) {
+    if (c) {
+        atomicAdd((unsigned long long *)A.cc(s) + own, c);
+        atomicAdd((unsigned long long *)A.gc(s) + own / CPG, c);
+    }
+    if (p) {
+        atomicAdd((unsigned long long *)A.cp(s) + own, p);
+        atomicAdd((unsigned long long *)A.gp(s) + own / CPG, p);
+    }
+}
+
+// Add (c, p) to chunk `own` of slot s (and to its group).  Lanes with nothing
+// to add pass own = -1.  One set of atomics per warp when all lanes share one
+// owner (the usual case), per lane otherwise.
 __device__ __forceinline__ void flush_counts(const AggSlots &A, int s, int own, unsigned long long c,
                                              unsigned long long p) {
-    const unsigned have = __ballot_sync(0xffffffffu, own >= 0 && (c | p));
+    const bool mine = own >= 0 && (c | p);
+    const unsigned have = __ballot_sync(0xffffffffu, mine);
     if (!have) return;
     const int own0 = __shfl_sync(0xffffffffu, own, __ffs(have) - 1);
-    const bool mine = own >= 0 && (c | p);
     if (__all_sync(0xffffffffu, !mine || own == own0)) {
         if (!mine) c = p = 0;
 #pragma unroll
@@ -154,91 +155,88 @@ __device__ __forceinline__ void flush_counts(const AggSlots &A, int s, int own, 
             c += __shfl_xor_sync(0xffffffffu, c, o);
             p += __shfl_xor_sync(0xffffffffu, p, o);
         }
-        if ((threadIdx.x & 31) == 0) {
-            if (c) {
-                atomicAdd((unsigned long long *)A.wc(s) + own0, c);
-                atomicAdd((unsigned long long *)A.bc(s) + own0 / NW, c);
-            }
-            if (p) {
-                atomicAdd((unsigned long long *)A.wp(s) + own0, p);
-                atomicAdd((unsigned long long *)A.bp(s) + own0 / NW, p);
-            }
-        }
+        if ((threadIdx.x & 31) == 0) add_counts(A, s, own0, c, p);
     } else if (mine) {
-        if (c) {
-            atomicAdd((unsigned long long *)A.wc(s) + own, c);
-            atomicAdd((unsigned long long *)A.bc(s) + own / NW, c);
-        }
-        if (p) {
-            atomicAdd((unsigned long long *)A.wp(s) + own, p);
-            atomicAdd((unsigned long long *)A.bp(s) + own / NW, p);
-        }
+        add_counts(A, s, own, c, p);
     }
 }
 
-// One persistent cooperative launch walks the levels.  Level k is split into
-// GW equal contiguous chunks, one per warp.  Before a warp touches level k it
-// knows how many children and PPs every chunk produces: the count word of
-// each path of level k (tcnt) was computed when that path was written, and
-// the writers added it to the entry of the chunk that owns the path.  After
-// one grid barrier per level, a block sums the block entries before its own
-// and a warp the warp entries before its own in the block: that is the
-// warp's exact offset in level k+1 and in the PP list.  The warp then walks
-// its chunk in tiles of 32 * ITEMS paths (lane l owns paths j*32 + l, so
-// every load is coalesced) with warp-level scans only -- no block-wide
-// synchronisation inside a level -- and writes every child together with
-// the child's own count word.  Each path is read once and written once.
+// One persistent cooperative launch walks the levels.  Level k is cut into
+// NC = CPG * G equal contiguous chunks; warp w of the GW warps takes chunks
+// w, w + GW, w + 2GW, ..., so each warp's work is spread over the whole level
+// and a region of costly paths is shared by many warps.  Any chunk's
+// offsets in level k+1 and in the PP list are known before the level starts:
+// the count word of each path of level k (tcnt) was computed when that path
+// was written, and the writer added it to the entry of the chunk that owns
+// the path and to that chunk's group (CPG consecutive chunks).  After one
+// grid barrier per level each block scans the G group totals into shared
+// memory; a warp that claims chunk c adds the entries of the chunks before c
+// in its group.  The warp walks the chunk in tiles of 32 * ITEMS paths (lane
+// l owns paths j*32 + l, so every load is coalesced) with warp-level scans
+// only, and writes every child together with the child's own count word.
+// Each path is read once and written once.
 //
 // Slots rotate: level k reads slot k%3, accumulates into slot (k+1)%3, and
-// each warp / block clears its own entries of slot (k+2)%3, which nobody
-// reads or accumulates until after the next barrier.  The first level of a
-// launch (level 1 of a fresh run, or the level a resume starts at) is
-// counted by a separate pass.
+// each block clears its group's entries of slot (k+2)%3, which nobody reads
+// or accumulates until after the next barrier.  The first level of a launch
+// (level 1 of a fresh run, or the level a resume starts at) is counted by a
+// separate pass with a static chunk assignment.
 template <int W, int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_kernel(EnumArgs a) {
     constexpr int NW = BLOCK / 32;
+    constexpr int F = CPG / NW;      // chunks per warp in the counting pass
     constexpr int WT = 32 * ITEMS;  // paths per warp tile
+    static_assert(CPG % NW == 0, "a block's warps split its chunks evenly");
+    extern __shared__ long long s_gpre[];  // [2 * G]: exclusive group prefixes (children, PPs)
     __shared__ long long s_wsum[NW][2];
-    __shared__ long long s_lvl[4];
+    __shared__ long long s_tot[2];
     const GraphDev &g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int G = gridDim.x, b = blockIdx.x, GW = G * NW, gw = b * NW + wid;
+    const int G = gridDim.x, b = blockIdx.x, NC = CPG * G;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const AggSlots A{a.agg, GW, G};
+    const AggSlots A{a.agg, NC, G};
 
     // ---- counting pass over the first level of this launch ----
     {
         const int k = a.start_level;
         const long long count = __ldcg(&a.levels[k].count);
-        const int chunk = warp_chunk(count, GW);
-        const int lo = (int)min((long long)gw * chunk, count), hi = (int)min((long long)lo + chunk, count);
+        const int chunk = level_chunk(count, NC);
         const int2 *in_fl = a.tfl[k & 1];
         const unsigned *in_vis = a.tvis[k & 1];
         unsigned short *cnt = a.tcnt[k & 1];
-        long long c_sum = 0, p_sum = 0;
-        for (int i = lo + lane; i < hi; i += 32) {
-            const int2 fl = __ldcg(in_fl + i);
-            unsigned vis[W];
+        long long wc_sum = 0, wp_sum = 0;
+        for (int f = 0; f < F; ++f) {
+            const int c = b * CPG + wid * F + f;
+            const int lo = (int)min((long long)c * chunk, count), hi = (int)min((long long)lo + chunk, count);
+            long long c_sum = 0, p_sum = 0;
+            for (int i = lo + lane; i < hi; i += 32) {
+                const int2 fl = __ldcg(in_fl + i);
+                unsigned vis[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) vis[w] = __ldcg(in_vis + w * a.lvl_cap + i);
-            const int vb = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + fl.x)) : 0;
-            const unsigned cw = eval_path<W>(g, k, fl.x, fl.y, vb, vis, -1);
-            cnt[i] = (unsigned short)cw;
-            c_sum += cw & CNT_MASK;
-            p_sum += cw >> 15;
-        }
+                for (int w = 0; w < W; ++w) vis[w] = __ldcg(in_vis + w * a.lvl_cap + i);
+                const int vb = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + fl.x)) : 0;
+                const unsigned cw = eval_path<W>(g, k, fl.x, fl.y, vb, vis, -1);
+                cnt[i] = (unsigned short)cw;
+                c_sum += cnt_children(cw);
+                p_sum += cw >> 15;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            c_sum += __shfl_xor_sync(0xffffffffu, c_sum, o);
-            p_sum += __shfl_xor_sync(0xffffffffu, p_sum, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                c_sum += __shfl_xor_sync(0xffffffffu, c_sum, o);
+                p_sum += __shfl_xor_sync(0xffffffffu, p_sum, o);
+            }
+            if (lane == 0) {
+                A.cc(k % 3)[c] = c_sum;
+                A.cp(k % 3)[c] = p_sum;
+                A.cc((k + 1) % 3)[c] = A.cp((k + 1) % 3)[c] = 0;
+                A.cc((k + 2) % 3)[c] = A.cp((k + 2) % 3)[c] = 0;
+            }
+            wc_sum += c_sum;
+            wp_sum += p_sum;
         }
         if (lane == 0) {
-            A.wc(k % 3)[gw] = c_sum;
-            A.wp(k % 3)[gw] = p_sum;
-            A.wc((k + 1) % 3)[gw] = A.wp((k + 1) % 3)[gw] = 0;
-            A.wc((k + 2) % 3)[gw] = A.wp((k + 2) % 3)[gw] = 0;
-            s_wsum[wid][0] = c_sum;
-            s_wsum[wid][1] = p_sum;
+            s_wsum[wid][0] = wc_sum;
+            s_wsum[wid][1] = wp_sum;
         }
         __syncthreads();
         if (tid == 0) {
@@ -248,21 +246,20 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                 c += s_wsum[w][0];
                 p += s_wsum[w][1];
             }
-            A.bc(k % 3)[b] = c;
-            A.bp(k % 3)[b] = p;
-            A.bc((k + 1) % 3)[b] = A.bp((k + 1) % 3)[b] = 0;
-            A.bc((k + 2) % 3)[b] = A.bp((k + 2) % 3)[b] = 0;
+            A.gc(k % 3)[b] = c;
+            A.gp(k % 3)[b] = p;
+            A.gc((k + 1) % 3)[b] = A.gp((k + 1) % 3)[b] = 0;
+            A.gc((k + 2) % 3)[b] = A.gp((k + 2) % 3)[b] = 0;
         }
-        if (!grid_barrier_tree(a.bar, a.err)) return;
+        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
     }
 
-    for (int k = a.start_level; k + 1 < a.max_levels; ++k) {
-        if (__ldcg(a.err) & (ERR_OVERFLOW_MASK | ERR_TIMEOUT | ERR_OVF_LEVELS | ERR_OVF_COUNT | ERR_INVAL)) break;
-        const LevelRec *Lp = a.levels + k;
-        const long long count = __ldcg(&Lp->count);
-        if (count <= 0) break;
-        int2 *const lnodes = (int2 *)__ldcg((const unsigned long long *)&Lp->nodes);
-        int *const lpp = (int *)__ldcg((const unsigned long long *)&Lp->pp);
+    // the level being processed; after the first, every block derives the
+    // next level's record from the totals it computed itself
+    long long count = __ldcg(&a.levels[a.start_level].count);
+    int2 *lnodes = (int2 *)__ldcg((const unsigned long long *)&a.levels[a.start_level].nodes);
+    int *lpp = (int *)__ldcg((const unsigned long long *)&a.levels[a.start_level].pp);
+    for (int k = a.start_level; k + 1 < a.max_levels && count > 0; ++k) {
         int2 *const next = (k == a.start_level && a.next_nodes) ? a.next_nodes : lnodes + count;
         const long long next_off = next - a.seg;  // offset of the next level in the segment
         const long long pp_off = lpp - a.pp_seg;  // offset of this level's PPs in their segment
@@ -274,43 +271,32 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
         unsigned short *out_cnt = a.tcnt[(k + 1) & 1];
         const int s0 = k % 3, s1 = (k + 1) % 3, s2 = (k + 2) % 3;
 
-        // level totals and this block's offsets: sums over the block entries
+        // exclusive prefixes of the group totals, and the level totals
         {
-            long long v[4] = {0, 0, 0, 0};
-            for (int j = tid; j < G; j += BLOCK) {
-                const long long c = __ldcg(A.bc(s0) + j), p = __ldcg(A.bp(s0) + j);
-                v[0] += c;
-                v[1] += p;
-                if (j < b) {
-                    v[2] += c;
-                    v[3] += p;
-                }
+            const int per = (G + BLOCK - 1) / BLOCK, g0 = min(tid * per, G), g1 = min(g0 + per, G);
+            long long sc = 0, sp = 0;
+            for (int q = g0; q < g1; ++q) {
+                sc += __ldcg(A.gc(s0) + q);
+                sp += __ldcg(A.gp(s0) + q);
             }
-            block_sum4<BLOCK>(v);
+            long long tc, tp;
+            long long xc = block_excl_scan_i64<BLOCK>(sc, tc);
+            long long xp = block_excl_scan_i64<BLOCK>(sp, tp);
+            for (int q = g0; q < g1; ++q) {
+                s_gpre[q] = xc;
+                s_gpre[G + q] = xp;
+                xc += __ldcg(A.gc(s0) + q);
+                xp += __ldcg(A.gp(s0) + q);
+            }
             if (tid == 0) {
-                s_lvl[0] = v[0];
-                s_lvl[1] = v[1];
-                s_lvl[2] = v[2];
-                s_lvl[3] = v[3];
-                A.bc(s2)[b] = A.bp(s2)[b] = 0;
+                s_tot[0] = tc;
+                s_tot[1] = tp;
+                A.gc(s2)[b] = A.gp(s2)[b] = 0;
             }
+            if (tid < CPG) A.cc(s2)[b * CPG + tid] = A.cp(s2)[b * CPG + tid] = 0;
             __syncthreads();
         }
-        const long long C = s_lvl[0], P = s_lvl[1];
-        // this warp's offsets: the block's plus the warp entries before it
-        long long wc = 0, wpv = 0;
-        if (lane < NW) {
-            wc = __ldcg(A.wc(s0) + b * NW + lane);
-            wpv = __ldcg(A.wp(s0) + b * NW + lane);
-        }
-        const long long own_c = __shfl_sync(0xffffffffu, wc, wid), own_p = __shfl_sync(0xffffffffu, wpv, wid);
-        long long xc = lane < wid ? wc : 0, xp = lane < wid ? wpv : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            xc += __shfl_xor_sync(0xffffffffu, xc, o);
-            xp += __shfl_xor_sync(0xffffffffu, xp, o);
-        }
-        if (lane == 0) A.wc(s2)[gw] = A.wp(s2)[gw] = 0;
+        const long long C = s_tot[0], P = s_tot[1];
 
         // every block takes the same decision from the same counts
         int e = 0;
@@ -336,118 +322,164 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
         if (e) break;
 
         // all positions below fit in int32 (C, P < 2^31 - 1)
-        const int chunk = warp_chunk(count, GW);
-        const int lo = (int)min((long long)gw * chunk, count), hi = (int)min((long long)lo + chunk, count);
-        const int chunk_n = C > 0 ? warp_chunk(C, GW) : 1;  // the next level's chunk
-        const int pa = (int)(s_lvl[2] + xc), pb = (int)(s_lvl[3] + xp);
-        int pos_c = pa, pos_p = pb;
-        // next-level counts of the children this lane wrote, per owner chunk
-        int cur_own = -1;
+        const int chunk = level_chunk(count, NC);
+        const int nchk = (int)((count + chunk - 1) / chunk);  // chunks that hold paths
+        const int chunk_n = C > 0 ? level_chunk(C, NC) : 1;  // the next level's chunk
+        // next-level counts of the children this lane wrote, per owner chunk;
+        // a finished owner's counts retire and are flushed by the whole warp
+        int cur_own = -1, ret_own = -1;
         unsigned bound = 0;  // first position of the chunk after cur_own
-        unsigned long long acc_c = 0, acc_p = 0;
+        unsigned long long acc_c = 0, acc_p = 0, ret_c = 0, ret_p = 0;
 
-        for (int t0 = lo; t0 < hi; t0 += WT) {
-            int first[ITEMS], last[ITEMS];
-            unsigned cw[ITEMS];
-            unsigned vis[ITEMS][W];
-#pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const int i = t0 + j * 32 + lane;
-                if (i < hi) {
-                    const int2 fl = __ldcg(in_fl + i);
-                    first[j] = fl.x;
-                    last[j] = fl.y;
-                    cw[j] = __ldcg(in_cnt + i);
-#pragma unroll
-                    for (int w = 0; w < W; ++w) vis[j][w] = __ldcg(in_vis + w * a.lvl_cap + i);
-                } else {
-                    first[j] = -1;
-                    last[j] = 0;
-                    cw[j] = 0;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) vis[j][w] = 0u;
-                }
+        // chunk entries of the group of chunk c that precede it, and its own
+        // (lanes 0..r of the group, r = c's place in it)
+        auto load_entries = [&](int c, long long &ec, long long &ep) {
+            const int grp = c / CPG, r = c - grp * CPG;
+            ec = ep = 0;
+            if (c < nchk && lane <= r) {
+                ec = __ldcg(A.cc(s0) + grp * CPG + lane);
+                ep = __ldcg(A.cp(s0) + grp * CPG + lane);
             }
+        };
+        const int GW = G * NW, gw = b * NW + wid;
+        long long ec, ep;
+        load_entries(gw, ec, ep);
+        for (int c = gw; c < nchk; c += GW) {
+            // the next chunk's entries load while this chunk is processed
+            long long ec_next, ep_next;
+            load_entries(c + GW, ec_next, ep_next);
+            // offsets of chunk c: its group's prefix plus the chunks before it in the group
+            const int grp = c / CPG, r = c - grp * CPG;
+            const long long own_c = __shfl_sync(0xffffffffu, ec, r), own_p = __shfl_sync(0xffffffffu, ep, r);
+            long long xc = lane < r ? ec : 0, xp = lane < r ? ep : 0;
 #pragma unroll
-            for (int j = 0; j < ITEMS; ++j) {
-                const int i = t0 + j * 32 + lane;
-                const int nch = (int)(cw[j] & CNT_MASK);
-                const bool pp = (cw[j] & CNT_PP) != 0;
-                int x = nch;
+            for (int o = 16; o > 0; o >>= 1) {
+                xc += __shfl_xor_sync(0xffffffffu, xc, o);
+                xp += __shfl_xor_sync(0xffffffffu, xp, o);
+            }
+            const int pa = (int)(s_gpre[grp] + xc), pb = (int)(s_gpre[G + grp] + xp);
+            const int lo = (int)min((long long)c * chunk, count), hi = (int)min((long long)lo + chunk, count);
+            int pos_c = pa, pos_p = pb;
+
+            for (int t0 = lo; t0 < hi; t0 += WT) {
+                int first[ITEMS], last[ITEMS];
+                unsigned cw[ITEMS];
+                unsigned vis[ITEMS][W];
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                const int tot = __shfl_sync(0xffffffffu, x, 31);
-                const unsigned ppm = __ballot_sync(0xffffffffu, pp);
-                if (a.root_counts) {
-                    // per-root totals: paths arrive sorted by first vertex, so
-                    // a warp's lanes mostly share one root; one atomic per group
-                    const unsigned grp = __match_any_sync(0xffffffffu, first[j]);
-                    const unsigned c0 = __reduce_add_sync(grp, first[j] >= 0 ? 1u : 0u);
-                    const unsigned c1 = __reduce_add_sync(grp, pp ? 1u : 0u);
-                    const unsigned c2 = __reduce_add_sync(grp, pp ? (unsigned)k : 0u);
-                    if (first[j] >= 0 && lane == __ffs(grp) - 1) {
-                        unsigned long long *rc = a.root_counts + 3ll * first[j];
-                        atomicAdd(rc, (unsigned long long)c0);
-                        if (c1) atomicAdd(rc + 1, (unsigned long long)c1);
-                        if (c2) atomicAdd(rc + 2, (unsigned long long)c2);
+                for (int j = 0; j < ITEMS; ++j) {
+                    const int i = t0 + j * 32 + lane;
+                    if (i < hi) {
+                        const int2 fl = __ldcg(in_fl + i);
+                        first[j] = fl.x;
+                        last[j] = fl.y;
+                        cw[j] = __ldcg(in_cnt + i);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) vis[j][w] = __ldcg(in_vis + w * a.lvl_cap + i);
+                    } else {
+                        first[j] = -1;
+                        last[j] = 0;
+                        cw[j] = 0;
+#pragma unroll
+                        for (int w = 0; w < W; ++w) vis[j][w] = 0u;
                     }
                 }
-                if (nch > 0) {
-                    const int vb = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + first[j])) : 0;
-                    int cpos = pos_c + x - nch;
-                    const int e0 = __ldg(g.rp + last[j]), e1 = __ldg(g.rp + last[j] + 1);
-                    for (int e = e0; e < e1; ++e) {
-                        const int w = __ldg(g.col + e);
-                        const bool closes = (w == first[j]);
-                        if (!closes && test_bit<W>(vis[j], w - vb)) continue;
-                        const unsigned c2w = eval_path<W>(g, k + 1, first[j], w, vb, vis[j], w);
-                        if (cpos < C && next_off + cpos < a.seg_cap) {  // holds when the counts agree
-                            next[cpos] = make_int2(w, i);
-                            out_fl[cpos] = make_int2(first[j], w);
-                            out_cnt[cpos] = (unsigned short)c2w;
-                            if (!closes) {
-                                const int bb = w - vb;
 #pragma unroll
-                                for (int ww = 0; ww < W; ++ww)
-                                    out_vis[ww * a.lvl_cap + cpos] =
-                                        vis[j][ww] | ((ww == (bb >> 5)) ? (1u << (bb & 31)) : 0u);
-                            }
-                            if ((unsigned)cpos >= bound) {
-                                // the child belongs to a later chunk: hand over
-                                // the finished owner's counts
-                                if (cur_own >= 0 && (acc_c | acc_p)) {
-                                    atomicAdd((unsigned long long *)A.wc(s1) + cur_own, acc_c);
-                                    atomicAdd((unsigned long long *)A.bc(s1) + cur_own / NW, acc_c);
-                                    if (acc_p) {
-                                        atomicAdd((unsigned long long *)A.wp(s1) + cur_own, acc_p);
-                                        atomicAdd((unsigned long long *)A.bp(s1) + cur_own / NW, acc_p);
-                                    }
-                                }
-                                cur_own = cpos / chunk_n;
-                                bound = (unsigned)(cur_own + 1) * (unsigned)chunk_n;
-                                acc_c = acc_p = 0;
-                            }
-                            acc_c += c2w & CNT_MASK;
-                            acc_p += c2w >> 15;
+                for (int j = 0; j < ITEMS; ++j) {
+                    const int i = t0 + j * 32 + lane;
+                    const int nch = cnt_children(cw[j]);
+                    const bool pp = (cw[j] & CNT_PP) != 0;
+                    int x = nch;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    const int tot = __shfl_sync(0xffffffffu, x, 31);
+                    const unsigned ppm = __ballot_sync(0xffffffffu, pp);
+                    if (a.root_counts) {
+                        // per-root totals: paths arrive sorted by first vertex,
+                        // so a warp's lanes mostly share one root
+                        const unsigned grp2 = __match_any_sync(0xffffffffu, first[j]);
+                        const unsigned c0 = __reduce_add_sync(grp2, first[j] >= 0 ? 1u : 0u);
+                        const unsigned c1 = __reduce_add_sync(grp2, pp ? 1u : 0u);
+                        const unsigned c2 = __reduce_add_sync(grp2, pp ? (unsigned)k : 0u);
+                        if (first[j] >= 0 && lane == __ffs(grp2) - 1) {
+                            unsigned long long *rc = a.root_counts + 3ll * first[j];
+                            atomicAdd(rc, (unsigned long long)c0);
+                            if (c1) atomicAdd(rc + 1, (unsigned long long)c1);
+                            if (c2) atomicAdd(rc + 2, (unsigned long long)c2);
                         }
-                        ++cpos;
+                    }
+                    if (nch > 0) {
+                        const int vb = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + first[j])) : 0;
+                        int cpos = pos_c + x - nch;
+                        // write child w (its record, bitset and own count word)
+                        // and add its counts to the owner of its position
+                        auto emit = [&](int w) {
+                            const bool closes = (w == first[j]);
+                            const unsigned c2w = eval_path<W>(g, k + 1, first[j], w, vb, vis[j], w);
+                            if (cpos < C && next_off + cpos < a.seg_cap) {  // holds when the counts agree
+                                next[cpos] = make_int2(w, i);
+                                out_fl[cpos] = make_int2(first[j], w);
+                                out_cnt[cpos] = (unsigned short)c2w;
+                                if (!closes) {
+                                    const int bb = w - vb;
+#pragma unroll
+                                    for (int ww = 0; ww < W; ++ww)
+                                        out_vis[ww * a.lvl_cap + cpos] =
+                                            vis[j][ww] | ((ww == (bb >> 5)) ? (1u << (bb & 31)) : 0u);
+                                }
+                                if ((unsigned)cpos >= bound) {
+                                    // the child belongs to a later chunk: the
+                                    // finished owner's counts retire
+                                    if (ret_own >= 0) add_counts(A, s1, ret_own, ret_c, ret_p);  // rare: 2nd in one item
+                                    ret_own = cur_own;
+                                    ret_c = acc_c;
+                                    ret_p = acc_p;
+                                    cur_own = cpos / chunk_n;
+                                    bound = (unsigned)(cur_own + 1) * (unsigned)chunk_n;
+                                    acc_c = acc_p = 0;
+                                }
+                                acc_c += (unsigned)cnt_children(c2w);
+                                acc_p += c2w >> 15;
+                            }
+                            ++cpos;
+                        };
+                        const int e0 = __ldg(g.rp + last[j]);
+                        if (!(cw[j] & CNT_WIDE)) {
+                            // the stored mask names the extending successors
+                            for (unsigned m = cw[j] & CNT_BITS; m; m &= m - 1) emit(__ldg(g.col + e0 + __ffs(m) - 1));
+                        } else {
+                            const int e1 = __ldg(g.rp + last[j] + 1);
+                            for (int e = e0; e < e1; ++e) {
+                                const int w = __ldg(g.col + e);
+                                if (w == first[j] || !test_bit<W>(vis[j], w - vb)) emit(w);
+                            }
+                        }
+                    }
+                    if (pp) {
+                        const int q = pos_p + __popc(ppm & lt_mask);
+                        if (pp_off + q < a.pp_seg_cap) lpp[q] = i;
+                    }
+                    pos_c += tot;
+                    pos_p += __popc(ppm);
+                    if (__any_sync(0xffffffffu, ret_own >= 0)) {
+                        flush_counts(A, s1, ret_own, ret_c, ret_p);
+                        ret_own = -1;
                     }
                 }
-                if (pp) {
-                    const int q = pos_p + __popc(ppm & lt_mask);
-                    if (pp_off + q < a.pp_seg_cap) lpp[q] = i;
-                }
-                pos_c += tot;
-                pos_p += __popc(ppm);
             }
+            // the chunk must have produced exactly what its count promised
+            if (lane == 0 && (pos_c - pa != own_c || pos_p - pb != own_p)) atomicOr(a.err, ERR_INVAL);
+            ec = ec_next;
+            ep = ep_next;
         }
-        flush_counts<NW>(A, s1, cur_own, acc_c, acc_p);
-        // the chunk must have produced exactly what its count promised
-        if (lane == 0 && (pos_c - pa != own_c || pos_p - pb != own_p)) atomicOr(a.err, ERR_INVAL);
-        if (!grid_barrier_tree(a.bar, a.err)) break;
+        flush_counts(A, s1, cur_own, acc_c, acc_p);
+        if (C == 0) break;  // nothing follows; the end of the launch orders the writes
+        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT | ERR_INVAL)) break;
+        count = C;
+        lnodes = next;
+        lpp += P;
     }
 }
 
@@ -456,16 +488,23 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
 // ---------------------------------------------------------------------------
 template <int W, int BLOCK, int ITEMS>
 static cudaError_t launch_wbi(const EnumArgs &args, int num_sms, cudaStream_t s, int *grid_out) {
+    // the group prefixes take 2 * grid int64 of shared memory; size it for
+    // the largest grid this block size can have
+    const size_t smem = sizeof(long long) * 2 * (size_t)num_sms * (2048 / BLOCK);
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &blocks_per_sm, enumerate_kernel<W, BLOCK, ITEMS>, BLOCK, 0);
+        cudaError_t e = cudaFuncSetAttribute(enumerate_kernel<W, BLOCK, ITEMS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, enumerate_kernel<W, BLOCK, ITEMS>, BLOCK,
+                                                          smem);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (blocks_per_sm > 2048 / BLOCK) blocks_per_sm = 2048 / BLOCK;
     }
     const int grid = num_sms * blocks_per_sm;
     *grid_out = grid;
-    if (args.agg_cap < 3 * (2ll * grid * (BLOCK / 32) + 2ll * grid)) return cudaErrorInvalidValue;
+    if (args.agg_cap < enum_agg_words(grid)) return cudaErrorInvalidValue;
     cudaError_t e;
     if (args.seed_level1) {
         if ((e = launch_seed_level1(args, s)) != cudaSuccess) return e;
@@ -473,7 +512,7 @@ static cudaError_t launch_wbi(const EnumArgs &args, int num_sms, cudaStream_t s,
     EnumArgs a = args;
     void *params[] = {&a};
     e = cudaLaunchCooperativeKernel((const void *)enumerate_kernel<W, BLOCK, ITEMS>, dim3(grid), dim3(BLOCK),
-                                    params, 0, s);
+                                    params, smem, s);
     if (e == cudaSuccess) note_launch();
     return e;
 }
@@ -482,11 +521,7 @@ static cudaError_t launch_wbi(const EnumArgs &args, int num_sms, cudaStream_t s,
 template <int W>
 static cudaError_t launch_w(const EnumArgs &args, EnumShape shape, int num_sms, cudaStream_t s, int *grid_out) {
     if constexpr (W <= 8) {
-        if (shape.block == 128) {
-            if (shape.items == 1) return launch_wbi<W, 128, 1>(args, num_sms, s, grid_out);
-            if (shape.items == 2) return launch_wbi<W, 128, 2>(args, num_sms, s, grid_out);
-            if (shape.items == 4) return launch_wbi<W, 128, 4>(args, num_sms, s, grid_out);
-        } else if (shape.block == 256) {
+        if (shape.block == 256) {
             if (shape.items == 1) return launch_wbi<W, 256, 1>(args, num_sms, s, grid_out);
             if (shape.items == 2) return launch_wbi<W, 256, 2>(args, num_sms, s, grid_out);
             if (shape.items == 4) return launch_wbi<W, 256, 4>(args, num_sms, s, grid_out);
@@ -521,7 +556,7 @@ cudaError_t relayout_frontier(const int2 *fl_old, const unsigned *vis_old, long 
 
 bool enum_shape_supported(int W, EnumShape shape) {
     if (W > 8) return shape.block == 256 && shape.items == 1;
-    if (shape.block == 128 || shape.block == 256) return shape.items == 1 || shape.items == 2 || shape.items == 4;
+    if (shape.block == 256) return shape.items == 1 || shape.items == 2 || shape.items == 4;
     if (shape.block == 512) return shape.items == 1 || shape.items == 2;
     return false;
 }

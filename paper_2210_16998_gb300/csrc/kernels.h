@@ -12,13 +12,28 @@ namespace tpg {
 extern std::atomic<long long> g_kernel_launches;
 inline void note_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
-// per-chunk level counts of the frontier launch: 3 rotating slots of
-// {children, PPs} per warp and per block; the buffer holds ENUM_AGG_WORDS
-// int64 values, enough for grids of up to 8192 blocks and 16384 warps
-constexpr long long ENUM_AGG_WORDS = 3 * (2 * 16384 + 2 * 8192);
-// frontier count word: children (bits 0-12, at most TPG_MAX_N) and PP flag
-constexpr unsigned CNT_MASK = 0x1fffu;
+// per-chunk level counts of the frontier launch: a level is cut into
+// ENUM_CPG chunks per block; 3 rotating slots of {children, PPs} per chunk
+// and per block.  ENUM_AGG_WORDS int64 values hold them for grids of up to
+// 2048 blocks.
+constexpr int ENUM_CPG = 32;
+constexpr long long enum_agg_words(long long grid) { return 3 * (2 * ENUM_CPG * grid + 2 * grid) + 4; }
+constexpr long long ENUM_AGG_WORDS = enum_agg_words(2048);
+// frontier count word of a path: bits 0-12 are the mask of the successors of
+// its last vertex that extend it (successor list position s -> bit s; lists
+// of at most CNT_MASK_DEG successors), or, with CNT_WIDE set, the number of
+// such successors (at most TPG_MAX_N); CNT_PP flags a prime path
+constexpr unsigned CNT_BITS = 0x1fffu;
+constexpr unsigned CNT_WIDE = 0x4000u;
 constexpr unsigned CNT_PP = 0x8000u;
+constexpr int CNT_MASK_DEG = 13;
+__host__ __device__ inline int cnt_children(unsigned cw) {
+#ifdef __CUDA_ARCH__
+    return (cw & CNT_WIDE) ? (int)(cw & CNT_BITS) : __popc(cw & CNT_BITS);
+#else
+    return (cw & CNT_WIDE) ? (int)(cw & CNT_BITS) : __builtin_popcount(cw & CNT_BITS);
+#endif
+}
 // control block of a launch (err, stop_level, ...); the frontier's grid
 // barrier lives at CTL_BAR_OFFSET, other cooperative kernels use offset 128
 constexpr int CTL_BYTES = 512;
@@ -40,7 +55,7 @@ struct EnumArgs {
     int start_level;         // first level processed by this launch
     int seed_level1;         // 1 on a fresh run: level 1 is written first (never on a resume)
     long long *agg;          // per-block level counts (no initialisation needed)
-    long long agg_cap;       // int64 values in agg (3 * (2 * warps + 2 * blocks) at least)
+    long long agg_cap;       // int64 values in agg (enum_agg_words(grid) at least)
     int *err;                // error flags (zeroed)
     int *stop_level;         // level whose next level did not fit (written with the flags)
     unsigned *bar;           // tree grid barrier, BAR_WORDS words (zeroed)

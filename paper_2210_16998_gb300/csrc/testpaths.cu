@@ -55,27 +55,67 @@ cudaError_t tp_lengths(const long long *pp_off, const int *pp_vert, const int *p
     return cudaGetLastError();
 }
 
-// one warp per TP; lanes stride over its positions (coalesced reads/writes)
-__global__ void tp_write_kernel(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
-                                GraphDev g, const long long *tp_off, int *tp_vert) {
+// One warp per 32 consecutive TPs.  Lane l first gathers the parts of TP
+// i0 + l (prefix path entry -> first vertex, the PP, suffix path last vertex
+// -> exit) in parallel with the other lanes; the warp then copies the TPs one
+// after another with its lanes striding over positions (coalesced).  When
+// every TP of the warp is its own PP (empty prefix and suffix), the 32 TPs
+// are one contiguous copy of the 32 PPs.
+__global__ void tp_write_kernel(const long long *__restrict__ pp_off, const int *__restrict__ pp_vert,
+                                const int *__restrict__ pp_graph, long long P, GraphDev g,
+                                const long long *__restrict__ tp_off, int *__restrict__ tp_vert) {
     const int lane = threadIdx.x & 31;
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < P; i += nw) {
-        const long long o0 = pp_off[i], o1 = pp_off[i + 1];
-        const int gid = pp_graph ? pp_graph[i] : 0;
-        const int vb = g.vgraph ? g.vbase[gid] : 0;
-        const int f = pp_vert[o0] + vb, l = pp_vert[o1 - 1] + vb;
-        const long long pl = g.pre_len[f] - 1, plen = o1 - o0;
-        const long long total = tp_off[i + 1] - tp_off[i];
-        const int *pre = g.pre_seq + g.pre_off[f];
-        const int *suf = g.suf_seq + g.suf_off[l] + 1;
-        int *dst = tp_vert + tp_off[i];
-        for (long long p = lane; p < total; p += 32) {
-            int v;
-            if (p < pl) v = pre[p];
-            else if (p < pl + plen) v = pp_vert[o0 + (p - pl)];
-            else v = suf[p - pl - plen];
-            dst[p] = v;
+    for (long long i0 = (blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; i0 < P;
+         i0 += nw * 32) {
+        const long long i = i0 + lane;
+        const bool valid = i < P;
+        long long o0 = 0, plen = 0, d0 = 0, total = 0;
+        int pl = 0;
+        const int *pre = nullptr, *suf = nullptr;
+        if (valid) {
+            o0 = pp_off[i];
+            plen = pp_off[i + 1] - o0;
+            d0 = tp_off[i];
+            total = tp_off[i + 1] - d0;
+            const int gid = pp_graph ? pp_graph[i] : 0;
+            const int vb = g.vgraph ? g.vbase[gid] : 0;
+            const int f = pp_vert[o0] + vb, l = pp_vert[o0 + plen - 1] + vb;
+            pl = g.pre_len[f] - 1;
+            pre = g.pre_seq + g.pre_off[f];
+            suf = g.suf_seq + g.suf_off[l] + 1;
+        }
+        const int last = (int)((P - i0 < 32 ? P - i0 : 32) - 1);
+        if (__all_sync(0xffffffffu, !valid || (pl == 0 && total == plen))) {
+            // TP == PP for all: one contiguous range
+            const long long src0 = __shfl_sync(0xffffffffu, o0, 0), dst0 = __shfl_sync(0xffffffffu, d0, 0);
+            const long long len = __shfl_sync(0xffffffffu, d0 + total, last) - dst0;
+            const int *src = pp_vert + src0;
+            int *dst = tp_vert + dst0;
+            long long p = lane;
+            for (; p + 96 < len; p += 128) {
+                const int a = src[p], b = src[p + 32], c = src[p + 64], d = src[p + 96];
+                dst[p] = a;
+                dst[p + 32] = b;
+                dst[p + 64] = c;
+                dst[p + 96] = d;
+            }
+            for (; p < len; p += 32) dst[p] = src[p];
+            continue;
+        }
+        for (int t = 0; t <= last; ++t) {
+            const long long to0 = __shfl_sync(0xffffffffu, o0, t), td0 = __shfl_sync(0xffffffffu, d0, t);
+            const long long tplen = __shfl_sync(0xffffffffu, plen, t), ttot = __shfl_sync(0xffffffffu, total, t);
+            const int tpl = __shfl_sync(0xffffffffu, pl, t);
+            const int *tpre = (const int *)__shfl_sync(0xffffffffu, (unsigned long long)pre, t);
+            const int *tsuf = (const int *)__shfl_sync(0xffffffffu, (unsigned long long)suf, t);
+            for (long long p = lane; p < ttot; p += 32) {
+                int v;
+                if (p < tpl) v = tpre[p];
+                else if (p < tpl + tplen) v = pp_vert[to0 + (p - tpl)];
+                else v = tsuf[p - tpl - tplen];
+                tp_vert[td0 + p] = v;
+            }
         }
     }
 }
@@ -83,8 +123,8 @@ __global__ void tp_write_kernel(const long long *pp_off, const int *pp_vert, con
 cudaError_t tp_write(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
                      const GraphDev &g, const long long *tp_off, int *tp_vert, cudaStream_t s) {
     if (P <= 0) return cudaSuccess;
-    long long blocks = (P + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    long long blocks = (P + 255) / 256;  // 8 warps of 32 TPs
+    if (blocks > 65535) blocks = 65535;
     tp_write_kernel<<<(unsigned)blocks, 256, 0, s>>>(pp_off, pp_vert, pp_graph, P, g, tp_off, tp_vert);
     note_launch();
     return cudaGetLastError();
