@@ -107,6 +107,12 @@ __device__ __forceinline__ unsigned eval_path(const GraphDev &g, int k, int firs
     return CNT_PP;
 }
 
+// position of the (r+1)-th set bit of m (r = 0: the lowest); m has more than r set bits
+__device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
+    for (; r > 0; --r) m &= m - 1;
+    return __ffs(m) - 1;
+}
+
 constexpr int CPG = ENUM_CPG;  // chunks per block: a level is cut into CPG * blocks chunks
 
 // paths per chunk of a level of `count` paths cut into nchk chunks:
@@ -410,51 +416,81 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                             if (c2) atomicAdd(rc + 2, (unsigned long long)c2);
                         }
                     }
+                    // The item's children are dealt to lanes in output order:
+                    // child q of the warp (0 <= q < tot, at position pos_c + q)
+                    // goes to lane q % 32, which finds its parent lane (the last
+                    // lane whose first child is at or before q) and reads the
+                    // parent's path through shuffles.  A parent with many
+                    // children thus costs the warp one round per 32 children,
+                    // and the child records are stored contiguously.
+                    const int excl = x - nch;
+                    int vb_l = 0, e0_l = 0;
                     if (nch > 0) {
-                        const int vb = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + first[j])) : 0;
-                        int cpos = pos_c + x - nch;
-                        // write child w (its record, bitset and own count word)
-                        // and add its counts to the owner of its position
-                        auto emit = [&](int w) {
-                            const bool closes = (w == first[j]);
-                            const unsigned c2w = eval_path<W>(g, k + 1, first[j], w, vb, vis[j], w);
-                            if (cpos < C && next_off + cpos < a.seg_cap) {  // holds when the counts agree
-                                next[cpos] = make_int2(w, i);
-                                out_fl[cpos] = make_int2(first[j], w);
-                                out_cnt[cpos] = (unsigned short)c2w;
-                                if (!closes) {
-                                    const int bb = w - vb;
+                        vb_l = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + first[j])) : 0;
+                        e0_l = __ldg(g.rp + last[j]);
+                    }
+                    for (int q0 = 0; q0 < tot; q0 += 32) {
+                        const int q = q0 + lane;
+                        int p = 0;
 #pragma unroll
-                                    for (int ww = 0; ww < W; ++ww)
-                                        out_vis[ww * a.lvl_cap + cpos] =
-                                            vis[j][ww] | ((ww == (bb >> 5)) ? (1u << (bb & 31)) : 0u);
-                                }
-                                if ((unsigned)cpos >= bound) {
-                                    // the child belongs to a later chunk: the
-                                    // finished owner's counts retire
-                                    if (ret_own >= 0) add_counts(A, s1, ret_own, ret_c, ret_p);  // rare: 2nd in one item
-                                    ret_own = cur_own;
-                                    ret_c = acc_c;
-                                    ret_p = acc_p;
-                                    cur_own = cpos / chunk_n;
-                                    bound = (unsigned)(cur_own + 1) * (unsigned)chunk_n;
-                                    acc_c = acc_p = 0;
-                                }
-                                acc_c += (unsigned)cnt_children(c2w);
-                                acc_p += c2w >> 15;
-                            }
-                            ++cpos;
-                        };
-                        const int e0 = __ldg(g.rp + last[j]);
-                        if (!(cw[j] & CNT_WIDE)) {
-                            // the stored mask names the extending successors
-                            for (unsigned m = cw[j] & CNT_BITS; m; m &= m - 1) emit(__ldg(g.col + e0 + __ffs(m) - 1));
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const int cand = p + step;  // <= 31
+                            if (__shfl_sync(0xffffffffu, excl, cand) <= q) p = cand;
+                        }
+                        const int pf = __shfl_sync(0xffffffffu, first[j], p);
+                        const int pl = __shfl_sync(0xffffffffu, last[j], p);
+                        const int pvb = __shfl_sync(0xffffffffu, vb_l, p);
+                        const int pe0 = __shfl_sync(0xffffffffu, e0_l, p);
+                        const unsigned pcw = __shfl_sync(0xffffffffu, cw[j], p);
+                        const int rank = q - __shfl_sync(0xffffffffu, excl, p);
+                        unsigned pvis[W];
+#pragma unroll
+                        for (int ww = 0; ww < W; ++ww) pvis[ww] = __shfl_sync(0xffffffffu, vis[j][ww], p);
+                        if (q >= tot) continue;
+                        const int pi = t0 + j * 32 + p;
+                        // the rank-th successor of the parent's last vertex that extends it
+                        int w;
+                        if (!(pcw & CNT_WIDE)) {
+                            w = __ldg(g.col + pe0 + nth_set_bit(pcw & CNT_BITS, rank));
                         } else {
-                            const int e1 = __ldg(g.rp + last[j] + 1);
-                            for (int e = e0; e < e1; ++e) {
-                                const int w = __ldg(g.col + e);
-                                if (w == first[j] || !test_bit<W>(vis[j], w - vb)) emit(w);
+                            const int pe1 = __ldg(g.rp + pl + 1);
+                            int left = rank, e = pe0;
+                            for (; e < pe1; ++e) {
+                                const int v = __ldg(g.col + e);
+                                if (v == pf || !test_bit<W>(pvis, v - pvb)) {
+                                    if (left == 0) break;
+                                    --left;
+                                }
                             }
+                            w = __ldg(g.col + (e < pe1 ? e : pe1 - 1));
+                        }
+                        const int cpos = pos_c + q;
+                        const bool closes = (w == pf);
+                        const unsigned c2w = eval_path<W>(g, k + 1, pf, w, pvb, pvis, w);
+                        if (cpos < C && next_off + cpos < a.seg_cap) {  // holds when the counts agree
+                            next[cpos] = make_int2(w, pi);
+                            out_fl[cpos] = make_int2(pf, w);
+                            out_cnt[cpos] = (unsigned short)c2w;
+                            if (!closes) {
+                                const int bb = w - pvb;
+#pragma unroll
+                                for (int ww = 0; ww < W; ++ww)
+                                    out_vis[ww * a.lvl_cap + cpos] =
+                                        pvis[ww] | ((ww == (bb >> 5)) ? (1u << (bb & 31)) : 0u);
+                            }
+                            if ((unsigned)cpos >= bound) {
+                                // the child belongs to a later chunk: the
+                                // finished owner's counts retire
+                                if (ret_own >= 0) add_counts(A, s1, ret_own, ret_c, ret_p);  // rare: 2nd in one item
+                                ret_own = cur_own;
+                                ret_c = acc_c;
+                                ret_p = acc_p;
+                                cur_own = cpos / chunk_n;
+                                bound = (unsigned)(cur_own + 1) * (unsigned)chunk_n;
+                                acc_c = acc_p = 0;
+                            }
+                            acc_c += (unsigned)cnt_children(c2w);
+                            acc_p += c2w >> 15;
                         }
                     }
                     if (pp) {
@@ -563,7 +599,7 @@ bool enum_shape_supported(int W, EnumShape shape) {
 
 EnumShape default_enum_shape(int W) {
     if (W > 8) return EnumShape{256, 1};
-    return EnumShape{256, 2};
+    return EnumShape{512, 1};
 }
 
 int bitset_words_supported(int maxn) {
