@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(GMB) gm_pp_lengths(GmArgs a) {
 
 constexpr int GM_MAT_WARPS = 8;
 
-__global__ void __launch_bounds__(GM_MAT_WARPS * 32) gm_materialize(GmArgs a) {
-    __shared__ int sbuf[GM_MAT_WARPS][MAT_BUF];
+__global__ void __launch_bounds__(GM_MAT_WARPS * 32, 8) gm_materialize(GmArgs a) {
+    __shared__ unsigned short sbuf[GM_MAT_WARPS][MAT_BUF];
     __shared__ int2 *s_nodes[MAT_MAX_LV];
     int2 *const *lv = cache_level_nodes(a.levels, a.max_levels, s_nodes);
     const long long P = gm_P(a);

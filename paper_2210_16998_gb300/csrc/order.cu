@@ -133,11 +133,11 @@ cudaError_t pp_offsets_single_level(long long *off, long long n, int level, cuda
 
 constexpr int MAT_WARPS = 8;
 
-__global__ void __launch_bounds__(MAT_WARPS * 32)
+__global__ void __launch_bounds__(MAT_WARPS * 32, 8)
     pp_materialize_kernel(const long long *refs, const int *single_refs, int single_level, long long n,
                           const long long *offsets, const LevelRec *levels, int max_levels, GraphDev g,
                           int *out, int *out_graph) {
-    __shared__ int buf[MAT_WARPS][MAT_BUF];
+    __shared__ unsigned short buf[MAT_WARPS][MAT_BUF];
     __shared__ int2 *s_nodes[MAT_MAX_LV];
     int2 *const *lv = cache_level_nodes(levels, max_levels, s_nodes);
     materialize_warps(refs, single_refs, single_level, n, offsets, levels, g, out, out_graph, buf, lv);

@@ -44,11 +44,15 @@ __device__ __forceinline__ int key_cmp(long long a, long long b, const long long
 // Materialise PPs [0, n): one warp handles 32 consecutive PPs; each lane
 // walks its path's parent links from the last vertex back to the first,
 // writing into a per-warp shared-memory window that the warp then stores
-// contiguously (lanes store directly when the window does not fit).  A PP is
+// contiguously (lanes store directly when the window does not fit).  The
+// window holds local ids as 16-bit values (a graph has at most TPG_MAX_N
+// vertices), so more warps fit an SM: the walk is latency-bound and the
+// number of walks in flight sets its speed.  A PP is
 // refs[i] = (level << 32 | index in level), or, with refs == nullptr, index
 // single_refs[i] in level single_level.  out_graph (optional) receives the
 // graph id of each PP.
-constexpr int MAT_BUF = 2048;  // int32 per warp (8 KB)
+static_assert(TPG_MAX_N <= 65536, "local vertex ids fit 16 bits");
+constexpr int MAT_BUF = 1536;  // local vertex ids (uint16, < TPG_MAX_N) per warp: 32 PPs of up to 48 vertices
 constexpr int MAT_MAX_LV = 512; // level-pointer table cached in shared memory up to this many levels
 
 // Copy the levels' node pointers to shared memory (one dependent load per
@@ -65,7 +69,7 @@ template <int NWARPS>
 __device__ __forceinline__ void materialize_warps(const long long *refs, const int *single_refs, int single_level,
                                                   long long n, const long long *offsets, const LevelRec *levels,
                                                   const GraphDev &g, int *out, int *out_graph,
-                                                  int (&buf)[NWARPS][MAT_BUF], int2 *const *lvl_nodes) {
+                                                  unsigned short (&buf)[NWARPS][MAT_BUF], int2 *const *lvl_nodes) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long nwarps = (long long)gridDim.x * NWARPS;
     for (long long w0 = (blockIdx.x * (long long)NWARPS + wid) * 32; w0 < n; w0 += nwarps * 32) {
@@ -92,7 +96,7 @@ __device__ __forceinline__ void materialize_warps(const long long *refs, const i
             const int2 rec = lvl_nodes ? lvl_nodes[j][node] : levels[j].nodes[node];
             const int v = rec.x;
             const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
-            if (staged) buf[wid][off - start + (j - 1)] = loc;
+            if (staged) buf[wid][off - start + (j - 1)] = (unsigned short)loc;
             else out[off + (j - 1)] = loc;
             root = v;
             node = rec.y;
@@ -100,7 +104,7 @@ __device__ __forceinline__ void materialize_warps(const long long *refs, const i
         if (valid && out_graph) out_graph[idx] = g.vgraph ? g.vgraph[root] : 0;
         if (staged) {
             __syncwarp();
-            for (long long t = lane; t < span; t += 32) out[start + t] = buf[wid][t];
+            for (long long t = lane; t < span; t += 32) out[start + t] = (int)buf[wid][t];
             __syncwarp();
         }
     }
