@@ -189,8 +189,8 @@ int tpg_set_allocator(tpg_alloc_fn alloc, tpg_release_fn release, void *ctx);
 /*
  * Tile shape of the frontier kernel for this handle: `block` threads per
  * block, `items` paths per thread.  Supported: block 256 with items 1, 2
- * or 4, block 512 with items 1 or 2 (bitsets of <= 8 words); block 256
- * items 1 for wider bitsets.  TPG_EINVAL otherwise.  Results never depend
+ * or 4, block 512 with items 1 or 2, block 1024 with items 1 (bitsets of
+ * <= 8 words); block 256 items 1 for wider bitsets.  TPG_EINVAL otherwise.  Results never depend
  * on the shape; the autotuner uses this.
  */
 int tpg_set_tile_shape(tpg_cfg *g, int32_t block, int32_t items);

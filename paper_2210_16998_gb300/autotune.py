@@ -20,7 +20,7 @@ import time
 from . import cfggen
 from . import tpg
 
-SHAPES_NARROW = [(256, 1), (256, 2), (256, 4), (512, 1), (512, 2)]
+SHAPES_NARROW = [(256, 1), (256, 2), (256, 4), (512, 1), (512, 2), (1024, 1)]
 SHAPES_WIDE = [(256, 1)]
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuned_shapes.json")
 

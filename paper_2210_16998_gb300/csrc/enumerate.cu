@@ -135,6 +135,7 @@ struct AggSlots {
 
 __device__ __forceinline__ void add_counts(const AggSlots &A, int s, int own, unsigned long long c,
                                            unsigned long long p) {
+    // (c, p) fit 32 bits for one lane; a warp sum is widened before it is added
     if (c) {
         atomicAdd((unsigned long long *)A.cc(s) + own, c);
         atomicAdd((unsigned long long *)A.gc(s) + own / CPG, c);
@@ -333,9 +334,10 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
         const int chunk_n = C > 0 ? level_chunk(C, NC) : 1;  // the next level's chunk
         // next-level counts of the children this lane wrote, per owner chunk;
         // a finished owner's counts retire and are flushed by the whole warp
+        // (32-bit sums: a chunk holds < 2^31 / NC + 32 positions of < 2^13 children)
         int cur_own = -1, ret_own = -1;
         unsigned bound = 0;  // first position of the chunk after cur_own
-        unsigned long long acc_c = 0, acc_p = 0, ret_c = 0, ret_p = 0;
+        unsigned acc_c = 0, acc_p = 0, ret_c = 0, ret_p = 0;
 
         // chunk entries of the group of chunk c that precede it, and its own
         // (lanes 0..r of the group, r = c's place in it)
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                         const int cpos = pos_c + q;
                         const bool closes = (w == pf);
                         const unsigned c2w = eval_path<W>(g, k + 1, pf, w, pvb, pvis, w);
-                        if (cpos < C && next_off + cpos < a.seg_cap) {  // holds when the counts agree
+                        if (cpos < C) {  // holds when the counts agree; C fits the segment and the frontier
                             next[cpos] = make_int2(w, pi);
                             out_fl[cpos] = make_int2(pf, w);
                             out_cnt[cpos] = (unsigned short)c2w;
@@ -564,6 +566,8 @@ static cudaError_t launch_w(const EnumArgs &args, EnumShape shape, int num_sms, 
         } else if (shape.block == 512) {
             if (shape.items == 1) return launch_wbi<W, 512, 1>(args, num_sms, s, grid_out);
             if (shape.items == 2) return launch_wbi<W, 512, 2>(args, num_sms, s, grid_out);
+        } else if (shape.block == 1024) {
+            if (shape.items == 1) return launch_wbi<W, 1024, 1>(args, num_sms, s, grid_out);
         }
         return cudaErrorInvalidValue;
     } else {
@@ -594,6 +598,7 @@ bool enum_shape_supported(int W, EnumShape shape) {
     if (W > 8) return shape.block == 256 && shape.items == 1;
     if (shape.block == 256) return shape.items == 1 || shape.items == 2 || shape.items == 4;
     if (shape.block == 512) return shape.items == 1 || shape.items == 2;
+    if (shape.block == 1024) return shape.items == 1;
     return false;
 }
 

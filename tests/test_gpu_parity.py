@@ -194,7 +194,7 @@ def test_tiny_arena_resumes_at_the_failing_level(caps, config3_ref):
     assert stats["prime_paths"] == ref.num_pp
 
 
-@pytest.mark.parametrize("shape", [(256, 1), (256, 2), (256, 4), (512, 1), (512, 2)])
+@pytest.mark.parametrize("shape", [(256, 1), (256, 2), (256, 4), (512, 1), (512, 2), (1024, 1)])
 def test_every_tile_shape(shape, config3_ref):
     ref, stats = check_cfg(G.config3_cfg(), shape=shape, ref=config3_ref)
     assert (stats["tile_block"], stats["tile_items"]) == shape
