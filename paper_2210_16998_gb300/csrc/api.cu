@@ -206,6 +206,7 @@ struct tpg_cfg {
     EnumShape shape{0, 0};
     // generic scratch
     DevBuf s_keys[2], s_refs[2], s_len, s_tmp, s_i32[3], s_i64[4];
+    DevBuf rank_cnt, rank_pre[2], rank_noff, rank_bsum;  // PP ranking scratch
 
     // cached PP list on the device (shared with device results)
     Block *pp_off = nullptr, *pp_vert = nullptr, *pp_graph = nullptr, *pp_gptr = nullptr;
@@ -224,7 +225,7 @@ struct tpg_cfg {
         DevBuf seg, ppseg, tfl[2], tvis[2], tcnt[2];
         DevBuf lvl_pp_off, keys[2], refs[2], len, scan_tmp, pp_graph, tp_len, run_start, run_rank, tp_graph0,
             run_base, nruns, bounds0, tp_off0, tp_vert0, perm[2], keep, keep_off, keep_rank, tp_graph, counts,
-            key_off, key;
+            key_off, key, rank_cnt, rank_pre[2], rank_noff, rank_bsum;
         Block *pp_off = nullptr, *pp_vert = nullptr, *pp_gptr = nullptr;
         Block *tp_off = nullptr, *tp_vert = nullptr, *tp_gptr = nullptr;
         long long seg_cap = 0, pp_cap = 0, lvl_cap = 0;
@@ -295,7 +296,8 @@ void release_plan(tpg_cfg *g) {
                      &p.keys[0], &p.keys[1], &p.refs[0], &p.refs[1], &p.len, &p.scan_tmp, &p.pp_graph, &p.tp_len,
                      &p.run_start, &p.run_rank, &p.tp_graph0, &p.run_base, &p.nruns, &p.bounds0, &p.tp_off0,
                      &p.tp_vert0, &p.perm[0], &p.perm[1], &p.keep, &p.keep_off, &p.keep_rank, &p.tp_graph,
-                     &p.counts, &p.key_off, &p.key};
+                     &p.counts, &p.key_off, &p.key, &p.rank_cnt, &p.rank_pre[0], &p.rank_pre[1],
+                     &p.rank_noff, &p.rank_bsum};
     for (DevBuf *b : all) release(g, *b);
     Block *bl[] = {p.pp_off, p.pp_vert, p.pp_gptr, p.tp_off, p.tp_vert, p.tp_gptr};
     for (Block *b : bl) block_unref(b);
@@ -316,7 +318,8 @@ void destroy_cfg(tpg_cfg *g) {
                      &g->pre_seq, &g->suf_seq, &g->tfl[0], &g->tfl[1], &g->tvis[0], &g->tvis[1], &g->tcnt[0], &g->tcnt[1],
                      &g->levels, &g->agg, &g->ctl, &g->s_keys[0], &g->s_keys[1],
                      &g->s_refs[0], &g->s_refs[1], &g->s_len, &g->s_tmp, &g->s_i32[0], &g->s_i32[1],
-                     &g->s_i32[2], &g->s_i64[0], &g->s_i64[1], &g->s_i64[2], &g->s_i64[3]};
+                     &g->s_i32[2], &g->s_i64[0], &g->s_i64[1], &g->s_i64[2], &g->s_i64[3], &g->rank_cnt,
+                     &g->rank_pre[0], &g->rank_pre[1], &g->rank_noff, &g->rank_bsum};
     for (DevBuf *b : all) release(g, *b);
     for (auto &b : g->node_segs) release(g, b);
     for (auto &b : g->pp_segs) release(g, b);
@@ -660,31 +663,31 @@ int run_prime_paths(tpg_cfg *g) {
         CK(pp_materialize(nullptr, refs, k, P, (const long long *)off->p, dlev, g->max_levels, g->gd, (int *)vert->p,
                           pgraph ? (int *)pgraph->p : nullptr, s));
     } else {
-        for (int b = 0; b < 2; ++b) {
-            RC(ensure(g, g->s_keys[b], sizeof(int) * P));
-            RC(ensure(g, g->s_refs[b], sizeof(long long) * P));
-        }
+        // canonical order by pre-order rank in the arena's prefix tree
+        RC(ensure(g, g->s_refs[0], sizeof(long long) * P));
         RC(ensure(g, g->s_len, sizeof(long long) * (P + 1)));
         RC(ensure(g, g->s_tmp, sizeof(long long) * scan_tmp_elems(P + 1)));
-        int cur = 0;
-        long long na = 0;
-        int cur_level = 0;
-        for (int idx = (int)pp_levels.size() - 1; idx >= 0; --idx) {
-            const int k = pp_levels[idx];
-            const LevelRec &L = g->h_levels[k];
-            const int *lref = L.pp;
-            if (na == 0) {
-                CK(order_init_run(lref, k, L.pp_count, g->s_keys[cur].as<int>(), g->s_refs[cur].as<long long>(), s));
-                na = L.pp_count;
-            } else {
-                CK(order_merge(g->s_keys[cur].as<int>(), g->s_refs[cur].as<long long>(), na, lref, k, L.pp_count,
-                               g->s_keys[cur ^ 1].as<int>(), g->s_refs[cur ^ 1].as<long long>(), dlev, cur_level,
-                               s));
-                cur ^= 1;
-                na += L.pp_count;
-            }
-            cur_level = k;
-        }
+        RC(ensure(g, g->rank_cnt, sizeof(int) * nodes));
+        for (int b = 0; b < 2; ++b) RC(ensure(g, g->rank_pre[b], sizeof(int) * peak));
+        RC(ensure(g, g->rank_noff, sizeof(long long) * (g->max_levels + 8)));
+        RC(ensure(g, g->rank_bsum, sizeof(long long) * rank_pps_grid(g->num_sms)));
+        CK(cudaMemsetAsync(g->ctl.p, 0, CTL_BYTES, s));
+        RankArgs r{};
+        r.levels = dlev;
+        r.max_levels = g->max_levels;
+        r.cnt = g->rank_cnt.as<int>();
+        r.cnt_cap = nodes;
+        r.pre[0] = g->rank_pre[0].as<int>();
+        r.pre[1] = g->rank_pre[1].as<int>();
+        r.pre_cap = peak;
+        r.noff = g->rank_noff.as<long long>();
+        r.bsum = g->rank_bsum.as<long long>();
+        r.refs = g->s_refs[0].as<long long>();
+        r.refs_cap = P;
+        r.bar = (unsigned *)(g->ctl.as<char>() + CTL_RANK_BAR_OFFSET);
+        r.err = g->ctl.as<int>();
+        CK(rank_pps(r, g->num_sms, s));
+        const int cur = 0;
         const long long *refs = g->s_refs[cur].as<long long>();
         CK(pp_lengths(refs, P, g->s_len.as<long long>(), s));
         CK(scan_i64(g->s_len.as<long long>(), (long long *)off->p, P, g->s_tmp.as<long long>(), s));
@@ -700,8 +703,11 @@ int run_prime_paths(tpg_cfg *g) {
         CK(cudaMemcpyAsync(gptr->p, h, 2 * sizeof(long long), cudaMemcpyHostToDevice, s));
     }
     CK(cudaEventRecord(g->ev[3], s));
+    CK(cudaMemcpyAsync(g->h_small, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     cudaEventElapsedTime(&g->stats.t_order_ms, g->ev[2], g->ev[3]);
+    if (g->h_small[0] & ERR_TIMEOUT) return TPG_ETIMEOUT;
+    if (g->h_small[0]) return TPG_ECUDA;  // the ranking found its scratch too small
     g->P = P;
     g->V = V;
     g->pp_valid = true;
@@ -983,6 +989,10 @@ int capture_plan(tpg_cfg *g) {
     const long long K_cap = p.TV0_cap / (64 / key_bits) + Pc + 1;
     RC(ensure(g, p.key_off, sizeof(long long) * (Pc + 1)));
     RC(ensure(g, p.key, sizeof(unsigned long long) * K_cap));
+    RC(ensure(g, p.rank_cnt, sizeof(int) * p.seg_cap));
+    for (int b = 0; b < 2; ++b) RC(ensure(g, p.rank_pre[b], sizeof(int) * p.lvl_cap));
+    RC(ensure(g, p.rank_noff, sizeof(long long) * (g->max_levels + 8)));
+    RC(ensure(g, p.rank_bsum, sizeof(long long) * rank_pps_grid(g->num_sms)));
     RC(alloc_fixed_workspace(g));
     p.pp_off = block_new(g->fns, sizeof(long long) * (Pc + 1), s);
     p.pp_vert = block_new(g->fns, sizeof(int) * p.V_cap, s);
@@ -1062,6 +1072,14 @@ int capture_plan(tpg_cfg *g) {
     m.tp_graph = p.tp_graph.as<int>();
     m.tp_gptr = (long long *)p.tp_gptr->p;
     m.counts = p.counts.as<GmCounts>();
+    m.rank_cnt = p.rank_cnt.as<int>();
+    m.rank_cnt_cap = p.seg_cap;
+    m.rank_pre[0] = p.rank_pre[0].as<int>();
+    m.rank_pre[1] = p.rank_pre[1].as<int>();
+    m.rank_pre_cap = p.lvl_cap;
+    m.rank_noff = p.rank_noff.as<long long>();
+    m.rank_bsum = p.rank_bsum.as<long long>();
+    m.rank_bar = (unsigned *)(g->ctl.as<char>() + CTL_RANK_BAR_OFFSET);
     CK(cudaStreamSynchronize(s));
 
     cudaGraph_t graph = nullptr;

@@ -152,73 +152,6 @@ __device__ __forceinline__ long long gm_P(const GmArgs &a) {
     return clampc(c->P, a.P_cap);
 }
 
-// Sequential ancestor merge over the levels, deepest first, in one
-// cooperative launch.  All blocks read the same level table, so they take
-// the same branches; the final buffer index is published in counts->pp_buf.
-__global__ void __launch_bounds__(GMB) gm_order_kernel(GmArgs a) {
-    const long long P = gm_P(a);
-    const int ml = a.max_levels;
-    const long long tid = blockIdx.x * (long long)GMB + threadIdx.x;
-    const long long nthr = (long long)gridDim.x * GMB;
-    int cur = 0, cur_level = 0;
-    long long na = 0;
-    bool ok = true;
-    for (int k = ml - 1; k >= 1 && P > 0 && ok; --k) {
-        const long long lo = a.lvl_pp_off[k], nb = a.lvl_pp_off[k + 1] - lo;
-        if (nb == 0) continue;
-        const int *lref = a.levels[k].pp;
-        if (na == 0) {
-            for (long long i = tid; i < nb; i += nthr) {
-                const int rl = lref[i];
-                a.keys[cur][i] = rl;
-                a.refs[cur][i] = ((long long)k << 32) | (unsigned)rl;
-            }
-        } else {
-            // merge the accumulated run (keys at cur_level, lifted to level k
-            // on the fly) with level k's PPs
-            const int *ka = a.keys[cur];
-            const long long *ra = a.refs[cur];
-            int *kc = a.keys[cur ^ 1];
-            long long *rc = a.refs[cur ^ 1];
-            const long long total = na + nb;
-            const int up = cur_level;
-            auto lift = [&](long long i) {
-                int key = ka[i];
-                for (int j = up; j > k; --j) key = a.levels[j].nodes[key].y;
-                return key;
-            };
-            for (long long d0 = tid * GM_ITEMS; d0 < total; d0 += nthr * GM_ITEMS) {
-                long long lo2 = d0 > nb ? d0 - nb : 0, hi2 = d0 < na ? d0 : na;
-                while (lo2 < hi2) {
-                    const long long mid = (lo2 + hi2) >> 1;
-                    if (lift(mid) <= lref[d0 - mid - 1]) lo2 = mid + 1;
-                    else hi2 = mid;
-                }
-                long long i = lo2, j = d0 - lo2;
-                int ki = (i < na) ? lift(i) : 0;
-                for (int t = 0; t < GM_ITEMS && d0 + t < total; ++t) {
-                    if (i < na && (j >= nb || ki <= lref[j])) {
-                        kc[d0 + t] = ki;
-                        rc[d0 + t] = ra[i];
-                        ++i;
-                        if (i < na) ki = lift(i);
-                    } else {
-                        const int rl = lref[j];
-                        kc[d0 + t] = rl;
-                        rc[d0 + t] = ((long long)k << 32) | (unsigned)rl;
-                        ++j;
-                    }
-                }
-            }
-            cur ^= 1;
-        }
-        na += nb;
-        cur_level = k;
-        if (!grid_barrier(a.bar, &a.counts->flags)) { ok = false; break; }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.counts->pp_buf = cur;
-}
-
 __global__ void __launch_bounds__(GMB) gm_pp_lengths(GmArgs a) {
     const long long P = gm_P(a);
     const long long *refs = a.refs[a.counts->pp_buf];
@@ -472,19 +405,24 @@ cudaError_t gm_enqueue_pp(const GmArgs &a, cudaStream_t s) {
     const unsigned grid = stream_grid(a.num_sms);
     gm_level_summary<<<1, GMB, 0, s>>>(a);
     note_launch();
-    static int order_blocks = -1;
-    if (order_blocks < 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&order_blocks, gm_order_kernel, GMB, 0);
-        if (e != cudaSuccess) return e;
-        if (order_blocks < 1) order_blocks = 1;
-        if (order_blocks > 4) order_blocks = 4;
-    }
-    GmArgs args = a;
-    void *params[] = {&args};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)gm_order_kernel, dim3(a.num_sms * order_blocks),
-                                                dim3(GMB), params, 0, s);
+    RankArgs r{};
+    r.levels = a.levels;
+    r.max_levels = a.max_levels;
+    r.cnt = a.rank_cnt;
+    r.cnt_cap = a.rank_cnt_cap;
+    r.pre[0] = a.rank_pre[0];
+    r.pre[1] = a.rank_pre[1];
+    r.pre_cap = a.rank_pre_cap;
+    r.noff = a.rank_noff;
+    r.bsum = a.rank_bsum;
+    r.refs = a.refs[0];  // counts->pp_buf stays 0
+    r.refs_cap = a.P_cap;
+    r.bar = a.rank_bar;
+    r.err = &a.counts->flags;  // any flag sends the replay to the exact path
+    r.skip = &a.counts->flags;
+    r.skip_mask = GM_ENUM_FAILED | GM_OVF_PP | GM_OVF_PPV;
+    cudaError_t e = rank_pps(r, a.num_sms, s);
     if (e != cudaSuccess) return e;
-    note_launch();
     gm_pp_lengths<<<grid, GMB, 0, s>>>(a);
     note_launch();
     e = gm_scan<long long>(a.len, a.pp_off, &a.counts->P, a.P_cap, a.scan_tmp, nullptr, a.num_sms, s);

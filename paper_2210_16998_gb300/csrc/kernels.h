@@ -35,9 +35,11 @@ __host__ __device__ inline int cnt_children(unsigned cw) {
 #endif
 }
 // control block of a launch (err, stop_level, ...); the frontier's grid
-// barrier lives at CTL_BAR_OFFSET, other cooperative kernels use offset 128
-constexpr int CTL_BYTES = 512;
+// barrier lives at CTL_BAR_OFFSET, the PP ranking's at CTL_RANK_BAR_OFFSET,
+// other cooperative kernels use offset 128
+constexpr int CTL_BYTES = 1024;
 constexpr int CTL_BAR_OFFSET = 256;
+constexpr int CTL_RANK_BAR_OFFSET = 512;  // grid barrier of the PP ranking
 
 struct EnumArgs {
     GraphDev g;
@@ -103,6 +105,28 @@ cudaError_t pp_materialize(const long long *refs, const int *single_refs, int si
                            int *out_vertices, int *out_graph, cudaStream_t s);
 cudaError_t graph_ptr_from_ids(const int *ids, long long n, int G, long long *ptr, cudaStream_t s);
 
+// canonical PP order by pre-order rank in the arena's prefix tree (one
+// cooperative launch; all level sizes are read from the device level table)
+struct RankArgs {
+    const LevelRec *levels;
+    int max_levels;
+    int *cnt;             // [cnt_cap] >= all simple paths: per-node PP counts
+    long long cnt_cap;
+    int *pre[2];          // [pre_cap] each >= the largest level: ranks of two consecutive levels
+    long long pre_cap;
+    long long *noff;      // [max_levels + 8]: node offset of each level, then totals
+    long long *bsum;      // [grid]
+    long long *refs;      // [refs_cap]: the sorted PP references (level << 32 | index)
+    long long refs_cap;
+    unsigned *bar;        // tree grid barrier, BAR_WORDS words (zeroed)
+    int *err;             // ERR_INVAL (a capacity too small), ERR_TIMEOUT
+    const int *skip;      // optional: nothing is done when (*skip & skip_mask)
+    int skip_mask;
+};
+// scratch of rank_pps beyond cnt/pre: noff [max_levels + 8], bsum [rank_pps_grid(num_sms)]
+int rank_pps_grid(int num_sms);
+cudaError_t rank_pps(const RankArgs &a, int num_sms, cudaStream_t s);
+
 // graphmode.cu: the device-driven pipeline captured into a CUDA graph
 enum : int {
     GM_ENUM_FAILED = 1,  // the frontier launch stopped (capacity) or failed
@@ -156,6 +180,13 @@ struct GmArgs {
     int *tp_graph;          // [P_cap]
     long long *tp_gptr;     // [G+1]
     GmCounts *counts;
+    // PP ranking scratch (rank_pps)
+    int *rank_cnt;
+    long long rank_cnt_cap;
+    int *rank_pre[2];
+    long long rank_pre_cap;
+    long long *rank_noff, *rank_bsum;
+    unsigned *rank_bar;
 };
 int gm_tp_rounds(int maxn);
 size_t gm_scan_tmp_elems(long long n_cap);

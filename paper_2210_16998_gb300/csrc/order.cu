@@ -173,4 +173,244 @@ cudaError_t graph_ptr_from_ids(const int *ids, long long n, int G, long long *pt
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// PP order by pre-order rank (Def. 1 makes the PPs leaves of the prefix tree)
+// ---------------------------------------------------------------------------
+// The arena is the prefix tree of all simple paths: level k holds the paths
+// of k vertices in lexicographic order, every node points at its parent, and
+// the children of a node are consecutive and ordered by their last vertex.
+// Lexicographic order with a proper prefix first is the tree's pre-order,
+// and a PP has no descendant in the tree (it is never a proper prefix of a
+// simple path), so the canonical PP list is the pre-order list of the PP
+// nodes.  Its rank is computed in two sweeps over the levels:
+//   bottom-up  cnt(v) = [v is a PP] + sum of cnt over v's children;
+//   top-down   rank(v) = rank(parent) + sum of cnt over v's earlier
+//              siblings (rank of level-1 nodes: the prefix sum of cnt),
+// and every PP is written to position rank.  The work is one read and one
+// write of a 4-byte count per arena node in each sweep, whatever the number
+// of levels; one cooperative launch with a grid barrier between levels.
+constexpr int RANK_BLOCK = 256;
+
+__device__ __forceinline__ const int2 *level_nodes(const LevelRec *levels, int k) {
+    return (const int2 *)__ldcg((const unsigned long long *)&levels[k].nodes);
+}
+
+__global__ void __launch_bounds__(RANK_BLOCK) rank_pps_kernel(RankArgs a) {
+    __shared__ long long s_x[2];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int G = gridDim.x, b = blockIdx.x;
+    const long long T = (long long)G * RANK_BLOCK, gtid = (long long)b * RANK_BLOCK + tid;
+    const unsigned full = 0xffffffffu;
+    const int ml = a.max_levels;
+    if (a.skip && (*a.skip & a.skip_mask)) return;  // the same on every block
+    long long *meta = a.noff + ml + 1;              // L, total nodes, P, largest level
+
+    // node offsets of the levels and the totals (block 0), then everyone reads them
+    if (b == 0) {
+        long long carry = 0, pcarry = 0, peak = 0;
+        int L = 0;
+        bool live = true;
+        for (int base = 1; base < ml; base += RANK_BLOCK) {
+            const int k = base + tid;
+            long long c = 0, pc = 0;
+            if (k < ml) {
+                c = a.levels[k].count;
+                pc = a.levels[k].pp_count;
+            }
+            // levels end at the first empty one
+            const unsigned dead = __syncthreads_or(k < ml && c <= 0) ? 1u : 0u;
+            __shared__ int s_first_dead;
+            if (tid == 0) s_first_dead = RANK_BLOCK;
+            __syncthreads();
+            if (k < ml && c <= 0) atomicMin(&s_first_dead, tid);
+            __syncthreads();
+            const int fd = s_first_dead;
+            if (!live || tid >= fd) c = pc = 0;
+            long long tot, ptot;
+            const long long ex = block_excl_scan_i64<RANK_BLOCK>(c, tot);
+            block_excl_scan_i64<RANK_BLOCK>(pc, ptot);
+            long long mx = c;
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(full, mx, o));
+            __shared__ long long s_mx[RANK_BLOCK / 32];
+            if (lane == 0) s_mx[tid >> 5] = mx;
+            __syncthreads();
+            if (tid == 0)
+                for (int w = 0; w < RANK_BLOCK / 32; ++w) peak = max(peak, s_mx[w]);
+            if (live && k < ml && tid < fd) a.noff[k] = carry + ex;
+            if (live && k < ml && tid < fd && c > 0) L = max(L, k);
+            carry += tot;
+            pcarry += ptot;
+            if (dead) live = false;
+            __syncthreads();
+        }
+        // L = the largest level index with paths (block maximum)
+        __shared__ int s_L;
+        if (tid == 0) s_L = 0;
+        __syncthreads();
+        atomicMax(&s_L, L);
+        __syncthreads();
+        if (tid == 0) {
+            a.noff[s_L + 1] = carry;
+            meta[0] = s_L;
+            meta[1] = carry;
+            meta[2] = pcarry;
+            meta[3] = peak;
+            if (carry > a.cnt_cap || peak > a.pre_cap || pcarry > a.refs_cap) atomicOr(a.err, ERR_INVAL);
+        }
+    }
+    if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT | ERR_INVAL)) return;
+    const int L = (int)__ldcg(meta + 0);
+    const long long total = __ldcg(meta + 1);
+    if (L < 1) return;
+
+    // counts: 0, then 1 at every PP
+    for (long long i = gtid; i < total; i += T) a.cnt[i] = 0;
+    if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+    for (int k = 1; k <= L; ++k) {
+        const long long np = __ldcg(&a.levels[k].pp_count), o = __ldcg(a.noff + k);
+        const int *pp = (const int *)__ldcg((const unsigned long long *)&a.levels[k].pp);
+        for (long long i = gtid; i < np; i += T) a.cnt[o + pp[i]] = 1;
+    }
+    if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+
+    // bottom-up: add each node's count to its parent (consecutive nodes
+    // mostly share a parent: one atomic per group of lanes)
+    for (int k = L; k >= 2; --k) {
+        const long long n = __ldcg(a.noff + k + 1) - __ldcg(a.noff + k), o = __ldcg(a.noff + k);
+        const long long op = __ldcg(a.noff + k - 1);
+        const int2 *nodes = level_nodes(a.levels, k);
+        constexpr int U = 4;  // chunks in flight per warp
+        for (long long i0 = gtid - lane; i0 < n; i0 += T * U) {
+            int v[U], p[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long i = i0 + u * T + lane;
+                v[u] = i < n ? a.cnt[o + i] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long i = i0 + u * T + lane;
+                p[u] = v[u] ? __ldcg(&nodes[i].y) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const unsigned grp = __match_any_sync(full, p[u]);
+                const unsigned sum = __reduce_add_sync(grp, (unsigned)v[u]);
+                if (p[u] >= 0 && lane == __ffs(grp) - 1) atomicAdd(a.cnt + op + p[u], (int)sum);
+            }
+        }
+        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+    }
+
+    // level 1: rank = exclusive prefix sum of cnt (two passes over blocks)
+    {
+        const long long n = __ldcg(a.noff + 2) - __ldcg(a.noff + 1), o = __ldcg(a.noff + 1);
+        const long long per = (n + G - 1) / G, lo = min((long long)b * per, n), hi = min(lo + per, n);
+        long long sum = 0;
+        for (long long i = lo + tid; i < hi; i += RANK_BLOCK) sum += a.cnt[o + i];
+        long long tot;
+        block_excl_scan_i64<RANK_BLOCK>(sum, tot);
+        if (tid == 0) a.bsum[b] = tot;
+        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+        long long off = 0;
+        for (int j = tid; j < b; j += RANK_BLOCK) off += __ldcg(a.bsum + j);
+        long long offt;
+        block_excl_scan_i64<RANK_BLOCK>(off, offt);
+        long long run = offt;
+        for (long long t0 = lo; t0 < hi; t0 += RANK_BLOCK) {
+            const long long i = t0 + tid;
+            const int v = i < hi ? a.cnt[o + i] : 0;
+            long long ttot;
+            const long long ex = block_excl_scan_i64<RANK_BLOCK>(v, ttot);
+            if (i < hi) a.pre[1][i] = (int)(run + ex);
+            run += ttot;
+        }
+        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+    }
+
+    // top-down: rank(v) = rank(parent) + counts of earlier siblings; the PPs
+    // of the level above are placed in the same pass
+    for (int k = 2; k <= L + 1; ++k) {
+        {
+            // place level k-1's PPs (their ranks are complete)
+            const long long np = __ldcg(&a.levels[k - 1].pp_count);
+            const int *pp = (const int *)__ldcg((const unsigned long long *)&a.levels[k - 1].pp);
+            const int *rk = a.pre[(k - 1) & 1];
+            for (long long i = gtid; i < np; i += T) {
+                const int x = pp[i];
+                const long long r = rk[x];
+                if (r >= 0 && r < a.refs_cap) a.refs[r] = ((long long)(k - 1) << 32) | (unsigned)x;
+            }
+        }
+        if (k > L) break;
+        const long long n = __ldcg(a.noff + k + 1) - __ldcg(a.noff + k), o = __ldcg(a.noff + k);
+        const int *rp = a.pre[(k - 1) & 1];
+        int *rk = a.pre[k & 1];
+        const int2 *nodes = level_nodes(a.levels, k);
+        // each warp walks a contiguous range of the level, carrying the
+        // sibling run that crosses from one 32-node chunk into the next
+        const long long nwarps = T / 32, wg = gtid / 32;
+        const long long per = (((n + nwarps - 1) / nwarps) + 31) & ~31ll;
+        const long long lo = min(wg * per, n), hi = min(lo + per, n);
+        int run_p = -2, run_sum = 0;  // parent and count sum of the open run
+        if (lo < hi && lo > 0) {
+            int sum = 0, p0 = 0;
+            if (lane == 0) {
+                p0 = __ldcg(&nodes[lo].y);
+                for (long long s2 = lo - 1; s2 >= 0 && __ldcg(&nodes[s2].y) == p0; --s2) sum += a.cnt[o + s2];
+            }
+            run_p = __shfl_sync(full, p0, 0);
+            run_sum = __shfl_sync(full, sum, 0);
+        }
+        // the next chunk's count and parent load while this one is ranked
+        int v_next = (lo + lane < hi) ? a.cnt[o + lo + lane] : 0;
+        int p_next = (lo + lane < hi) ? __ldcg(&nodes[lo + lane].y) : -1;
+        for (long long i0 = lo; i0 < hi; i0 += 32) {
+            const long long i = i0 + lane;
+            const bool in = i < hi;
+            const int v = v_next, p = p_next;
+            const long long inx = i + 32;
+            v_next = inx < hi ? a.cnt[o + inx] : 0;
+            p_next = inx < hi ? __ldcg(&nodes[inx].y) : -1;
+            int pprev = __shfl_up_sync(full, p, 1);
+            if (lane == 0) pprev = run_p;
+            const bool head = !in || p != pprev;
+            // warp prefix of v, restarted at every head
+            int x = v;
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const int y = __shfl_up_sync(full, x, o2);
+                if (lane >= o2) x += y;
+            }
+            const unsigned hm = __ballot_sync(full, head) & (lane == 31 ? full : ((2u << lane) - 1u));
+            const int start = hm ? 31 - __clz(hm) : 0;  // first lane of this lane's sibling run
+            const int before = __shfl_sync(full, x, start > 0 ? start - 1 : 0);
+            int sib = x - v - (start > 0 ? before : 0);
+            if (start == 0 && !(hm & 1u)) sib += run_sum;  // the run began in an earlier chunk
+            if (in) rk[i] = v ? rp[p] + sib : -1;
+            const int lastl = (int)min(31ll, hi - i0 - 1);
+            run_p = __shfl_sync(full, p, lastl);
+            run_sum = __shfl_sync(full, sib + v, lastl);
+        }
+        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+    }
+}
+
+int rank_pps_grid(int num_sms) { return num_sms * 8; }
+
+cudaError_t rank_pps(const RankArgs &args, int num_sms, cudaStream_t s) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rank_pps_kernel, RANK_BLOCK, 0);
+        if (e != cudaSuccess) return e;
+        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+    }
+    RankArgs a = args;
+    void *params[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)rank_pps_kernel, dim3(num_sms * per_sm),
+                                                dim3(RANK_BLOCK), params, 0, s);
+    if (e == cudaSuccess) note_launch();
+    return e;
+}
+
 }  // namespace tpg
