@@ -187,6 +187,17 @@ typedef void (*tpg_release_fn)(void *ptr, void *stream, void *ctx);
 int tpg_set_allocator(tpg_alloc_fn alloc, tpg_release_fn release, void *ctx);
 
 /*
+ * Device blocks the library releases (handle scratch, freed results) are
+ * kept, up to 32 GiB, for reuse by later calls with the same allocator on
+ * the same stream and of the same size class (4 KiB steps up to 1 MiB, 2 MiB
+ * steps above), so a repeated call sequence stops allocating after its
+ * first round.  This hands every kept block back to its allocator (it is
+ * also done by tpg_set_allocator).  Blocks still owned by handles or
+ * results are not affected.  Always TPG_OK.
+ */
+int tpg_release_cached_memory(void);
+
+/*
  * Tile shape of the frontier kernel for this handle: `block` threads per
  * block, `items` paths per thread.  Supported: block 256 with items 1, 2
  * or 4, block 512 with items 1 or 2, block 1024 with items 1 (bitsets of

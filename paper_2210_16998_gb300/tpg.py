@@ -172,6 +172,8 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
                      "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_capacity", "tpg_set_output_capacity",
                      "tpg_graph_capture", "tpg_graph_launch"):
             getattr(lib, name).restype = ctypes.c_int
+        lib.tpg_release_cached_memory.argtypes = []
+        lib.tpg_release_cached_memory.restype = ctypes.c_int
         _lib = lib
     if install_torch_allocator:
         _install_torch_allocator()
@@ -399,6 +401,11 @@ def tpg_set_stream(cfg: Cfg, stream):
 
 def tpg_set_result_location(cfg: Cfg, location: int):
     _check(load_library().tpg_set_result_location(cfg.handle, int(location)), "tpg_set_result_location")
+
+
+def tpg_release_cached_memory():
+    """Hand the device blocks the library keeps for reuse back to their allocator."""
+    _check(load_library().tpg_release_cached_memory(), "tpg_release_cached_memory")
 
 
 def tpg_set_tile_shape(cfg: Cfg, block: int, items: int):
