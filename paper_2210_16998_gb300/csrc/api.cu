@@ -913,6 +913,21 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
         R = h[1];
         g->last_tv0 = TV;
         if (((int *)(h + 2))[0] & ERR_UNREACH) { rc = TPG_EUNREACH; break; }
+        if (TV == g->V) {
+            // A TP is never shorter than its PP, so equal totals mean every
+            // prefix and suffix is empty: each TP is its own PP, and the TP
+            // list is the PP list, in canonical order and without
+            // duplicates.  The result shares the PP list's blocks.
+            block_ref(g->pp_off);
+            block_ref(g->pp_vert);
+            block_ref(g->pp_gptr);
+            f_off = g->pp_off;
+            f_vert = g->pp_vert;
+            f_gptr = g->pp_gptr;
+            T = P;
+            FTV = TV;
+            break;
+        }
         tp_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
         if (!tp_vert) { rc = TPG_ENOMEM; break; }
         if (cuda_err(tp_write(pp_off, pp_vert, pp_graph, P, g->gd, (const long long *)tp_off->p, (int *)tp_vert->p, s))) {
