@@ -258,9 +258,13 @@ def run_ours(args, rank, world, local_rank):
             tpg.tpg_set_tile_shape(h, *shape)
         pp = tpg.tpg_prime_paths(h)
         tp = tpg.tpg_test_paths(h)
-        nbytes = 0
+        # bytes read back to the host: a TP list equal to the PP list shares
+        # its host copy, so count every distinct buffer once
+        bufs = {}
         for r in (pp, tp):
-            nbytes += r.graph_path_ptr.nbytes + r.offsets.nbytes + r.vertices.nbytes
+            for arr in (r.graph_path_ptr, r.offsets, r.vertices):
+                bufs[arr.ctypes.data] = max(bufs.get(arr.ctypes.data, 0), arr.nbytes)
+        nbytes = sum(bufs.values())
         P = pp.num_paths
         pp.free()
         tp.free()

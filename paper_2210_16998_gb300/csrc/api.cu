@@ -149,6 +149,15 @@ struct DevBuf {
     T *as() const { return (T *)p; }
 };
 
+// A page-locked host copy of a device block, shared by every host result
+// made from that block (a block's contents never change once filled).
+struct HostCopy {
+    void *p = nullptr;
+    size_t bytes = 0;
+    std::atomic<int> refs{1};
+};
+void host_copy_unref(HostCopy *h);
+
 // Reference-counted device block, shared by a handle's cache and results.
 struct Block {
     void *p = nullptr;
@@ -156,6 +165,7 @@ struct Block {
     AllocFns fns;
     cudaStream_t stream = nullptr;
     std::atomic<int> refs{1};
+    HostCopy *mirror = nullptr;  // host copy made for a host result, if any
 };
 
 Block *block_new(const AllocFns &f, size_t bytes, cudaStream_t s) {
@@ -173,6 +183,7 @@ void block_ref(Block *b) {
 }
 void block_unref(Block *b) {
     if (b && b->refs.fetch_sub(1) == 1) {
+        host_copy_unref(b->mirror);
         dev_release(b->fns, b->p, b->stream);
         delete b;
     }
@@ -223,6 +234,13 @@ PinnedPool &pinned() {
     return *pool;
 }
 
+void host_copy_unref(HostCopy *h) {
+    if (h && h->refs.fetch_sub(1) == 1) {
+        pinned().put(h->p);
+        delete h;
+    }
+}
+
 int cuda_err(cudaError_t e) {
     if (e == cudaSuccess) return TPG_OK;
     cudaGetLastError();
@@ -268,7 +286,7 @@ void lib_dev_free(void *p, cudaStream_t s) {
 struct PathsImpl {
     tpg_paths pub;  // first member: a tpg_paths* is a PathsImpl*
     int location = TPG_RESULT_HOST;
-    void *host[3] = {nullptr, nullptr, nullptr};
+    HostCopy *host[3] = {nullptr, nullptr, nullptr};
     Block *dev[3] = {nullptr, nullptr, nullptr};
 };
 
@@ -825,29 +843,42 @@ int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, l
         const size_t sz[3] = {sizeof(long long) * (g->G + 1), sizeof(long long) * (P + 1),
                               sizeof(int) * (size_t)std::max<long long>(V, 1)};
         Block *b[3] = {gptr, off, vert};
+        bool copied = false;
         for (int i = 0; i < 3; ++i) {
-            r->host[i] = pinned().get(sz[i]);
-            if (!r->host[i]) {
-                for (int j = 0; j < i; ++j) pinned().put(r->host[j]);
-                delete r;
-                return TPG_ENOMEM;
+            HostCopy *m = b[i]->mirror;
+            if (m && m->bytes >= sz[i]) {
+                // another host result of the same block already holds its copy
+                m->refs.fetch_add(1);
+                r->host[i] = m;
+                continue;
             }
-            if (cudaMemcpyAsync(r->host[i], b[i]->p, sz[i], cudaMemcpyDeviceToHost, g->stream) != cudaSuccess) {
+            HostCopy *h = new HostCopy();
+            h->p = pinned().get(sz[i]);
+            h->bytes = sz[i];
+            if (!h->p || cudaMemcpyAsync(h->p, b[i]->p, sz[i], cudaMemcpyDeviceToHost, g->stream) != cudaSuccess) {
                 cudaGetLastError();
-                for (int j = 0; j <= i; ++j) pinned().put(r->host[j]);
+                const int rc = h->p ? TPG_ECUDA : TPG_ENOMEM;
+                host_copy_unref(h);
+                for (int j = 0; j < i; ++j) host_copy_unref(r->host[j]);
                 delete r;
-                return TPG_ECUDA;
+                return rc;
+            }
+            r->host[i] = h;
+            copied = true;
+            if (!m) {
+                h->refs.fetch_add(1);  // the block keeps it for later results
+                b[i]->mirror = h;
             }
         }
-        if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+        if (copied && cudaStreamSynchronize(g->stream) != cudaSuccess) {
             cudaGetLastError();
-            for (int j = 0; j < 3; ++j) pinned().put(r->host[j]);
+            for (int j = 0; j < 3; ++j) host_copy_unref(r->host[j]);
             delete r;
             return TPG_ECUDA;
         }
-        r->pub.graph_path_ptr = (const int64_t *)r->host[0];
-        r->pub.offsets = (const int64_t *)r->host[1];
-        r->pub.vertices = (const int32_t *)r->host[2];
+        r->pub.graph_path_ptr = (const int64_t *)r->host[0]->p;
+        r->pub.offsets = (const int64_t *)r->host[1]->p;
+        r->pub.vertices = (const int32_t *)r->host[2]->p;
     }
     *out = &r->pub;
     return TPG_OK;
@@ -1884,7 +1915,7 @@ void tpg_free(void *handle) {
     } else if (magic == MAGIC_PATHS) {
         PathsImpl *r = (PathsImpl *)handle;
         for (int i = 0; i < 3; ++i) {
-            if (r->host[i]) pinned().put(r->host[i]);
+            host_copy_unref(r->host[i]);
             block_unref(r->dev[i]);
         }
         r->pub.magic = MAGIC_DEAD;

@@ -208,3 +208,31 @@ def test_unsupported_tile_shape_rejected():
         with pytest.raises(tpg.TPGError) as e:
             tpg.tpg_set_tile_shape(h, 128, 1)
         assert e.value.code == tpg.TPG_EINVAL
+
+
+@pytest.mark.parametrize("location", [tpg.TPG_RESULT_HOST, tpg.TPG_RESULT_DEVICE])
+def test_tp_list_shares_the_pp_list_when_every_tp_is_its_pp(location):
+    """Every PP of a diamond chain runs entry -> exit, so its TP is itself: the
+    TP result shares the PP result's storage, and either outlives the other."""
+    cfg = G.diamond_chain(6)
+    ref = oracle.run_cfg(cfg)
+    with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=location) as h:
+        pp = tpg.tpg_prime_paths(h)
+        tp = tpg.tpg_test_paths(h)
+        if location == tpg.TPG_RESULT_HOST:
+            assert tp.vertices.ctypes.data == pp.vertices.ctypes.data
+        else:
+            assert tp.vertices.data_ptr() == pp.vertices.data_ptr()
+        pp.free()
+        _, toff, tvert = tp.host_arrays()
+        assert_paths_equal(toff, tvert, ref.tp_offsets, ref.tp_vertices, "shared TP")
+        tp.free()
+    # a graph with prefixes and suffixes gets its own TP list
+    cfg = G.config1_cfg()
+    with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=location) as h:
+        pp = tpg.tpg_prime_paths(h)
+        tp = tpg.tpg_test_paths(h)
+        if location == tpg.TPG_RESULT_HOST:
+            assert tp.vertices.ctypes.data != pp.vertices.ctypes.data
+        pp.free()
+        tp.free()
