@@ -217,7 +217,12 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
             const int lo = (int)min((long long)c * chunk, count), hi = (int)min((long long)lo + chunk, count);
             long long c_sum = 0, p_sum = 0;
             for (int i = lo + lane; i < hi; i += 32) {
-                const int2 fl = __ldcg(in_fl + i);
+                int2 fl = __ldcg(in_fl + i);
+                // ids are clamped into range before any use as an index (a
+                // record is a path whenever the level counts agree, which the
+                // chunks check; this only keeps a broken count from faulting)
+                fl.x = (int)min((unsigned)fl.x, (unsigned)(g.N - 1));
+                fl.y = (int)min((unsigned)fl.y, (unsigned)(g.N - 1));
                 unsigned vis[W];
 #pragma unroll
                 for (int w = 0; w < W; ++w) vis[w] = __ldcg(in_vis + w * a.lvl_cap + i);
@@ -378,8 +383,10 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                     const int i = t0 + j * 32 + lane;
                     if (i < hi) {
                         const int2 fl = __ldcg(in_fl + i);
-                        first[j] = fl.x;
-                        last[j] = fl.y;
+                        // clamped into range before any use as an index (see
+                        // the counting pass)
+                        first[j] = (int)min((unsigned)fl.x, (unsigned)(g.N - 1));
+                        last[j] = (int)min((unsigned)fl.y, (unsigned)(g.N - 1));
                         cw[j] = __ldcg(in_cnt + i);
 #pragma unroll
                         for (int w = 0; w < W; ++w) vis[j][w] = __ldcg(in_vis + w * a.lvl_cap + i);
@@ -453,7 +460,9 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                         // the rank-th successor of the parent's last vertex that extends it
                         int w;
                         if (!(pcw & CNT_WIDE)) {
-                            w = __ldg(g.col + pe0 + nth_set_bit(pcw & CNT_BITS, rank));
+                            // (clamped: a wrong count word must not index past the arcs)
+                            const unsigned ci = (unsigned)(pe0 + nth_set_bit(pcw & CNT_BITS, rank));
+                            w = __ldg(g.col + min(ci, (unsigned)(g.M - 1)));
                         } else {
                             const int pe1 = __ldg(g.rp + pl + 1);
                             int left = rank, e = pe0;
