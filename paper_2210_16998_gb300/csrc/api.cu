@@ -934,16 +934,26 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
     long long TV = 0, R = 0, T = 0, FTV = 0;
     long long *h = (long long *)g->h_small;
     do {
-        if (cuda_err(scan_i64(tp_len, (long long *)tp_off->p, P, g->s_tmp.as<long long>(), s))) { rc = TPG_ECUDA; break; }
-        if (cuda_err(scan_i32_to_i64(run_start, run_rank, P, g->s_tmp.as<long long>(), s))) { rc = TPG_ECUDA; break; }
-        cudaMemcpyAsync(h, (long long *)tp_off->p + P, sizeof(long long), cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(h + 1, run_rank + P, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        // the TP vertex total first: the offsets and the runs are needed only
+        // when the TP list differs from the PP list
+        long long *tmp = g->s_tmp.as<long long>();
+        if (cuda_err(scan_i64_sums(tp_len, P, tmp, s))) { rc = TPG_ECUDA; break; }
+        cudaMemcpyAsync(h, tmp + scan_total_index(P), sizeof(long long), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(h + 2, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = TPG_ECUDA; break; }
         TV = h[0];
-        R = h[1];
         g->last_tv0 = TV;
         if (((int *)(h + 2))[0] & ERR_UNREACH) { rc = TPG_EUNREACH; break; }
+        if (TV != g->V) {
+            if (cuda_err(scan_i64_finish(tp_len, (long long *)tp_off->p, P, tmp, s)) ||
+                cuda_err(scan_i32_to_i64(run_start, run_rank, P, tmp, s))) {
+                rc = TPG_ECUDA;
+                break;
+            }
+            cudaMemcpyAsync(h + 1, run_rank + P, sizeof(long long), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) { rc = TPG_ECUDA; break; }
+            R = h[1];
+        }
         if (TV == g->V) {
             // A TP is never shorter than its PP, so equal totals mean every
             // prefix and suffix is empty: each TP is its own PP, and the TP

@@ -86,6 +86,11 @@ cudaError_t relayout_frontier(const int2 *fl_old, const unsigned *vis_old, long 
 // scan_tmp_elems(n) int64 values.  out[n] receives the total.
 size_t scan_tmp_elems(long long n);
 cudaError_t scan_i64(const long long *in, long long *out, long long n, long long *tmp, cudaStream_t s);
+// scan_i64 in two halves: the total first (at tmp[scan_total_index(n)]),
+// the prefix array only when it is needed
+cudaError_t scan_i64_sums(const long long *in, long long n, long long *tmp, cudaStream_t s);
+long long scan_total_index(long long n);
+cudaError_t scan_i64_finish(const long long *in, long long *out, long long n, const long long *tmp, cudaStream_t s);
 // exclusive scan of int32 inputs into int64 outputs (out[n] = total)
 cudaError_t scan_i32_to_i64(const int *in, long long *out, long long n, long long *tmp, cudaStream_t s);
 

@@ -83,6 +83,33 @@ cudaError_t scan_i64(const long long *in, long long *out, long long n, long long
     return scan_impl<long long>(in, out, n, tmp, s);
 }
 
+// The two halves of scan_i64: the first leaves the tile prefixes in tmp and
+// the total at tmp[scan_total_index(n)]; the second writes out[0..n].
+cudaError_t scan_i64_sums(const long long *in, long long n, long long *tmp, cudaStream_t s) {
+    if (n <= 0) {
+        scan_empty_kernel<<<1, 1, 0, s>>>(tmp);
+        note_launch();
+        return cudaGetLastError();
+    }
+    const long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    scan_reduce_kernel<long long><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, tmp);
+    scan_tile_sums_kernel<<<1, SCAN_BLOCK, 0, s>>>(tmp, ntiles);
+    note_launch(2);
+    return cudaGetLastError();
+}
+long long scan_total_index(long long n) { return n <= 0 ? 0 : (n + SCAN_TILE - 1) / SCAN_TILE; }
+cudaError_t scan_i64_finish(const long long *in, long long *out, long long n, const long long *tmp, cudaStream_t s) {
+    if (n <= 0) {
+        scan_empty_kernel<<<1, 1, 0, s>>>(out);
+        note_launch();
+        return cudaGetLastError();
+    }
+    const long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    scan_down_kernel<long long><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, tmp, ntiles);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t scan_i32_to_i64(const int *in, long long *out, long long n, long long *tmp, cudaStream_t s) {
     return scan_impl<int>(in, out, n, tmp, s);
 }
