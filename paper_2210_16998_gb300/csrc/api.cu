@@ -314,6 +314,7 @@ struct tpg_cfg {
     // generic scratch
     DevBuf s_keys[2], s_refs[2], s_len, s_tmp, s_i32[3], s_i64[4];
     DevBuf rank_cnt, rank_pre[2], rank_noff, rank_bsum;  // PP ranking scratch
+    DevBuf pp_ends;  // (first, last) local vertex of each cached PP, for the TP lengths
 
     // cached PP list on the device (shared with device results)
     Block *pp_off = nullptr, *pp_vert = nullptr, *pp_graph = nullptr, *pp_gptr = nullptr;
@@ -426,7 +427,7 @@ void destroy_cfg(tpg_cfg *g) {
                      &g->levels, &g->agg, &g->ctl, &g->s_keys[0], &g->s_keys[1],
                      &g->s_refs[0], &g->s_refs[1], &g->s_len, &g->s_tmp, &g->s_i32[0], &g->s_i32[1],
                      &g->s_i32[2], &g->s_i64[0], &g->s_i64[1], &g->s_i64[2], &g->s_i64[3], &g->rank_cnt,
-                     &g->rank_pre[0], &g->rank_pre[1], &g->rank_noff, &g->rank_bsum};
+                     &g->rank_pre[0], &g->rank_pre[1], &g->rank_noff, &g->rank_bsum, &g->pp_ends};
     for (DevBuf *b : all) release(g, *b);
     for (auto &b : g->node_segs) release(g, b);
     for (auto &b : g->pp_segs) release(g, b);
@@ -760,6 +761,8 @@ int run_prime_paths(tpg_cfg *g) {
     g->pp_gptr = gptr;
     g->pp_graph = pgraph;
     const LevelRec *dlev = g->levels.as<LevelRec>();
+    RC(ensure(g, g->pp_ends, sizeof(int2) * std::max<long long>(P, 1)));
+    int2 *ends = g->pp_ends.as<int2>();
     CK(cudaEventRecord(g->ev[2], s));
     if (P == 0) {
         CK(cudaMemsetAsync(off->p, 0, sizeof(long long), s));
@@ -768,7 +771,7 @@ int run_prime_paths(tpg_cfg *g) {
         const int *refs = g->h_levels[k].pp;
         CK(pp_offsets_single_level((long long *)off->p, P, k, s));
         CK(pp_materialize(nullptr, refs, k, P, (const long long *)off->p, dlev, g->max_levels, g->gd, (int *)vert->p,
-                          pgraph ? (int *)pgraph->p : nullptr, s));
+                          pgraph ? (int *)pgraph->p : nullptr, s, ends));
     } else {
         // canonical order by pre-order rank in the arena's prefix tree
         RC(ensure(g, g->s_refs[0], sizeof(long long) * P));
@@ -799,7 +802,7 @@ int run_prime_paths(tpg_cfg *g) {
         CK(pp_lengths(refs, P, g->s_len.as<long long>(), s));
         CK(scan_i64(g->s_len.as<long long>(), (long long *)off->p, P, g->s_tmp.as<long long>(), s));
         CK(pp_materialize(refs, nullptr, 0, P, (const long long *)off->p, dlev, g->max_levels, g->gd, (int *)vert->p,
-                          pgraph ? (int *)pgraph->p : nullptr, s));
+                          pgraph ? (int *)pgraph->p : nullptr, s, ends));
     }
     if (g->G > 1) {
         CK(graph_ptr_from_ids(pgraph ? (const int *)pgraph->p : nullptr, P, g->G, (long long *)gptr->p, s));
@@ -926,7 +929,8 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
     long long *run_rank = g->s_i64[1].as<long long>();
     int *run_start = g->s_i32[0].as<int>();
     int *tp_graph = g->s_i32[1].as<int>();
-    CK(tp_lengths(pp_off, pp_vert, pp_graph, P, g->gd, tp_len, run_start, tp_graph, g->ctl.as<int>(), s));
+    CK(tp_lengths(pp_off, g->pp_ends.as<int2>(), pp_graph, P, g->gd, tp_len, run_start, tp_graph, g->ctl.as<int>(),
+                  s));
     Block *tp_off = block_new(g->fns, sizeof(long long) * (P + 1), s);
     if (!tp_off) return TPG_ENOMEM;
     int rc = TPG_OK;

@@ -105,9 +105,11 @@ cudaError_t order_merge(const int *ka, const long long *ra, long long na, const 
                         cudaStream_t s);
 cudaError_t pp_lengths(const long long *refs, long long n, long long *len_out, cudaStream_t s);
 cudaError_t pp_offsets_single_level(long long *off, long long n, int level, cudaStream_t s);
+// out_graph and out_ends (optional) receive each PP's graph id and its
+// (first, last) local vertex.
 cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,
                            const long long *offsets, const LevelRec *levels, int max_levels, const GraphDev &g,
-                           int *out_vertices, int *out_graph, cudaStream_t s);
+                           int *out_vertices, int *out_graph, cudaStream_t s, int2 *out_ends = nullptr);
 cudaError_t graph_ptr_from_ids(const int *ids, long long n, int G, long long *ptr, cudaStream_t s);
 
 // canonical PP order by pre-order rank in the arena's prefix tree (one
@@ -239,7 +241,7 @@ cudaError_t tour_lengths(const GraphDev &g, long long *scan_tmp, cudaStream_t s)
 cudaError_t tour_fill(const GraphDev &g, cudaStream_t s);
 
 // testpaths.cu
-cudaError_t tp_lengths(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
+cudaError_t tp_lengths(const long long *pp_off, const int2 *pp_ends, const int *pp_graph, long long P,
                        const GraphDev &g, long long *tp_len, int *run_start, int *tp_graph, int *err,
                        cudaStream_t s);
 cudaError_t tp_write(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,

@@ -50,7 +50,7 @@ __device__ __forceinline__ int key_cmp(long long a, long long b, const long long
 // number of walks in flight sets its speed.  A PP is
 // refs[i] = (level << 32 | index in level), or, with refs == nullptr, index
 // single_refs[i] in level single_level.  out_graph (optional) receives the
-// graph id of each PP.
+// graph id of each PP, out_ends (optional) its (first, last) local vertex.
 static_assert(TPG_MAX_N <= 65536, "local vertex ids fit 16 bits");
 constexpr int MAT_BUF = 1536;  // local vertex ids (uint16, < TPG_MAX_N) per warp: 32 PPs of up to 48 vertices
 constexpr int MAT_MAX_LV = 512; // level-pointer table cached in shared memory up to this many levels
@@ -69,7 +69,8 @@ template <int NWARPS>
 __device__ __forceinline__ void materialize_warps(const long long *refs, const int *single_refs, int single_level,
                                                   long long n, const long long *offsets, const LevelRec *levels,
                                                   const GraphDev &g, int *out, int *out_graph,
-                                                  unsigned short (&buf)[NWARPS][MAT_BUF], int2 *const *lvl_nodes) {
+                                                  unsigned short (&buf)[NWARPS][MAT_BUF], int2 *const *lvl_nodes,
+                                                  int2 *out_ends = nullptr) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long nwarps = (long long)gridDim.x * NWARPS;
     for (long long w0 = (blockIdx.x * (long long)NWARPS + wid) * 32; w0 < n; w0 += nwarps * 32) {
@@ -91,17 +92,20 @@ __device__ __forceinline__ void materialize_warps(const long long *refs, const i
         const long long span = offsets[w_end_idx] - start;
         const long long off = valid ? offsets[idx] : 0;
         const bool staged = span <= MAT_BUF;
-        int node = rel, root = 0;
+        int node = rel, root = 0, first_loc = 0, last_loc = 0;
         for (int j = level; j >= 1; --j) {
             const int2 rec = lvl_nodes ? lvl_nodes[j][node] : levels[j].nodes[node];
             const int v = rec.x;
             const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
             if (staged) buf[wid][off - start + (j - 1)] = (unsigned short)loc;
             else out[off + (j - 1)] = loc;
+            if (j == level) last_loc = loc;
+            first_loc = loc;
             root = v;
             node = rec.y;
         }
         if (valid && out_graph) out_graph[idx] = g.vgraph ? g.vgraph[root] : 0;
+        if (valid && out_ends) out_ends[idx] = make_int2(first_loc, last_loc);
         if (staged) {
             __syncwarp();
             for (long long t = lane; t < span; t += 32) out[start + t] = (int)buf[wid][t];

@@ -23,14 +23,18 @@ static unsigned grid_for(long long n, int block = 256) {
     return (unsigned)b;
 }
 
-__global__ void tp_len_kernel(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
-                              GraphDev g, long long *tp_len, int *run_start, int *tp_graph, int *err) {
+// TP lengths and run starts from each PP's (first, last) local vertex, which
+// the materialisation wrote beside the PP list (coalesced reads only).
+__global__ void tp_len_kernel(const long long *__restrict__ pp_off, const int2 *__restrict__ pp_ends,
+                              const int *__restrict__ pp_graph, long long P, GraphDev g, long long *tp_len,
+                              int *run_start, int *tp_graph, int *err) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
          i += (long long)gridDim.x * blockDim.x) {
         const long long o0 = pp_off[i], o1 = pp_off[i + 1];
         const int gid = pp_graph ? pp_graph[i] : 0;
         const int vb = g.vgraph ? g.vbase[gid] : 0;
-        const int f = pp_vert[o0] + vb, l = pp_vert[o1 - 1] + vb;
+        const int2 e = pp_ends[i];
+        const int f = e.x + vb, l = e.y + vb;
         const int pl = g.pre_len[f], sl = g.suf_len[l];
         long long len = 0;
         if (pl == 0 || sl == 0) atomicOr(err, ERR_UNREACH);
@@ -40,17 +44,17 @@ __global__ void tp_len_kernel(const long long *pp_off, const int *pp_vert, const
         int start = 1;
         if (i > 0) {
             const int gprev = pp_graph ? pp_graph[i - 1] : 0;
-            start = (gprev != gid) || (pp_vert[pp_off[i - 1]] != pp_vert[o0]);
+            start = (gprev != gid) || (pp_ends[i - 1].x != e.x);
         }
         run_start[i] = start;
     }
 }
 
-cudaError_t tp_lengths(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
+cudaError_t tp_lengths(const long long *pp_off, const int2 *pp_ends, const int *pp_graph, long long P,
                        const GraphDev &g, long long *tp_len, int *run_start, int *tp_graph, int *err,
                        cudaStream_t s) {
     if (P <= 0) return cudaSuccess;
-    tp_len_kernel<<<grid_for(P), 256, 0, s>>>(pp_off, pp_vert, pp_graph, P, g, tp_len, run_start, tp_graph, err);
+    tp_len_kernel<<<grid_for(P), 256, 0, s>>>(pp_off, pp_ends, pp_graph, P, g, tp_len, run_start, tp_graph, err);
     note_launch();
     return cudaGetLastError();
 }
