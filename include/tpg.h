@@ -67,6 +67,7 @@ typedef struct tpg_paths {
                                        [graph_path_ptr[g], graph_path_ptr[g+1]) */
     const int64_t *offsets;         /* [P+1], offsets[0] = 0 */
     const int32_t *vertices;        /* [offsets[P]], graph-local vertex ids, canonical order per graph */
+    int64_t num_vertices;           /* offsets[P], so that no read of a device array is needed */
 } tpg_paths;
 
 /* Statistics of the last tpg_prime_paths call on a handle. */

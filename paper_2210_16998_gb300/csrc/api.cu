@@ -234,6 +234,65 @@ PinnedPool &pinned() {
     return *pool;
 }
 
+// Process-wide pool of the per-handle host resources: the 16 KB page-locked
+// staging block (small read-backs in its first 4 KB, the level table of
+// graphs of up to 188 vertices in the rest), carved from 2 MB slabs (pinning
+// host memory takes hundreds of microseconds per call, as long as a small
+// graph's whole hot path), and the timing events, kept per device.
+struct HandlePool {
+    static constexpr size_t SMALL = 16384, SLAB = (size_t)2 << 20, LEVELS_AT = 4096;
+    std::mutex mu;
+    std::vector<void *> small;
+    std::map<int, std::vector<cudaEvent_t>> events;
+
+    void *get_small() {
+        std::lock_guard<std::mutex> lk(mu);
+        if (small.empty()) {
+            char *p = nullptr;
+            if (cudaHostAlloc((void **)&p, SLAB, cudaHostAllocPortable) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            for (size_t o = SLAB; o >= SMALL; o -= SMALL) small.push_back(p + o - SMALL);
+        }
+        void *p = small.back();
+        small.pop_back();
+        return p;
+    }
+    void put_small(void *p) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        small.push_back(p);
+    }
+    // n events of the current device `dev`; false (and none taken) on failure
+    bool get_events(int dev, cudaEvent_t *ev, int n) {
+        std::lock_guard<std::mutex> lk(mu);
+        auto &v = events[dev];
+        for (int i = 0; i < n; ++i) {
+            if (!v.empty()) {
+                ev[i] = v.back();
+                v.pop_back();
+            } else if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+                cudaGetLastError();
+                for (int j = 0; j < i; ++j) v.push_back(ev[j]);
+                for (int j = 0; j < n; ++j) ev[j] = nullptr;
+                return false;
+            }
+        }
+        return true;
+    }
+    void put_events(int dev, cudaEvent_t *ev, int n) {
+        std::lock_guard<std::mutex> lk(mu);
+        auto &v = events[dev];
+        for (int i = 0; i < n; ++i)
+            if (ev[i]) v.push_back(ev[i]);
+    }
+};
+HandlePool &handle_pool() {
+    static HandlePool *pool = new HandlePool();  // never destroyed: freed with the process
+    return *pool;
+}
+
 void host_copy_unref(HostCopy *h) {
     if (h && h->refs.fetch_sub(1) == 1) {
         pinned().put(h->p);
@@ -343,7 +402,9 @@ struct tpg_cfg {
     long long out_cap[4] = {0, 0, 0, 0};  // explicit output capacities P, V, TV0, TV (0 = last run)
     unsigned long long *root_counts = nullptr;  // set while a counting run is in progress
     std::vector<LevelRec> h_levels;
-    int *h_small = nullptr;  // pinned staging for small read-backs (4 KB)
+    int *h_small = nullptr;  // pinned staging for small read-backs (16 KB, see HandlePool)
+    void *h_lvl_stage = nullptr;  // pinned staging for level tables too large for h_small
+    size_t h_lvl_bytes = 0;
 };
 
 // one training batch of the learned sizer: a copy of a handle's graph,
@@ -432,9 +493,9 @@ void destroy_cfg(tpg_cfg *g) {
     for (auto &b : g->node_segs) release(g, b);
     for (auto &b : g->pp_segs) release(g, b);
     cudaStreamSynchronize(g->stream);
-    if (g->h_small) cudaFreeHost(g->h_small);
-    for (cudaEvent_t e : g->ev)
-        if (e) cudaEventDestroy(e);
+    handle_pool().put_small(g->h_small);
+    handle_pool().put_events(g->device, g->ev, 8);
+    pinned().put(g->h_lvl_stage);
     g->magic = MAGIC_DEAD;
     delete g;
 }
@@ -468,11 +529,9 @@ int new_cfg(void *stream, tpg_cfg **out) {
     g->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&g->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess ||
-        cudaHostAlloc((void **)&g->h_small, 4096, cudaHostAllocDefault) != cudaSuccess ||
-        cudaEventCreate(&g->ev[0]) || cudaEventCreate(&g->ev[1]) || cudaEventCreate(&g->ev[2]) ||
-        cudaEventCreate(&g->ev[3]) || cudaEventCreate(&g->ev[4]) || cudaEventCreate(&g->ev[5]) ||
-        cudaEventCreate(&g->ev[6]) || cudaEventCreate(&g->ev[7])) {
+        !(g->h_small = (int *)handle_pool().get_small()) || !handle_pool().get_events(g->device, g->ev, 8)) {
         cudaGetLastError();
+        handle_pool().put_small(g->h_small);
         delete g;
         return TPG_ECUDA;
     }
@@ -481,9 +540,13 @@ int new_cfg(void *stream, tpg_cfg **out) {
 }
 
 // Predecessor CSR, BFS tables and tour tables (everything after the union
-// CSR, vgraph/vbase and entry/exit are on the device).
-int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h) {
+// CSR, vgraph/vbase and entry/exit are on the device).  validate: check the
+// CSR on the device first, TPG_EINVAL if it fails (a single graph whose
+// entry and exit are given; the caller has zeroed the handle's error word).
+int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h, bool validate = false, int entry = 0,
+               int exit = 0) {
     cudaStream_t s = g->stream;
+    const bool small = g->G == 1 && g->N <= PREP_SMALL_N;
     g->W = bitset_words_supported(g->maxn);
     if (g->W < 0) return TPG_ETOOBIG;
     g->max_levels = g->maxn + 4;
@@ -497,11 +560,18 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h) {
     RC(ensure(g, g->suf_len, sizeof(int) * g->N));
     RC(ensure(g, g->pre_off, sizeof(long long) * (g->N + 1)));
     RC(ensure(g, g->suf_off, sizeof(long long) * (g->N + 1)));
-    RC(ensure(g, g->s_i32[0], sizeof(int) * (g->N + 1)));
-    RC(ensure(g, g->s_i64[0], sizeof(long long) * (g->N + 2)));
-    RC(ensure(g, g->s_tmp, sizeof(long long) * scan_tmp_elems(g->N + 1)));
-    CK(cudaMemcpyAsync(g->tbl_base.p, tbl_base_h.data(), sizeof(long long) * tbl_base_h.size(),
-                       cudaMemcpyHostToDevice, s));
+    if (small) {
+        const long long bound = (long long)g->N * (g->N + 1) / 2;
+        RC(ensure(g, g->pre_seq, sizeof(int) * bound));
+        RC(ensure(g, g->suf_seq, sizeof(int) * bound));
+        RC(ensure(g, g->ctl, CTL_BYTES));
+    } else {
+        RC(ensure(g, g->s_i32[0], sizeof(int) * (g->N + 1)));
+        RC(ensure(g, g->s_i64[0], sizeof(long long) * (g->N + 2)));
+        RC(ensure(g, g->s_tmp, sizeof(long long) * scan_tmp_elems(g->N + 1)));
+        CK(cudaMemcpyAsync(g->tbl_base.p, tbl_base_h.data(), sizeof(long long) * tbl_base_h.size(),
+                           cudaMemcpyHostToDevice, s));
+    }
 
     GraphDev &d = g->gd;
     d = GraphDev{};
@@ -525,6 +595,24 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h) {
     d.suf_len = g->suf_len.as<int>();
     d.pre_off = g->pre_off.as<long long>();
     d.suf_off = g->suf_off.as<long long>();
+
+    if (small) {
+        d.pre_seq = g->pre_seq.as<int>();
+        d.suf_seq = g->suf_seq.as<int>();
+        if (!validate) CK(cudaMemsetAsync(g->ctl.p, 0, sizeof(int), s));
+        CK(preprocess_small(d, g->prp.as<int>(), g->pcol.as<int>(), g->tbl_base.as<long long>(), validate, entry,
+                            exit, g->ctl.as<int>(), s));
+        if (!validate) return TPG_OK;  // launch errors surfaced above; the next call's read-back sees the rest
+        CK(cudaMemcpyAsync(g->h_small, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return (g->h_small[0] & ERR_INVAL) ? TPG_EINVAL : TPG_OK;
+    }
+    if (validate) {
+        CK(validate_csr_device(d.rp, d.col, g->N, g->M, entry, exit, g->ctl.as<int>(), s));
+        CK(cudaMemcpyAsync(g->h_small, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (g->h_small[0] & ERR_INVAL) return TPG_EINVAL;
+    }
 
     CK(build_pred_csr(d, g->prp.as<int>(), g->pcol.as<int>(), g->s_i32[0].as<int>(), g->s_tmp.as<long long>(),
                       g->s_i64[0].as<long long>(), s));
@@ -588,6 +676,19 @@ int prepare_segments(tpg_cfg *g, std::vector<DevBuf> &segs, size_t elem, long lo
     return push_segment(g, segs, elem, (long long)(need / elem));
 }
 
+// Page-locked staging for a level-table read-back of `bytes` (a pageable
+// destination would make the copy synchronous and slower); nullptr if none
+// can be had.
+void *level_stage(tpg_cfg *g, size_t bytes) {
+    if (bytes <= HandlePool::SMALL - HandlePool::LEVELS_AT) return (char *)g->h_small + HandlePool::LEVELS_AT;
+    if (g->h_lvl_bytes < bytes) {
+        pinned().put(g->h_lvl_stage);
+        g->h_lvl_stage = pinned().get(bytes);
+        g->h_lvl_bytes = g->h_lvl_stage ? bytes : 0;
+    }
+    return g->h_lvl_stage;
+}
+
 int enumerate_levels(tpg_cfg *g) {
     cudaStream_t s = g->stream;
     if (g->node_cap == 0) {
@@ -647,10 +748,13 @@ int enumerate_levels(tpg_cfg *g) {
         g->stats.tile_block = g->shape.block;
         g->stats.tile_items = g->shape.items;
         g->h_levels.resize(g->max_levels);
-        CK(cudaMemcpyAsync(g->h_levels.data(), g->levels.p, sizeof(LevelRec) * g->max_levels,
-                           cudaMemcpyDeviceToHost, s));
+        const size_t lv_bytes = sizeof(LevelRec) * g->max_levels;
+        void *stage = level_stage(g, lv_bytes);
+        CK(cudaMemcpyAsync(stage ? stage : (void *)g->h_levels.data(), g->levels.p, lv_bytes, cudaMemcpyDeviceToHost,
+                           s));
         CK(cudaMemcpyAsync(g->h_small, g->ctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        if (stage) std::memcpy(g->h_levels.data(), stage, lv_bytes);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]);
         total_ms += ms;
@@ -831,6 +935,7 @@ int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, l
     r->pub.magic = MAGIC_PATHS;
     r->pub.num_graphs = g->G;
     r->pub.num_paths = P;
+    r->pub.num_vertices = V;
     r->location = g->location;
     r->pub.location = g->location;
     if (g->location == TPG_RESULT_DEVICE) {
@@ -1412,18 +1517,12 @@ int tpg_load_cfg_device(int32_t n, int32_t m, const int32_t *row_ptr_dev, const 
             cudaMemcpyAsync(g->entry.p, hs, sizeof(int), cudaMemcpyHostToDevice, s) ||
             cudaMemcpyAsync(g->exitv.p, hs + 1, sizeof(int), cudaMemcpyHostToDevice, s) ||
             cudaMemcpyAsync(g->vbase.p, hs + 2, 2 * sizeof(int), cudaMemcpyHostToDevice, s) ||
-            cudaMemsetAsync(g->ctl.p, 0, sizeof(int), s) ||
-            validate_csr_device(g->rp.as<int>(), g->col.as<int>(), n, m, entry, exit, g->ctl.as<int>(), s) ||
-            cudaMemcpyAsync(hs + 8, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s)) {
+            cudaMemsetAsync(g->ctl.p, 0, sizeof(int), s)) {
             rc = TPG_ECUDA;
             cudaGetLastError();
             break;
         }
-        if (hs[8] & ERR_INVAL) {
-            rc = TPG_EINVAL;
-            break;
-        }
-        rc = preprocess(g, {0, (long long)n * n});
+        rc = preprocess(g, {0, (long long)n * n}, true, entry, exit);
     } while (false);
     if (rc) {
         destroy_cfg(g);

@@ -236,7 +236,15 @@ cudaError_t validate_csr_device(const int *rp, const int *col, int n, long long 
                                 int *err, cudaStream_t s);
 cudaError_t build_pred_csr(const GraphDev &g, int *prp, int *pcol, int *indeg_tmp, long long *scan_tmp,
                            long long *scan_buf, cudaStream_t s);
-cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s);
+// gate (optional): a device flag; the BFS does nothing when it is nonzero
+cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s, const int *gate = nullptr);
+// One graph of at most PREP_SMALL_N vertices: optional CSR validation (sets
+// ERR_INVAL in *err, which must be zero on entry, and skips the rest), the
+// predecessor CSR, tbl_base, the BFS tables and the tour tables in three
+// launches; g.pre_seq / g.suf_seq must hold N(N+1)/2 entries each.
+constexpr int PREP_SMALL_N = 1024;
+cudaError_t preprocess_small(const GraphDev &g, int *prp, int *pcol, long long *tbl_base, bool validate, int entry,
+                             int exit, int *err, cudaStream_t s);
 cudaError_t tour_lengths(const GraphDev &g, long long *scan_tmp, cudaStream_t s);
 cudaError_t tour_fill(const GraphDev &g, cudaStream_t s);
 

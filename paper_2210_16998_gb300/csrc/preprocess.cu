@@ -32,26 +32,31 @@ cudaError_t build_union_csr(const int *, const long long *rp_base_dev, const lon
     return cudaGetLastError();
 }
 
-// Device-side validation of one CSR (same rules as the host check).
-__global__ void validate_kernel(const int *rp, const int *col, int n, long long m, int entry, int exit,
-                                int *err) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
-    int bad = 0;
+// Device-side validation of one CSR (same rules as the host check): thread
+// tid of `stride` checks vertices tid, tid + stride, ...; true if it found a
+// violation.
+__device__ __forceinline__ bool csr_invalid(const int *rp, const int *col, int n, long long m, int entry, int exit,
+                                            int tid, int stride) {
     if (tid == 0) {
-        if (rp[0] != 0 || (long long)rp[n] != m) bad = 1;
-        if (entry < 0 || entry >= n || exit < 0 || exit >= n || entry == exit) bad = 1;
-        else if (rp[exit + 1] != rp[exit]) bad = 1;
+        if (rp[0] != 0 || (long long)rp[n] != m) return true;
+        if (entry < 0 || entry >= n || exit < 0 || exit >= n || entry == exit) return true;
+        if (rp[exit + 1] != rp[exit]) return true;
     }
-    for (int u = tid; u < n && !bad; u += stride) {
+    for (int u = tid; u < n; u += stride) {
         const int a = rp[u], b = rp[u + 1];
-        if (b < a || a < 0 || (long long)b > m) { bad = 1; break; }
+        if (b < a || a < 0 || (long long)b > m) return true;
         for (int e = a; e < b; ++e) {
             const int w = col[e];
-            if (w < 0 || w >= n || (e > a && w <= col[e - 1]) || w == entry) { bad = 1; break; }
+            if (w < 0 || w >= n || (e > a && w <= col[e - 1]) || w == entry) return true;
         }
     }
-    if (bad) atomicOr(err, ERR_INVAL);
+    return false;
+}
+
+__global__ void validate_kernel(const int *rp, const int *col, int n, long long m, int entry, int exit,
+                                int *err) {
+    if (csr_invalid(rp, col, n, m, entry, exit, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x))
+        atomicOr(err, ERR_INVAL);
 }
 
 cudaError_t validate_csr_device(const int *rp, const int *col, int n, long long m, int entry, int exit, int *err,
@@ -125,8 +130,9 @@ cudaError_t build_pred_csr(const GraphDev &g, int *prp, int *pcol, int *indeg_tm
 // an arc u -> x and dist(u) = d.
 constexpr int BFS_BLOCK = 128;
 
-__global__ void __launch_bounds__(BFS_BLOCK) bfs_kernel(GraphDev g) {
+__global__ void __launch_bounds__(BFS_BLOCK) bfs_kernel(GraphDev g, const int *gate) {
     extern __shared__ int dist_s[];
+    if (gate && *gate) return;  // the CSR failed validation
     const int a = blockIdx.x;
     const int gid = g.vgraph ? g.vgraph[a] : 0;
     const int vb = g.vgraph ? g.vbase[gid] : 0;
@@ -159,57 +165,61 @@ __global__ void __launch_bounds__(BFS_BLOCK) bfs_kernel(GraphDev g) {
     for (int x = threadIdx.x; x < ng; x += BFS_BLOCK) drow[x] = dist_s[x];
 }
 
-cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s) {
+cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s, const int *gate) {
     const size_t smem = sizeof(int) * (size_t)g.maxn;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    bfs_kernel<<<g.N, BFS_BLOCK, smem, s>>>(g);
+    bfs_kernel<<<g.N, BFS_BLOCK, smem, s>>>(g, gate);
     note_launch();
     return cudaGetLastError();
 }
 
 // pre_len[v] = vertices of path(entry -> v) (0 if none); suf_len[v] = vertices
 // of path(v -> exit).
+__device__ __forceinline__ void tour_len_one(const GraphDev &g, int v) {
+    const int gid = g.vgraph ? g.vgraph[v] : 0;
+    const int vb = g.vgraph ? g.vbase[gid] : 0;
+    const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
+    const int en = g.entry[gid] - vb, ex = g.exit[gid] - vb, vl = v - vb;
+    const int *D = g.dist + g.tbl_base[gid];
+    const int d1 = D[(long long)en * ng + vl];
+    const int d2 = D[(long long)vl * ng + ex];
+    g.pre_len[v] = d1 >= 0 ? d1 + 1 : 0;
+    g.suf_len[v] = d2 >= 0 ? d2 + 1 : 0;
+}
+
 __global__ void tour_len_kernel(GraphDev g) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x) {
-        const int gid = g.vgraph ? g.vgraph[v] : 0;
-        const int vb = g.vgraph ? g.vbase[gid] : 0;
-        const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
-        const int en = g.entry[gid] - vb, ex = g.exit[gid] - vb, vl = v - vb;
-        const int *D = g.dist + g.tbl_base[gid];
-        const int d1 = D[(long long)en * ng + vl];
-        const int d2 = D[(long long)vl * ng + ex];
-        g.pre_len[v] = d1 >= 0 ? d1 + 1 : 0;
-        g.suf_len[v] = d2 >= 0 ? d2 + 1 : 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x) tour_len_one(g, v);
+}
+
+__device__ __forceinline__ void tour_fill_one(const GraphDev &g, int v) {
+    const int gid = g.vgraph ? g.vgraph[v] : 0;
+    const int vb = g.vgraph ? g.vbase[gid] : 0;
+    const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
+    const int en = g.entry[gid] - vb, ex = g.exit[gid] - vb, vl = v - vb;
+    const int *P = g.pred + g.tbl_base[gid];
+    // path(entry -> v), backwards from v through P[entry][.]
+    int len = g.pre_len[v];
+    int *dst = g.pre_seq + g.pre_off[v];
+    int x = vl;
+    for (int i = len - 1; i >= 0; --i) {
+        dst[i] = x;
+        if (i > 0) x = P[(long long)en * ng + x];
+    }
+    // path(v -> exit), backwards from exit through P[v][.]
+    len = g.suf_len[v];
+    dst = g.suf_seq + g.suf_off[v];
+    x = ex;
+    for (int i = len - 1; i >= 0; --i) {
+        dst[i] = x;
+        if (i > 0) x = P[(long long)vl * ng + x];
     }
 }
 
 __global__ void tour_fill_kernel(GraphDev g) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x) {
-        const int gid = g.vgraph ? g.vgraph[v] : 0;
-        const int vb = g.vgraph ? g.vbase[gid] : 0;
-        const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
-        const int en = g.entry[gid] - vb, ex = g.exit[gid] - vb, vl = v - vb;
-        const int *P = g.pred + g.tbl_base[gid];
-        // path(entry -> v), backwards from v through P[entry][.]
-        int len = g.pre_len[v];
-        int *dst = g.pre_seq + g.pre_off[v];
-        int x = vl;
-        for (int i = len - 1; i >= 0; --i) {
-            dst[i] = x;
-            if (i > 0) x = P[(long long)en * ng + x];
-        }
-        // path(v -> exit), backwards from exit through P[v][.]
-        len = g.suf_len[v];
-        dst = g.suf_seq + g.suf_off[v];
-        x = ex;
-        for (int i = len - 1; i >= 0; --i) {
-            dst[i] = x;
-            if (i > 0) x = P[(long long)vl * ng + x];
-        }
-    }
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x) tour_fill_one(g, v);
 }
 
 cudaError_t tour_lengths(const GraphDev &g, long long *scan_tmp, cudaStream_t s) {
@@ -223,6 +233,112 @@ cudaError_t tour_lengths(const GraphDev &g, long long *scan_tmp, cudaStream_t s)
 
 cudaError_t tour_fill(const GraphDev &g, cudaStream_t s) {
     tour_fill_kernel<<<grid_for(g.N), 256, 0, s>>>(g);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// one graph of at most PREP_SMALL_N vertices: the steps above in three
+// launches (this kernel, the BFS, tour_small_kernel) and no host round trip
+// but the final error check
+// ---------------------------------------------------------------------------
+constexpr int PREP_BLOCK = 1024;
+
+// Optional CSR validation (an invalid CSR sets ERR_INVAL in *err and nothing
+// else runs), then the predecessor CSR with ascending lists and the table
+// base {0, N*N}.  Dynamic shared memory: N + 1 ints.
+__global__ void __launch_bounds__(PREP_BLOCK) prep_small_kernel(GraphDev g, int *prp, int *pcol,
+                                                                long long *tbl_base, int validate, int entry,
+                                                                int exit, int *err) {
+    extern __shared__ int s_cur[];
+    __shared__ int s_bad;
+    const int N = g.N, tid = threadIdx.x;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    if (validate) {
+        if (csr_invalid(g.rp, g.col, N, g.M, entry, exit, tid, PREP_BLOCK)) s_bad = 1;
+        __syncthreads();
+        if (s_bad) {
+            if (tid == 0) atomicOr(err, ERR_INVAL);
+            return;
+        }
+    }
+    for (int v = tid; v <= N; v += PREP_BLOCK) s_cur[v] = 0;
+    __syncthreads();
+    for (long long e = tid; e < g.M; e += PREP_BLOCK) atomicAdd(&s_cur[g.col[e]], 1);
+    __syncthreads();
+    // exclusive scan of the in-degrees: prp, and the scatter cursors
+    long long carry = 0;
+    for (int base = 0; base <= N; base += PREP_BLOCK) {
+        const int v = base + tid;
+        const long long c = v < N ? s_cur[v] : 0;
+        long long tot = 0;
+        const long long ex = block_excl_scan_i64<PREP_BLOCK>(c, tot);
+        if (v <= N) {
+            prp[v] = (int)(carry + ex);
+            s_cur[v] = (int)(carry + ex);
+        }
+        carry += tot;
+    }
+    if (tid == 0) {
+        tbl_base[0] = 0;
+        tbl_base[1] = (long long)N * N;
+    }
+    __syncthreads();
+    for (int u = tid; u < N; u += PREP_BLOCK)
+        for (int e = g.rp[u]; e < g.rp[u + 1]; ++e) pcol[atomicAdd(&s_cur[g.col[e]], 1)] = u;
+    __syncthreads();
+    for (int v = tid; v < N; v += PREP_BLOCK) {
+        const int a = prp[v], b = prp[v + 1];
+        for (int i = a + 1; i < b; ++i) {
+            const int x = pcol[i];
+            int j = i - 1;
+            while (j >= a && pcol[j] > x) {
+                pcol[j + 1] = pcol[j];
+                --j;
+            }
+            pcol[j + 1] = x;
+        }
+    }
+}
+
+// Tour lengths, their offsets and the tour sequences of one graph in one
+// block; pre_seq and suf_seq hold N(N+1)/2 entries each, an upper bound (the
+// i-th vertex in order of distance from the entry is at most i arcs away, so
+// its path has at most i + 1 vertices; the same toward the exit).
+__global__ void __launch_bounds__(PREP_BLOCK) tour_small_kernel(GraphDev g, const int *gate) {
+    if (*gate) return;
+    const int N = g.N, tid = threadIdx.x;
+    for (int v = tid; v < N; v += PREP_BLOCK) tour_len_one(g, v);
+    __syncthreads();
+    long long cp = 0, cs = 0;
+    for (int base = 0; base <= N; base += PREP_BLOCK) {
+        const int v = base + tid;
+        const long long a = v < N ? g.pre_len[v] : 0, b = v < N ? g.suf_len[v] : 0;
+        long long ta = 0, tb = 0;
+        const long long ea = block_excl_scan_i64<PREP_BLOCK>(a, ta);
+        const long long eb = block_excl_scan_i64<PREP_BLOCK>(b, tb);
+        if (v <= N) {
+            g.pre_off[v] = cp + ea;
+            g.suf_off[v] = cs + eb;
+        }
+        cp += ta;
+        cs += tb;
+    }
+    __syncthreads();
+    for (int v = tid; v < N; v += PREP_BLOCK) tour_fill_one(g, v);
+}
+
+cudaError_t preprocess_small(const GraphDev &g, int *prp, int *pcol, long long *tbl_base, bool validate, int entry,
+                             int exit, int *err, cudaStream_t s) {
+    if (g.G != 1 || g.N > PREP_SMALL_N) return cudaErrorInvalidValue;
+    prep_small_kernel<<<1, PREP_BLOCK, sizeof(int) * (g.N + 1), s>>>(g, prp, pcol, tbl_base, validate ? 1 : 0,
+                                                                     entry, exit, err);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = bfs_all_pairs(g, s, err)) != cudaSuccess) return e;
+    tour_small_kernel<<<1, PREP_BLOCK, 0, s>>>(g, err);
     note_launch();
     return cudaGetLastError();
 }

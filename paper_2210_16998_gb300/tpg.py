@@ -53,6 +53,7 @@ class _Paths(ctypes.Structure):
         ("graph_path_ptr", ctypes.c_void_p),
         ("offsets", ctypes.c_void_p),
         ("vertices", ctypes.c_void_p),
+        ("num_vertices", ctypes.c_int64),
     ]
 
 
@@ -275,7 +276,7 @@ class Paths:
                                        shape=(self.num_graphs + 1,))
             off = np.ctypeslib.as_array(ctypes.cast(p.offsets, ctypes.POINTER(ctypes.c_int64)),
                                         shape=(self.num_paths + 1,))
-            nv = int(off[-1])
+            nv = int(p.num_vertices)
             vert = (np.ctypeslib.as_array(ctypes.cast(p.vertices, ctypes.POINTER(ctypes.c_int32)), shape=(nv,))
                     if nv else np.zeros(0, np.int32))
             self.graph_path_ptr, self.offsets, self.vertices = gp, off, vert
@@ -285,13 +286,13 @@ class Paths:
             self.graph_path_ptr = torch.as_tensor(_CudaArray(p.graph_path_ptr, (self.num_graphs + 1,), "<i8"),
                                                   device="cuda")
             self.offsets = torch.as_tensor(_CudaArray(p.offsets, (self.num_paths + 1,), "<i8"), device="cuda")
-            nv = int(self.offsets[-1].item())
+            nv = int(p.num_vertices)
             self.vertices = (torch.as_tensor(_CudaArray(p.vertices, (nv,), "<i4"), device="cuda")
                              if nv else torch.zeros(0, dtype=torch.int32, device="cuda"))
 
     @property
     def num_vertices(self) -> int:
-        return int(self.offsets[-1])
+        return int(self._ptr.contents.num_vertices) if self._ptr is not None else int(self.offsets[-1])
 
     def host_arrays(self):
         """(graph_path_ptr, offsets, vertices) as numpy copies."""

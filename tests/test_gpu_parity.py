@@ -33,11 +33,13 @@ def gpu_run(cfg, location=tpg.TPG_RESULT_HOST, test_paths=True, capacity=None, s
             tpg.tpg_set_tile_shape(h, *shape)
         pp = tpg.tpg_prime_paths(h)
         ppa = pp.host_arrays()
+        assert pp.num_vertices == int(ppa[1][-1])  # the count the library reports, read from offsets
         pp.free()
         tpa = None
         if test_paths:
             tp = tpg.tpg_test_paths(h)
             tpa = tp.host_arrays()
+            assert tp.num_vertices == int(tpa[1][-1])
             tp.free()
         stats = tpg.tpg_get_stats(h)
     return ppa, tpa, stats
@@ -154,6 +156,62 @@ def test_device_load_rejects_bad_csr():
     with pytest.raises(tpg.TPGError) as e:
         tpg.tpg_load_cfg_device(2, 2, rp, col, 0, 1)
     assert e.value.code == tpg.TPG_EINVAL
+
+
+def _chain_csr(n):
+    """0 -> 1 -> ... -> n-1: one PP, the whole chain."""
+    rp = np.minimum(np.arange(n + 1), n - 1).astype(np.int32)
+    col = np.arange(1, n, dtype=np.int32)
+    return rp, col
+
+
+# 6 vertices take the single-block preprocessing, 1500 the general one
+@pytest.mark.parametrize("n", [6, 1500])
+@pytest.mark.parametrize("bad", ["arc_into_entry", "vertex_out_of_range", "arc_out_of_exit", "row_ptr_start",
+                                 "entry_is_exit", "unsorted_row"])
+def test_device_load_rejects_bad_csr_on_both_preprocessing_paths(n, bad):
+    import torch
+
+    rp, col = _chain_csr(n)
+    entry, exit = 0, n - 1
+    if bad == "arc_into_entry":
+        col[n // 2] = 0
+    elif bad == "vertex_out_of_range":
+        col[1] = n
+    elif bad == "arc_out_of_exit":
+        rp[n] = n
+        col = np.append(col, 1).astype(np.int32)
+    elif bad == "row_ptr_start":
+        rp[0] = 1
+    elif bad == "entry_is_exit":
+        exit = 0
+    elif bad == "unsorted_row":
+        # vertex 1 gets arcs (3, 2): out of order
+        rp = np.concatenate([[0, 1], np.arange(3, n + 1), [n]]).astype(np.int32)
+        col = np.concatenate([[1, 3, 2], np.arange(3, n)]).astype(np.int32)
+    m = int(rp[n])
+    assert len(col) >= m
+    with pytest.raises(tpg.TPGError) as e:
+        tpg.tpg_load_cfg_device(n, m, torch.as_tensor(rp, device="cuda"), torch.as_tensor(col, device="cuda"),
+                                entry, exit)
+    assert e.value.code == tpg.TPG_EINVAL
+
+
+@pytest.mark.parametrize("n", [6, 1000, 1025, 1500])
+def test_device_load_chain_on_both_preprocessing_paths(n):
+    import torch
+
+    rp, col = _chain_csr(n)
+    with tpg.tpg_load_cfg_device(n, n - 1, torch.as_tensor(rp, device="cuda"), torch.as_tensor(col, device="cuda"),
+                                 0, n - 1) as h:
+        pp = tpg.tpg_prime_paths(h)
+        tp = tpg.tpg_test_paths(h)
+        _, off, vert = pp.host_arrays()
+        _, toff, tvert = tp.host_arrays()
+        pp.free()
+        tp.free()
+    assert list(off) == [0, n] and list(vert) == list(range(n))
+    assert list(toff) == [0, n] and list(tvert) == list(range(n))
 
 
 def test_unreachable_reports_error():
