@@ -209,7 +209,7 @@ def run_ours(args, rank, world, local_rank):
         if check:
             assert tp.num_paths == pp.num_paths  # every PP already runs entry -> exit
             assert torch.equal(tp.vertices, pp.vertices)
-        st = tpg.tpg_get_stats(h)
+        st = tpg.tpg_get_stats(h, as_dict=False)  # converted after the timed region
         P = pp.num_paths
         pp.free()
         tp.free()
@@ -238,6 +238,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     launches = tpg.tpg_kernel_launches() - launches0
     clocks = sampler.stop() if sampler else None
+    stats = [tpg.stats_dict(s) for s in stats]
     ms = ev0.elapsed_time(ev1)
     t = torch.tensor([ms], device="cuda", dtype=torch.float64)
     if world > 1:

@@ -269,30 +269,48 @@ class Paths:
         p = ptr.contents
         self.num_graphs = int(p.num_graphs)
         self.num_paths = int(p.num_paths)
+        self.num_vertices = int(p.num_vertices)
         self.location = int(p.location)
         self._raw = (p.graph_path_ptr, p.offsets, p.vertices)
-        if self.location == TPG_RESULT_HOST:
-            gp = np.ctypeslib.as_array(ctypes.cast(p.graph_path_ptr, ctypes.POINTER(ctypes.c_int64)),
-                                       shape=(self.num_graphs + 1,))
-            off = np.ctypeslib.as_array(ctypes.cast(p.offsets, ctypes.POINTER(ctypes.c_int64)),
-                                        shape=(self.num_paths + 1,))
-            nv = int(p.num_vertices)
-            vert = (np.ctypeslib.as_array(ctypes.cast(p.vertices, ctypes.POINTER(ctypes.c_int32)), shape=(nv,))
-                    if nv else np.zeros(0, np.int32))
-            self.graph_path_ptr, self.offsets, self.vertices = gp, off, vert
-        else:
-            import torch
+        self._arrays = None  # built on first access (views of the library's buffers)
 
-            self.graph_path_ptr = torch.as_tensor(_CudaArray(p.graph_path_ptr, (self.num_graphs + 1,), "<i8"),
-                                                  device="cuda")
-            self.offsets = torch.as_tensor(_CudaArray(p.offsets, (self.num_paths + 1,), "<i8"), device="cuda")
-            nv = int(p.num_vertices)
-            self.vertices = (torch.as_tensor(_CudaArray(p.vertices, (nv,), "<i4"), device="cuda")
-                             if nv else torch.zeros(0, dtype=torch.int32, device="cuda"))
+    def _views(self):
+        if self._arrays is None:
+            if self._ptr is None:
+                raise ValueError("path list already freed")
+            gp_ptr, off_ptr, v_ptr = self._raw
+            nv = self.num_vertices
+            if self.location == TPG_RESULT_HOST:
+                gp = np.ctypeslib.as_array(ctypes.cast(gp_ptr, ctypes.POINTER(ctypes.c_int64)),
+                                           shape=(self.num_graphs + 1,))
+                off = np.ctypeslib.as_array(ctypes.cast(off_ptr, ctypes.POINTER(ctypes.c_int64)),
+                                            shape=(self.num_paths + 1,))
+                vert = (np.ctypeslib.as_array(ctypes.cast(v_ptr, ctypes.POINTER(ctypes.c_int32)), shape=(nv,))
+                        if nv else np.zeros(0, np.int32))
+            else:
+                import torch
+
+                gp = torch.as_tensor(_CudaArray(gp_ptr, (self.num_graphs + 1,), "<i8"), device="cuda")
+                off = torch.as_tensor(_CudaArray(off_ptr, (self.num_paths + 1,), "<i8"), device="cuda")
+                vert = (torch.as_tensor(_CudaArray(v_ptr, (nv,), "<i4"), device="cuda")
+                        if nv else torch.zeros(0, dtype=torch.int32, device="cuda"))
+            self._arrays = (gp, off, vert)
+        return self._arrays
 
     @property
-    def num_vertices(self) -> int:
-        return int(self._ptr.contents.num_vertices) if self._ptr is not None else int(self.offsets[-1])
+    def graph_path_ptr(self):
+        """[num_graphs + 1] int64: paths of graph g are [ptr[g], ptr[g+1])."""
+        return self._views()[0]
+
+    @property
+    def offsets(self):
+        """[num_paths + 1] int64."""
+        return self._views()[1]
+
+    @property
+    def vertices(self):
+        """[num_vertices] int32, graph-local vertex ids."""
+        return self._views()[2]
 
     def host_arrays(self):
         """(graph_path_ptr, offsets, vertices) as numpy copies."""
@@ -307,8 +325,8 @@ class Paths:
 
     def free(self):
         if self._ptr is not None:
-            # drop views first: device tensors alias library memory
-            self.graph_path_ptr = self.offsets = self.vertices = None
+            # drop views first: they alias library memory
+            self._arrays = None
             load_library().tpg_free(ctypes.cast(self._ptr, ctypes.c_void_p))
             self._ptr = None
 
@@ -456,9 +474,15 @@ def tpg_set_allocator(alloc=None, release=None):
     _callbacks = cb
 
 
-def tpg_get_stats(cfg: Cfg) -> dict:
+def tpg_get_stats(cfg: Cfg, as_dict: bool = True):
+    """Statistics of the handle's last calls: a dict, or with as_dict=False
+    the raw structure (cheaper; stats_dict() converts it later)."""
     st = _Stats()
     _check(load_library().tpg_get_stats(cfg.handle, ctypes.byref(st)), "tpg_get_stats")
+    return stats_dict(st) if as_dict else st
+
+
+def stats_dict(st) -> dict:
     return {name: (float(getattr(st, name)) if name.startswith("t_") else int(getattr(st, name)))
             for name, _ in _Stats._fields_}
 
