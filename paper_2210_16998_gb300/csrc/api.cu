@@ -358,7 +358,7 @@ struct tpg_cfg {
     int location = TPG_RESULT_HOST;
 
     int N = 0, G = 0, maxn = 0, W = 1, max_levels = 0;
-    long long M = 0;
+    long long M = 0, max_arcs = 0;  // arcs in total and in the graph with the most
     std::vector<int> h_vbase;
 
     DevBuf rp, col, prp, pcol, vgraph, vbase, entry, exitv, tbl_base, dist, pred;
@@ -616,7 +616,7 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h, bool valida
 
     CK(build_pred_csr(d, g->prp.as<int>(), g->pcol.as<int>(), g->s_i32[0].as<int>(), g->s_tmp.as<long long>(),
                       g->s_i64[0].as<long long>(), s));
-    CK(bfs_all_pairs(d, s));
+    CK(bfs_all_pairs(d, s, nullptr, g->max_arcs));
     CK(tour_lengths(d, g->s_tmp.as<long long>(), s));
     long long *h = (long long *)g->h_small;
     CK(cudaMemcpyAsync(h, d.pre_off + g->N, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -1455,6 +1455,7 @@ int tpg_load_cfg(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t 
     g->G = 1;
     g->maxn = n;
     g->M = m;
+    g->max_arcs = m;
     g->h_vbase = {0, n};
     int rc = TPG_OK;
     do {
@@ -1497,6 +1498,7 @@ int tpg_load_cfg_device(int32_t n, int32_t m, const int32_t *row_ptr_dev, const 
     g->G = 1;
     g->maxn = n;
     g->M = m;
+    g->max_arcs = m;
     g->h_vbase = {0, n};
     int rc = TPG_OK;
     do {
@@ -1540,7 +1542,7 @@ int tpg_load_cfg_batch(int32_t num_graphs, const int32_t *n_per_graph, const int
     const int G = num_graphs;
     std::vector<long long> rp_base(G + 1), arc_base(G + 1), tbl_base(G + 1);
     std::vector<int> vbase(G + 1), gent(G), gext(G);
-    long long N = 0, M = 0, R = 0, T = 0;
+    long long N = 0, M = 0, R = 0, T = 0, max_arcs = 0;
     int maxn = 0;
     for (int g = 0; g < G; ++g) {
         const int n = n_per_graph[g];
@@ -1556,6 +1558,7 @@ int tpg_load_cfg_batch(int32_t num_graphs, const int32_t *n_per_graph, const int
         gent[g] = entries[g] + (int)N;
         gext[g] = exits[g] + (int)N;
         M += rp[n];
+        max_arcs = std::max<long long>(max_arcs, rp[n]);
         R += n + 1;
         N += n;
         T += (long long)n * n;
@@ -1572,6 +1575,7 @@ int tpg_load_cfg_batch(int32_t num_graphs, const int32_t *n_per_graph, const int
     g->G = G;
     g->maxn = maxn;
     g->M = M;
+    g->max_arcs = max_arcs;
     g->h_vbase = vbase;
     int rc = TPG_OK;
     DevBuf t_rp, t_col, t_rpb, t_ab;

@@ -236,8 +236,10 @@ cudaError_t validate_csr_device(const int *rp, const int *col, int n, long long 
                                 int *err, cudaStream_t s);
 cudaError_t build_pred_csr(const GraphDev &g, int *prp, int *pcol, int *indeg_tmp, long long *scan_tmp,
                            long long *scan_buf, cudaStream_t s);
-// gate (optional): a device flag; the BFS does nothing when it is nonzero
-cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s, const int *gate = nullptr);
+// gate (optional): a device flag; the BFS does nothing when it is nonzero.
+// max_arcs: arcs of the graph with the most arcs (sizes the shared-memory
+// copy of the predecessor lists).
+cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s, const int *gate, long long max_arcs);
 // One graph of at most PREP_SMALL_N vertices: optional CSR validation (sets
 // ERR_INVAL in *err, which must be zero on entry, and skips the rest), the
 // predecessor CSR, tbl_base, the BFS tables and the tour tables in three

@@ -127,31 +127,23 @@ cudaError_t build_pred_csr(const GraphDev &g, int *prp, int *pcol, int *indeg_tm
 
 // One block per source vertex a: pull-style BFS inside a's graph.  A vertex
 // x first reached at distance d+1 takes as predecessor the lowest-id u with
-// an arc u -> x and dist(u) = d.
+// an arc u -> x and dist(u) = d.  The graph's predecessor lists are copied to
+// shared memory (local ids) when they fit in arc_cap arcs: every level then
+// reads shared memory only.
 constexpr int BFS_BLOCK = 128;
+constexpr int BFS_SMEM_BUDGET = 64 * 1024;
 
-__global__ void __launch_bounds__(BFS_BLOCK) bfs_kernel(GraphDev g, const int *gate) {
-    extern __shared__ int dist_s[];
-    if (gate && *gate) return;  // the CSR failed validation
-    const int a = blockIdx.x;
-    const int gid = g.vgraph ? g.vgraph[a] : 0;
-    const int vb = g.vgraph ? g.vbase[gid] : 0;
-    const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
-    const int al = a - vb;
-    int *drow = g.dist + g.tbl_base[gid] + (long long)al * ng;
-    int *prow = g.pred + g.tbl_base[gid] + (long long)al * ng;
-    for (int x = threadIdx.x; x < ng; x += BFS_BLOCK) {
-        dist_s[x] = (x == al) ? 0 : -1;
-        prow[x] = -1;
-    }
-    __syncthreads();
+template <bool STAGED>
+__device__ __forceinline__ void bfs_levels(const GraphDev &g, int vb, int ng, const int *prp_s, const int *pcol_s,
+                                           int *dist_s, int *prow) {
     for (int d = 0;; ++d) {
         int changed = 0;
         for (int x = threadIdx.x; x < ng; x += BFS_BLOCK) {
             if (dist_s[x] != -1) continue;
             int best = 0x7fffffff;
-            for (int e = g.prp[vb + x]; e < g.prp[vb + x + 1]; ++e) {
-                const int u = g.pcol[e] - vb;
+            const int e0 = STAGED ? prp_s[x] : g.prp[vb + x], e1 = STAGED ? prp_s[x + 1] : g.prp[vb + x + 1];
+            for (int e = e0; e < e1; ++e) {
+                const int u = STAGED ? pcol_s[e] : g.pcol[e] - vb;
                 if (dist_s[u] == d && u < best) best = u;
             }
             if (best != 0x7fffffff) {
@@ -162,16 +154,47 @@ __global__ void __launch_bounds__(BFS_BLOCK) bfs_kernel(GraphDev g, const int *g
         }
         if (!__syncthreads_or(changed)) break;
     }
+}
+
+__global__ void __launch_bounds__(BFS_BLOCK) bfs_kernel(GraphDev g, const int *gate, int arc_cap) {
+    extern __shared__ int smem[];
+    if (gate && *gate) return;  // the CSR failed validation
+    int *dist_s = smem;                 // [maxn]
+    int *prp_s = smem + g.maxn;         // [maxn + 1]
+    int *pcol_s = prp_s + g.maxn + 1;   // [arc_cap]
+    const int a = blockIdx.x;
+    const int gid = g.vgraph ? g.vgraph[a] : 0;
+    const int vb = g.vgraph ? g.vbase[gid] : 0;
+    const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
+    const int al = a - vb;
+    int *drow = g.dist + g.tbl_base[gid] + (long long)al * ng;
+    int *prow = g.pred + g.tbl_base[gid] + (long long)al * ng;
+    const int a0 = g.prp[vb], mg = g.prp[vb + ng] - a0;
+    const bool staged = mg <= arc_cap;
+    for (int x = threadIdx.x; x < ng; x += BFS_BLOCK) {
+        dist_s[x] = (x == al) ? 0 : -1;
+        prow[x] = -1;
+    }
+    if (staged) {
+        for (int x = threadIdx.x; x <= ng; x += BFS_BLOCK) prp_s[x] = g.prp[vb + x] - a0;
+        for (int e = threadIdx.x; e < mg; e += BFS_BLOCK) pcol_s[e] = g.pcol[a0 + e] - vb;
+    }
+    __syncthreads();
+    if (staged) bfs_levels<true>(g, vb, ng, prp_s, pcol_s, dist_s, prow);
+    else bfs_levels<false>(g, vb, ng, prp_s, pcol_s, dist_s, prow);
     for (int x = threadIdx.x; x < ng; x += BFS_BLOCK) drow[x] = dist_s[x];
 }
 
-cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s, const int *gate) {
-    const size_t smem = sizeof(int) * (size_t)g.maxn;
+cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s, const int *gate, long long max_arcs) {
+    const size_t base = sizeof(int) * (2 * (size_t)g.maxn + 1);
+    const size_t want = base + sizeof(int) * (size_t)max_arcs;
+    const int arc_cap = want <= (size_t)BFS_SMEM_BUDGET ? (int)max_arcs : 0;
+    const size_t smem = base + sizeof(int) * (size_t)arc_cap;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    bfs_kernel<<<g.N, BFS_BLOCK, smem, s>>>(g, gate);
+    bfs_kernel<<<g.N, BFS_BLOCK, smem, s>>>(g, gate, arc_cap);
     note_launch();
     return cudaGetLastError();
 }
@@ -194,12 +217,12 @@ __global__ void tour_len_kernel(GraphDev g) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x) tour_len_one(g, v);
 }
 
-__device__ __forceinline__ void tour_fill_one(const GraphDev &g, int v) {
+// P: v's graph's predecessor table (global, or a shared-memory copy)
+__device__ __forceinline__ void tour_fill_one(const GraphDev &g, int v, const int *P) {
     const int gid = g.vgraph ? g.vgraph[v] : 0;
     const int vb = g.vgraph ? g.vbase[gid] : 0;
     const int ng = g.vgraph ? g.vbase[gid + 1] - vb : g.N;
     const int en = g.entry[gid] - vb, ex = g.exit[gid] - vb, vl = v - vb;
-    const int *P = g.pred + g.tbl_base[gid];
     // path(entry -> v), backwards from v through P[entry][.]
     int len = g.pre_len[v];
     int *dst = g.pre_seq + g.pre_off[v];
@@ -219,7 +242,8 @@ __device__ __forceinline__ void tour_fill_one(const GraphDev &g, int v) {
 }
 
 __global__ void tour_fill_kernel(GraphDev g) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x) tour_fill_one(g, v);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.N; v += gridDim.x * blockDim.x)
+        tour_fill_one(g, v, g.pred + g.tbl_base[g.vgraph ? g.vgraph[v] : 0]);
 }
 
 cudaError_t tour_lengths(const GraphDev &g, long long *scan_tmp, cudaStream_t s) {
@@ -243,6 +267,7 @@ cudaError_t tour_fill(const GraphDev &g, cudaStream_t s) {
 // but the final error check
 // ---------------------------------------------------------------------------
 constexpr int PREP_BLOCK = 1024;
+constexpr size_t TOUR_STAGE_BYTES = 96 * 1024;  // predecessor tables up to 156 x 156 go to shared memory
 
 // Optional CSR validation (an invalid CSR sets ERR_INVAL in *err and nothing
 // else runs), then the predecessor CSR with ascending lists and the table
@@ -305,10 +330,17 @@ __global__ void __launch_bounds__(PREP_BLOCK) prep_small_kernel(GraphDev g, int 
 // Tour lengths, their offsets and the tour sequences of one graph in one
 // block; pre_seq and suf_seq hold N(N+1)/2 entries each, an upper bound (the
 // i-th vertex in order of distance from the entry is at most i arcs away, so
-// its path has at most i + 1 vertices; the same toward the exit).
-__global__ void __launch_bounds__(PREP_BLOCK) tour_small_kernel(GraphDev g, const int *gate) {
+// its path has at most i + 1 vertices; the same toward the exit).  With
+// stage_pred the N x N predecessor table is first copied to dynamic shared
+// memory, so the path walks read shared memory.
+__global__ void __launch_bounds__(PREP_BLOCK) tour_small_kernel(GraphDev g, const int *gate, int stage_pred) {
+    extern __shared__ int pred_s[];
     if (*gate) return;
     const int N = g.N, tid = threadIdx.x;
+    if (stage_pred) {
+        const long long nn = (long long)N * N;
+        for (long long i = tid; i < nn; i += PREP_BLOCK) pred_s[i] = g.pred[i];
+    }
     for (int v = tid; v < N; v += PREP_BLOCK) tour_len_one(g, v);
     __syncthreads();
     long long cp = 0, cs = 0;
@@ -326,7 +358,7 @@ __global__ void __launch_bounds__(PREP_BLOCK) tour_small_kernel(GraphDev g, cons
         cs += tb;
     }
     __syncthreads();
-    for (int v = tid; v < N; v += PREP_BLOCK) tour_fill_one(g, v);
+    for (int v = tid; v < N; v += PREP_BLOCK) tour_fill_one(g, v, stage_pred ? pred_s : g.pred);
 }
 
 cudaError_t preprocess_small(const GraphDev &g, int *prp, int *pcol, long long *tbl_base, bool validate, int entry,
@@ -337,8 +369,15 @@ cudaError_t preprocess_small(const GraphDev &g, int *prp, int *pcol, long long *
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if ((e = bfs_all_pairs(g, s, err)) != cudaSuccess) return e;
-    tour_small_kernel<<<1, PREP_BLOCK, 0, s>>>(g, err);
+    if ((e = bfs_all_pairs(g, s, err, g.M)) != cudaSuccess) return e;
+    const size_t pred_bytes = sizeof(int) * (size_t)g.N * g.N;
+    const int stage = pred_bytes <= TOUR_STAGE_BYTES;
+    if (stage && pred_bytes > 48 * 1024) {
+        if ((e = cudaFuncSetAttribute(tour_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)TOUR_STAGE_BYTES)) != cudaSuccess)
+            return e;
+    }
+    tour_small_kernel<<<1, PREP_BLOCK, stage ? pred_bytes : 0, s>>>(g, err, stage);
     note_launch();
     return cudaGetLastError();
 }

@@ -197,6 +197,31 @@ def test_device_load_rejects_bad_csr_on_both_preprocessing_paths(n, bad):
     assert e.value.code == tpg.TPG_EINVAL
 
 
+def _looped_chain(n):
+    """0 -> 1 -> ... -> n-1 with a back arc i -> i-5 at every tenth vertex:
+    loops give PPs off the entry-exit line, so TPs get prefixes and suffixes."""
+    arcs = [(i, i + 1) for i in range(n - 1)] + [(i, i - 5) for i in range(10, n - 1, 10)]
+    rp, col = G.csr_from_arcs(n, arcs)
+    return G.CFG(n=n, row_ptr=rp, col=col, entry=0, exit=n - 1, name=f"looped_chain_{n}")
+
+
+# 600 vertices take the single-block preprocessing, 1100 the general one
+@pytest.mark.parametrize("n", [600, 1100])
+def test_tours_on_both_preprocessing_paths(n):
+    import torch
+
+    cfg = _looped_chain(n)
+    ref, _ = check_cfg(cfg)  # host load
+    assert len(ref.tp_offsets) > 2 and len(ref.tp_vertices) > n
+    rp = torch.as_tensor(cfg.row_ptr, device="cuda")
+    col = torch.as_tensor(cfg.col, device="cuda")
+    with tpg.tpg_load_cfg_device(cfg.n, cfg.m, rp, col, cfg.entry, cfg.exit) as h:
+        tp = tpg.tpg_test_paths(h)
+        _, toff, tvert = tp.host_arrays()
+        tp.free()
+    assert_paths_equal(toff, tvert, ref.tp_offsets, ref.tp_vertices, f"{cfg.name} device-load TP")
+
+
 @pytest.mark.parametrize("n", [6, 1000, 1025, 1500])
 def test_device_load_chain_on_both_preprocessing_paths(n):
     import torch
