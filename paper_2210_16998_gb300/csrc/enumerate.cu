@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
     constexpr int F = CPG / NW;      // chunks per warp in the counting pass
     constexpr int WT = 32 * ITEMS;  // paths per warp tile
     static_assert(CPG % NW == 0, "a block's warps split its chunks evenly");
+    static_assert(CPG % 32 == 0 && CPG <= BLOCK, "lanes split a group's entries; threads clear them");
     extern __shared__ long long s_gpre[];  // [2 * G]: exclusive group prefixes (children, PPs)
     __shared__ long long s_wsum[NW][2];
     __shared__ long long s_tot[2];
@@ -344,14 +345,21 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
         unsigned bound = 0;  // first position of the chunk after cur_own
         unsigned acc_c = 0, acc_p = 0, ret_c = 0, ret_p = 0;
 
-        // chunk entries of the group of chunk c that precede it, and its own
-        // (lanes 0..r of the group, r = c's place in it)
-        auto load_entries = [&](int c, long long &ec, long long &ep) {
-            const int grp = c / CPG, r = c - grp * CPG;
-            ec = ep = 0;
-            if (c < nchk && lane <= r) {
-                ec = __ldcg(A.cc(s0) + grp * CPG + lane);
-                ep = __ldcg(A.cp(s0) + grp * CPG + lane);
+        // the entries of chunk c's group that precede c (r = c's place in
+        // the group), summed per lane: lane l takes those at l, l + 32, ...
+        auto load_entries = [&](int c, long long &sc, long long &sp) {
+            sc = sp = 0;
+            if (c < nchk) {
+                const int grp = c / CPG, r = c - grp * CPG;
+                const long long *ecc = A.cc(s0) + (long long)grp * CPG, *ecp = A.cp(s0) + (long long)grp * CPG;
+#pragma unroll
+                for (int t = 0; t < CPG / 32; ++t) {
+                    const int q = t * 32 + lane;
+                    if (q < r) {
+                        sc += __ldcg(ecc + q);
+                        sp += __ldcg(ecp + q);
+                    }
+                }
             }
         };
         const int GW = G * NW, gw = b * NW + wid;
@@ -361,10 +369,11 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
             // the next chunk's entries load while this chunk is processed
             long long ec_next, ep_next;
             load_entries(c + GW, ec_next, ep_next);
-            // offsets of chunk c: its group's prefix plus the chunks before it in the group
-            const int grp = c / CPG, r = c - grp * CPG;
-            const long long own_c = __shfl_sync(0xffffffffu, ec, r), own_p = __shfl_sync(0xffffffffu, ep, r);
-            long long xc = lane < r ? ec : 0, xp = lane < r ? ep : 0;
+            // offsets of chunk c: its group's prefix plus the chunks before it
+            // in the group; its own entry is checked when the chunk is done
+            const int grp = c / CPG;
+            const long long own_c = __ldcg(A.cc(s0) + c), own_p = __ldcg(A.cp(s0) + c);
+            long long xc = ec, xp = ep;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 xc += __shfl_xor_sync(0xffffffffu, xc, o);
