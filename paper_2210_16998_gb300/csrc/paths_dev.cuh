@@ -53,7 +53,8 @@ __device__ __forceinline__ int key_cmp(long long a, long long b, const long long
 // graph id of each PP, out_ends (optional) its (first, last) local vertex.
 static_assert(TPG_MAX_N <= 65536, "local vertex ids fit 16 bits");
 constexpr int MAT_BUF = 1536;  // local vertex ids (uint16, < TPG_MAX_N) per warp: 32 PPs of up to 48 vertices
-constexpr int MAT_MAX_LV = 512; // level-pointer table cached in shared memory up to this many levels
+constexpr int MAT_MAX_LV = 256; // level-pointer table cached in shared memory up to this many levels
+                                // (2 KB: with a 24 KB window per 8 warps, 8 blocks fit an SM)
 
 // Copy the levels' node pointers to shared memory (one dependent load per
 // parent-link step instead of two); returns nullptr when there are too many.
