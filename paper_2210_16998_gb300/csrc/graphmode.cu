@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(GMB) gm_tp_write(GmArgs a) {
     }
 }
 
-// one round of pairwise run merging inside every graph
+// one round of pairwise run merging inside every graph (both runs of a merge
+// belong to one graph, so the comparisons read no graph ids)
 __global__ void __launch_bounds__(GMB) gm_tp_merge_round(GmArgs a, int r, int buf) {
     const long long P = gm_P_tp(a);
     const long long *pin = a.perm[buf];
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(GMB) gm_tp_merge_round(GmArgs a, int r, int bu
                 long long lo = diag > nb ? diag - nb : 0, hi = diag < na ? diag : na;
                 while (lo < hi) {
                     const long long mid = (lo + hi) >> 1;
-                    if (key_cmp(pin[a_lo + mid], pin[a_hi + diag - mid - 1], a.key_off, a.key, a.tp_graph0) <= 0)
+                    if (key_cmp_same_graph(pin[a_lo + mid], pin[a_hi + diag - mid - 1], a.key_off, a.key) <= 0)
                         lo = mid + 1;
                     else
                         hi = mid;
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(GMB) gm_tp_merge_round(GmArgs a, int r, int bu
             bool take_a;
             if (i >= a_hi) take_a = false;
             else if (j >= b_hi) take_a = true;
-            else take_a = key_cmp(pin[i], pin[j], a.key_off, a.key, a.tp_graph0) <= 0;
+            else take_a = key_cmp_same_graph(pin[i], pin[j], a.key_off, a.key) <= 0;
             pout[d] = take_a ? pin[i++] : pin[j++];
         }
     }

@@ -25,11 +25,11 @@ __device__ __forceinline__ int tp_cmp(long long a, long long b, const long long 
 // in `bits` (8 or 16) bits, most significant first, vpw = 64 / bits vertices
 // per 64-bit word, the last word zero-padded.  Comparing word by word (a
 // missing word reads as 0) orders the sequences lexicographically with a
-// proper prefix first, and equal keys mean equal sequences.
-__device__ __forceinline__ int key_cmp(long long a, long long b, const long long *koff,
-                                       const unsigned long long *key, const int *graph) {
-    const int ga = graph[a], gb = graph[b];
-    if (ga != gb) return ga < gb ? -1 : 1;
+// proper prefix first, and equal keys mean equal sequences.  This form
+// compares two sequences of the same graph (no graph ids read); key_cmp
+// orders by graph id first.
+__device__ __forceinline__ int key_cmp_same_graph(long long a, long long b, const long long *koff,
+                                                  const unsigned long long *key) {
     const long long a0 = koff[a], wa = koff[a + 1] - a0;
     const long long b0 = koff[b], wb = koff[b + 1] - b0;
     const long long w = wa > wb ? wa : wb;
@@ -39,6 +39,13 @@ __device__ __forceinline__ int key_cmp(long long a, long long b, const long long
         if (x != y) return x < y ? -1 : 1;
     }
     return 0;
+}
+
+__device__ __forceinline__ int key_cmp(long long a, long long b, const long long *koff,
+                                       const unsigned long long *key, const int *graph) {
+    const int ga = graph[a], gb = graph[b];
+    if (ga != gb) return ga < gb ? -1 : 1;
+    return key_cmp_same_graph(a, b, koff, key);
 }
 
 // Materialise PPs [0, n): one warp handles 32 consecutive PPs; each lane
