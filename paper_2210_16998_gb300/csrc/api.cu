@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "testpaths.h"
 
 using namespace tpg;
 
@@ -374,6 +375,7 @@ struct tpg_cfg {
     DevBuf s_keys[2], s_refs[2], s_len, s_tmp, s_i32[3], s_i64[4];
     DevBuf rank_cnt, rank_pre[2], rank_noff, rank_bsum;  // PP ranking scratch
     DevBuf pp_ends;  // (first, last) local vertex of each cached PP, for the TP lengths
+    DevBuf tp_key_off, tp_key;  // packed comparison keys of the TPs being sorted
 
     // cached PP list on the device (shared with device results)
     Block *pp_off = nullptr, *pp_vert = nullptr, *pp_graph = nullptr, *pp_gptr = nullptr;
@@ -488,7 +490,7 @@ void destroy_cfg(tpg_cfg *g) {
                      &g->levels, &g->agg, &g->ctl, &g->s_keys[0], &g->s_keys[1],
                      &g->s_refs[0], &g->s_refs[1], &g->s_len, &g->s_tmp, &g->s_i32[0], &g->s_i32[1],
                      &g->s_i32[2], &g->s_i64[0], &g->s_i64[1], &g->s_i64[2], &g->s_i64[3], &g->rank_cnt,
-                     &g->rank_pre[0], &g->rank_pre[1], &g->rank_noff, &g->rank_bsum, &g->pp_ends};
+                     &g->rank_pre[0], &g->rank_pre[1], &g->rank_noff, &g->rank_bsum, &g->pp_ends, &g->tp_key_off, &g->tp_key};
     for (DevBuf *b : all) release(g, *b);
     for (auto &b : g->node_segs) release(g, b);
     for (auto &b : g->pp_segs) release(g, b);
@@ -1109,26 +1111,44 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
             FTV = TV;
             break;
         }
-        // pairwise merge rounds over the runs
+        // merge rounds over the runs inside every graph (a graph has at most
+        // one run per vertex: one per first vertex of its PPs), comparing
+        // packed keys (8 or 16 bits per vertex; at most TV / vpw + P words)
+        const int kbits = g->maxn <= 255 ? 8 : 16;
+        const long long K_ub = TV / (64 / kbits) + P + 1;
         if ((rc = ensure(g, g->s_i64[2], sizeof(long long) * (R + 2))) ||
-            (rc = ensure(g, g->s_i64[3], sizeof(long long) * (R + 2))) ||
+            (rc = ensure(g, g->s_i64[3], sizeof(long long) * (2 * (long long)g->G + 2))) ||
             (rc = ensure(g, g->s_refs[0], sizeof(long long) * (P + 1))) ||
-            (rc = ensure(g, g->s_refs[1], sizeof(long long) * (P + 1))))
+            (rc = ensure(g, g->s_refs[1], sizeof(long long) * (P + 1))) ||
+            (rc = ensure(g, g->s_len, sizeof(long long) * (P + 1))) ||
+            (rc = ensure(g, g->tp_key_off, sizeof(long long) * (P + 1))) ||
+            (rc = ensure(g, g->tp_key, sizeof(unsigned long long) * K_ub)))
             break;
-        long long *bounds[2] = {g->s_i64[2].as<long long>(), g->s_i64[3].as<long long>()};
+        long long *key_off = g->tp_key_off.as<long long>();
+        unsigned long long *key = g->tp_key.as<unsigned long long>();
+        if (cuda_err(tp_key_lengths((const long long *)tp_off->p, P, kbits, g->s_len.as<long long>(), s)) ||
+            cuda_err(scan_i64(g->s_len.as<long long>(), key_off, P, g->s_tmp.as<long long>(), s)) ||
+            cuda_err(tp_write_keys((const long long *)tp_off->p, (const int *)tp_vert->p, P, kbits, key_off, key,
+                                   s))) {
+            rc = TPG_ECUDA;
+            break;
+        }
+        long long *bounds = g->s_i64[2].as<long long>();
+        long long *run_base = g->s_i64[3].as<long long>(), *nruns = run_base + g->G;
         long long *perm[2] = {g->s_refs[0].as<long long>(), g->s_refs[1].as<long long>()};
-        if (cuda_err(tp_run_bounds(run_start, run_rank, P, R, bounds[0], s))) { rc = TPG_ECUDA; break; }
-        if (cuda_err(tp_iota(perm[0], P, s))) { rc = TPG_ECUDA; break; }
-        int cb = 0, cp = 0;
-        long long Rc = R;
-        while (Rc > 1 && rc == TPG_OK) {
-            if (cuda_err(tp_merge_round(perm[cp], perm[cp ^ 1], bounds[cb], Rc, P, (const long long *)tp_off->p,
-                                        (const int *)tp_vert->p, tp_graph, s)) ||
-                cuda_err(tp_halve_bounds(bounds[cb], Rc, bounds[cb ^ 1], s)))
+        const long long *tp_gptr = (const long long *)g->pp_gptr->p;  // TP i comes from PP i
+        if (cuda_err(tp_run_bounds(run_start, run_rank, P, R, bounds, s)) ||
+            cuda_err(tp_run_bases(tp_gptr, run_rank, g->G, run_base, nruns, s)) || cuda_err(tp_iota(perm[0], P, s))) {
+            rc = TPG_ECUDA;
+            break;
+        }
+        int cp = 0;
+        const int rounds = tp_merge_rounds(g->maxn);
+        for (int r = 0; r < rounds && rc == TPG_OK; ++r) {
+            if (cuda_err(tp_merge_graph_round_keys(perm[cp], perm[cp ^ 1], bounds, run_base, nruns, tp_gptr, g->G, r,
+                                                   P, key_off, key, s)))
                 rc = TPG_ECUDA;
             cp ^= 1;
-            cb ^= 1;
-            Rc = (Rc + 1) / 2;
         }
         if (rc) break;
         // dedup + compaction
@@ -1136,8 +1156,8 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
         long long *keep_len = g->s_i64[0].as<long long>(); // reuse tp_len
         long long *keep_off = g->s_i64[1].as<long long>(); // reuse run_rank
         long long *keep_rank = perm[cp ^ 1];
-        if (cuda_err(tp_dedup_flags(perm[cp], P, (const long long *)tp_off->p, (const int *)tp_vert->p, tp_graph,
-                                    keep_len, keep, s)) ||
+        if (cuda_err(tp_dedup_flags_keys(perm[cp], P, (const long long *)tp_off->p, key_off, key, tp_graph, keep_len,
+                                         keep, s)) ||
             cuda_err(scan_i64(keep_len, keep_off, P, g->s_tmp.as<long long>(), s)) ||
             cuda_err(scan_i32_to_i64(keep, keep_rank, P, g->s_tmp.as<long long>(), s))) {
             rc = TPG_ECUDA;

@@ -258,13 +258,7 @@ cudaError_t tp_write(const long long *pp_off, const int *pp_vert, const int *pp_
                      const GraphDev &g, const long long *tp_off, int *tp_vert, cudaStream_t s);
 cudaError_t tp_run_bounds(const int *run_start, const long long *run_rank, long long P, long long R,
                           long long *bounds, cudaStream_t s);
-cudaError_t tp_merge_round(const long long *perm_in, long long *perm_out, const long long *bounds,
-                           long long R, long long P, const long long *tp_off, const int *tp_vert,
-                           const int *tp_graph, cudaStream_t s);
-cudaError_t tp_halve_bounds(const long long *bounds, long long R, long long *out, cudaStream_t s);
 cudaError_t tp_iota(long long *perm, long long P, cudaStream_t s);
-cudaError_t tp_dedup_flags(const long long *perm, long long P, const long long *tp_off, const int *tp_vert,
-                           const int *tp_graph, long long *keep_len, int *keep, cudaStream_t s);
 cudaError_t tp_gather(const long long *perm, const int *keep, const long long *keep_rank, long long P,
                       const long long *tp_off, const int *tp_vert, const int *tp_graph,
                       const long long *keep_off, long long *final_off, int *out_vert, int *out_graph,

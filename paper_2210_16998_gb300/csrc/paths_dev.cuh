@@ -4,23 +4,6 @@
 
 namespace tpg {
 
-// (graph, sequence) order: graph id first, then lexicographic on the vertex
-// sequences, a proper prefix first.
-__device__ __forceinline__ int tp_cmp(long long a, long long b, const long long *off, const int *vert,
-                                      const int *graph) {
-    const int ga = graph[a], gb = graph[b];
-    if (ga != gb) return ga < gb ? -1 : 1;
-    const long long a0 = off[a], la = off[a + 1] - a0;
-    const long long b0 = off[b], lb = off[b + 1] - b0;
-    const long long l = la < lb ? la : lb;
-    for (long long t = 0; t < l; ++t) {
-        const int x = vert[a0 + t], y = vert[b0 + t];
-        if (x != y) return x < y ? -1 : 1;
-    }
-    if (la == lb) return 0;
-    return la < lb ? -1 : 1;
-}
-
 // Packed comparison keys of vertex sequences: vertex v is stored as v + 1
 // in `bits` (8 or 16) bits, most significant first, vpw = 64 / bits vertices
 // per 64-bit word, the last word zero-padded.  Comparing word by word (a

@@ -6,13 +6,15 @@
 // path(a -> b) read from the lowest-id BFS predecessor table.  Because the
 // PPs arrive in canonical order, TPs of PPs that share a first vertex share
 // their prefix and are already in order among themselves; so the TP list is
-// a sequence of sorted runs (one per (graph, first vertex)).  Runs are merged
-// pairwise with a merge-path kernel comparing whole sequences, and exact
+// a sequence of sorted runs (one per (graph, first vertex)).  The runs of
+// each graph are merged pairwise (merge path) in ceil(log2(runs)) rounds,
+// comparing packed keys (8 or 16 bits per vertex, 64-bit words), and exact
 // duplicates (two PPs of different first vertices can yield the same TP)
 // are dropped after the final round.
 #include "common.cuh"
 #include "kernels.h"
 #include "paths_dev.cuh"
+#include "testpaths.h"
 
 namespace tpg {
 
@@ -164,90 +166,160 @@ cudaError_t tp_iota(long long *perm, long long P, cudaStream_t s) {
 
 constexpr int TPM_ITEMS = 4;
 
-// One round of pairwise run merging: pair p = runs (2p, 2p+1).  Thread t
-// writes outputs [t*ITEMS, t*ITEMS + ITEMS), locating its pair and merge-path
-// split by binary search (A first on ties, so equal TPs stay adjacent).
-__global__ void tp_merge_kernel(const long long *perm_in, long long *perm_out, const long long *bounds,
-                                long long R, long long P, const long long *off, const int *vert,
-                                const int *graph) {
+// largest s in [lo, hi] with a[s] <= x (a nondecreasing, a[lo] <= x)
+__device__ __forceinline__ long long tp_slot(const long long *a, long long lo, long long hi, long long x) {
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (a[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void run_bases_kernel(const long long *gptr, const long long *run_rank, int G, long long *run_base,
+                                 long long *nruns) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        run_base[g] = run_rank[gptr[g]];
+        nruns[g] = run_rank[gptr[g + 1]] - run_base[g];
+    }
+}
+
+cudaError_t tp_run_bases(const long long *gptr, const long long *run_rank, int G, long long *run_base,
+                         long long *nruns, cudaStream_t s) {
+    run_bases_kernel<<<grid_for(G), 256, 0, s>>>(gptr, run_rank, G, run_base, nruns);
+    note_launch();
+    return cudaGetLastError();
+}
+
+int tp_merge_rounds(long long max_runs) {
+    int r = 0;
+    while ((1ll << r) < max_runs) ++r;
+    return r;
+}
+
+// Thread t writes outputs [t*ITEMS, t*ITEMS + ITEMS) of round r: it finds
+// the graph and run of each output, the two run groups merged there, and the
+// merge-path split by binary search (A first on ties, so equal TPs stay
+// adjacent).  Graphs without TPs own no outputs.  cmp(a, b) orders two TPs
+// of one graph (here: their packed keys).
+template <typename Cmp>
+__global__ void tp_merge_graph_kernel(const long long *perm_in, long long *perm_out, const long long *bounds,
+                                      const long long *run_base, const long long *nruns, const long long *gptr,
+                                      int G, int r, long long P, Cmp cmp) {
     const long long d0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * TPM_ITEMS;
     if (d0 >= P) return;
-    const long long npairs = (R + 1) / 2;
-    long long pair = -1, a_lo = 0, a_hi = 0, b_hi = 0, i = 0, j = 0;
+    long long a_hi = 0, b_hi = -1, i = 0, j = 0;
     for (int t = 0; t < TPM_ITEMS; ++t) {
         const long long d = d0 + t;
         if (d >= P) break;
-        if (pair < 0 || d >= b_hi) {
-            // locate the pair containing output position d
-            long long lo = 0, hi = npairs - 1;
-            while (lo < hi) {
-                const long long mid = (lo + hi + 1) >> 1;
-                if (bounds[2 * mid] <= d) lo = mid;
-                else hi = mid - 1;
-            }
-            pair = lo;
-            a_lo = bounds[2 * pair];
-            a_hi = (2 * pair + 1 <= R) ? bounds[2 * pair + 1] : P;
-            b_hi = (2 * pair + 2 <= R) ? bounds[2 * pair + 2] : a_hi;
+        if (d >= b_hi) {
+            const int gg = G > 1 ? (int)tp_slot(gptr, 0, G, d) : 0;
+            const long long rb = run_base[gg], nr = nruns[gg];
+            const long long q0 = tp_slot(bounds, rb, rb + nr - 1, d) - rb;
+            const long long m = q0 >> (r + 1);
+            const long long qa = m << (r + 1), qb = qa + (1ll << r), qe = (m + 1) << (r + 1);
+            const long long a_lo = bounds[rb + qa];
+            a_hi = bounds[rb + (qb < nr ? qb : nr)];
+            b_hi = bounds[rb + (qe < nr ? qe : nr)];
             const long long na = a_hi - a_lo, nb = b_hi - a_hi, diag = d - a_lo;
-            long long lo2 = diag > nb ? diag - nb : 0, hi2 = diag < na ? diag : na;
-            while (lo2 < hi2) {
-                const long long mid = (lo2 + hi2) >> 1;
-                if (tp_cmp(perm_in[a_lo + mid], perm_in[a_hi + diag - mid - 1], off, vert, graph) <= 0)
-                    lo2 = mid + 1;
-                else
-                    hi2 = mid;
+            long long lo = diag > nb ? diag - nb : 0, hi = diag < na ? diag : na;
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (cmp(perm_in[a_lo + mid], perm_in[a_hi + diag - mid - 1]) <= 0) lo = mid + 1;
+                else hi = mid;
             }
-            i = a_lo + lo2;
-            j = a_hi + (diag - lo2);
+            i = a_lo + lo;
+            j = a_hi + (diag - lo);
         }
         bool take_a;
         if (i >= a_hi) take_a = false;
         else if (j >= b_hi) take_a = true;
-        else take_a = tp_cmp(perm_in[i], perm_in[j], off, vert, graph) <= 0;
+        else take_a = cmp(perm_in[i], perm_in[j]) <= 0;
         perm_out[d] = take_a ? perm_in[i++] : perm_in[j++];
     }
 }
 
-cudaError_t tp_merge_round(const long long *perm_in, long long *perm_out, const long long *bounds, long long R,
-                           long long P, const long long *tp_off, const int *tp_vert, const int *tp_graph,
-                           cudaStream_t s) {
+struct KeyCmp {  // packed keys of one graph
+    const long long *koff;
+    const unsigned long long *key;
+    __device__ __forceinline__ int operator()(long long a, long long b) const {
+        return key_cmp_same_graph(a, b, koff, key);
+    }
+};
+
+cudaError_t tp_merge_graph_round_keys(const long long *perm_in, long long *perm_out, const long long *bounds,
+                                      const long long *run_base, const long long *nruns, const long long *gptr,
+                                      int G, int r, long long P, const long long *key_off,
+                                      const unsigned long long *key, cudaStream_t s) {
     if (P <= 0) return cudaSuccess;
     const long long threads = (P + TPM_ITEMS - 1) / TPM_ITEMS;
-    tp_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(perm_in, perm_out, bounds, R, P, tp_off,
-                                                                     tp_vert, tp_graph);
+    tp_merge_graph_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(perm_in, perm_out, bounds, run_base,
+                                                                           nruns, gptr, G, r, P,
+                                                                           KeyCmp{key_off, key});
     note_launch();
     return cudaGetLastError();
 }
 
-__global__ void halve_bounds_kernel(const long long *bounds, long long R, long long *out) {
-    const long long R2 = (R + 1) / 2;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r <= R2;
-         r += (long long)gridDim.x * blockDim.x)
-        out[r] = (r < R2) ? bounds[2 * r] : bounds[R];
-}
-
-cudaError_t tp_halve_bounds(const long long *bounds, long long R, long long *out, cudaStream_t s) {
-    halve_bounds_kernel<<<grid_for((R + 1) / 2 + 1), 256, 0, s>>>(bounds, R, out);
-    note_launch();
-    return cudaGetLastError();
-}
-
-__global__ void dedup_kernel(const long long *perm, long long P, const long long *off, const int *vert,
-                             const int *graph, long long *keep_len, int *keep) {
+__global__ void key_len_kernel(const long long *tp_off, long long P, int vpw, long long *key_len) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long a = perm[i];
-        const int k = (i == 0) || tp_cmp(perm[i - 1], a, off, vert, graph) != 0;
-        keep[i] = k;
-        keep_len[i] = k ? off[a + 1] - off[a] : 0;
+         i += (long long)gridDim.x * blockDim.x)
+        key_len[i] = (tp_off[i + 1] - tp_off[i] + vpw - 1) / vpw;
+}
+
+cudaError_t tp_key_lengths(const long long *tp_off, long long P, int bits, long long *key_len, cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    key_len_kernel<<<grid_for(P), 256, 0, s>>>(tp_off, P, 64 / bits, key_len);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// 8 lanes per TP, each packing 64 / bits consecutive vertices into a word
+constexpr int KEY_LANES = 8;
+__global__ void keys_kernel(const long long *tp_off, const int *tp_vert, long long P, int bits,
+                            const long long *key_off, unsigned long long *key) {
+    const int sub = threadIdx.x & (KEY_LANES - 1), vpw = 64 / bits;
+    const long long groups = (long long)gridDim.x * (blockDim.x / KEY_LANES);
+    for (long long i = blockIdx.x * (long long)(blockDim.x / KEY_LANES) + threadIdx.x / KEY_LANES; i < P;
+         i += groups) {
+        const long long t0 = tp_off[i], len = tp_off[i + 1] - t0, k0 = key_off[i], nw = key_off[i + 1] - k0;
+        for (long long w = sub; w < nw; w += KEY_LANES) {
+            unsigned long long word = 0;
+            for (int q = 0; q < vpw; ++q) {
+                const long long p = w * vpw + q;
+                const unsigned long long v = p < len ? (unsigned long long)(tp_vert[t0 + p] + 1) : 0ull;
+                word = (word << bits) | v;
+            }
+            key[k0 + w] = word;
+        }
     }
 }
 
-cudaError_t tp_dedup_flags(const long long *perm, long long P, const long long *tp_off, const int *tp_vert,
-                           const int *tp_graph, long long *keep_len, int *keep, cudaStream_t s) {
+cudaError_t tp_write_keys(const long long *tp_off, const int *tp_vert, long long P, int bits, const long long *key_off,
+                          unsigned long long *key, cudaStream_t s) {
     if (P <= 0) return cudaSuccess;
-    dedup_kernel<<<grid_for(P), 256, 0, s>>>(perm, P, tp_off, tp_vert, tp_graph, keep_len, keep);
+    long long blocks = (P + (256 / KEY_LANES) - 1) / (256 / KEY_LANES);
+    if (blocks > (1 << 20)) blocks = 1 << 20;
+    keys_kernel<<<(unsigned)blocks, 256, 0, s>>>(tp_off, tp_vert, P, bits, key_off, key);
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void dedup_keys_kernel(const long long *perm, long long P, const long long *tp_off, const long long *key_off,
+                                  const unsigned long long *key, const int *graph, long long *keep_len, int *keep) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long a = perm[i];
+        const int k = (i == 0) || key_cmp(perm[i - 1], a, key_off, key, graph) != 0;
+        keep[i] = k;
+        keep_len[i] = k ? tp_off[a + 1] - tp_off[a] : 0;
+    }
+}
+
+cudaError_t tp_dedup_flags_keys(const long long *perm, long long P, const long long *tp_off, const long long *key_off,
+                                const unsigned long long *key, const int *tp_graph, long long *keep_len, int *keep,
+                                cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    dedup_keys_kernel<<<grid_for(P), 256, 0, s>>>(perm, P, tp_off, key_off, key, tp_graph, keep_len, keep);
     note_launch();
     return cudaGetLastError();
 }
