@@ -24,7 +24,7 @@ namespace {
 
 constexpr int GMB = 256;      // threads per block of the streaming kernels
 constexpr int GM_ITEMS = 4;   // outputs per thread of the PP merge
-constexpr int TPM_ITEMS = 16; // outputs per thread of the TP run merge
+constexpr int TPM_ITEMS = 4;  // outputs per thread of the TP run merge
 constexpr int GM_SCAN_ITEMS = 8;
 constexpr long long GM_SCAN_TILE = (long long)GMB * GM_SCAN_ITEMS;
 
