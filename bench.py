@@ -175,12 +175,12 @@ def closed_form_check(pp):
 
 
 def parse_tile(text):
-    """'block,items' -> tuple, or None for the library default."""
+    """'block,items[,split]' -> tuple, or None for the library default."""
     if not text:
         return None
     v = tuple(int(x) for x in text.split(","))
-    if len(v) != 2:
-        raise SystemExit(f"--tile wants block,items, got {text!r}")
+    if len(v) not in (2, 3):
+        raise SystemExit(f"--tile wants block,items[,split], got {text!r}")
     return v
 
 
@@ -201,7 +201,7 @@ def run_ours(args, rank, world, local_rank):
     def step(check=False):
         h = tpg.tpg_load_cfg_device(cfg.n, cfg.m, rp, col, cfg.entry, cfg.exit)
         if shape:
-            tpg.tpg_set_tile_shape(h, *shape)
+            tpg.set_tile(h, shape)
         pp = tpg.tpg_prime_paths(h)
         if check:
             closed_form_check(pp)
@@ -256,7 +256,7 @@ def run_ours(args, rank, world, local_rank):
     def e2e_step():
         h = tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=tpg.TPG_RESULT_HOST)
         if shape:
-            tpg.tpg_set_tile_shape(h, *shape)
+            tpg.set_tile(h, shape)
         pp = tpg.tpg_prime_paths(h)
         tp = tpg.tpg_test_paths(h)
         # bytes read back to the host: a TP list equal to the PP list shares
@@ -301,7 +301,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded diamond-chain CFG)",
         "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                               "tile": [stats[-1]["tile_block"], stats[-1]["tile_items"]]}),
+                               "tile": [stats[-1]["tile_block"], stats[-1]["tile_items"],
+                                        shape[2] if shape and len(shape) > 2 else 1]}),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": int(bo),
                 "steps": e2e_steps},
         "gpu_launches": int(launches),
@@ -366,7 +367,7 @@ def run_batch(args, rank, world, local_rank):
     else:
         shape, tuned = autotune.tune()
     h = tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE)
-    tpg.tpg_set_tile_shape(h, *shape)
+    tpg.set_tile(h, shape)
     # host-driven batched run: exact sizes for the capture, and its own timing
     host_ms = []
     for i in range(3):
@@ -439,7 +440,7 @@ def run_batch(args, rank, world, local_rank):
     t0 = time.perf_counter()
     bo = 0
     he = tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_HOST)
-    tpg.tpg_set_tile_shape(he, *shape)
+    tpg.set_tile(he, shape)
     if not args.no_e2e:
         a = tpg.tpg_prime_paths(he)
         b = tpg.tpg_test_paths(he)
@@ -554,7 +555,7 @@ def run_sizer(args, rank, world, local_rank):
     # (a) plain host-driven enumerator, cold handle
     def plain_host():
         with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE) as h:
-            tpg.tpg_set_tile_shape(h, *shape)
+            tpg.set_tile(h, shape)
             a, b = tpg.tpg_prime_paths(h), tpg.tpg_test_paths(h)
             st = tpg.tpg_get_stats(h)
             P = a.num_paths
@@ -565,7 +566,7 @@ def run_sizer(args, rank, world, local_rank):
     # (b) graph mode sized by an exact run, cold handle
     def plain_graph():
         with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE) as h:
-            tpg.tpg_set_tile_shape(h, *shape)
+            tpg.set_tile(h, shape)
             tpg.tpg_graph_capture(h)
             a, b = tpg.tpg_graph_launch(h)
             P = a.num_paths
@@ -580,7 +581,7 @@ def run_sizer(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t_start = time.perf_counter()
         with tpg.tpg_load_cfg_batch(n_, r_, c_, e_, x_, location=tpg.TPG_RESULT_DEVICE) as h:
-            tpg.tpg_set_tile_shape(h, *shape)
+            tpg.set_tile(h, shape)
             caps = tpg.tpg_sizer_presize(z, h, margin)
             tpg.tpg_graph_capture(h)
             a, b = tpg.tpg_graph_launch(h)

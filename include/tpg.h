@@ -208,6 +208,16 @@ int tpg_release_cached_memory(void);
 int tpg_set_tile_shape(tpg_cfg *g, int32_t block, int32_t items);
 
 /*
+ * Work units per chunk of the frontier kernel for this handle (1..4,
+ * default 1): each chunk of a level is cut into `split` parts that go to
+ * different warps, which balances levels whose chunk costs vary a lot (a
+ * part's offsets are found by summing the count words of the chunk's
+ * earlier parts).  TPG_EINVAL outside 1..4.  Results never depend on it;
+ * the autotuner uses it.
+ */
+int tpg_set_work_split(tpg_cfg *g, int32_t split);
+
+/*
  * Initial capacities of the handle's path arena: total simple paths,
  * simple paths of one level, and prime paths.  The arena grows (and the
  * enumeration restarts from scratch) when one is exceeded, so results never

@@ -371,6 +371,7 @@ struct tpg_cfg {
     DevBuf tfl[2], tvis[2], tcnt[2], levels, agg, ctl;
     long long node_cap = 0, lvl_cap = 0, pp_cap = 0;
     EnumShape shape{0, 0};
+    int split = 1;  // work units per chunk of the frontier kernel
     // generic scratch
     DevBuf s_keys[2], s_refs[2], s_len, s_tmp, s_i32[3], s_i64[4];
     DevBuf rank_cnt, rank_pre[2], rank_noff, rank_bsum;  // PP ranking scratch
@@ -736,6 +737,7 @@ int enumerate_levels(tpg_cfg *g) {
         a.max_levels = g->max_levels;
         a.start_level = start_level;
         a.seed_level1 = (launch == 1) ? 1 : 0;
+        a.split = g->split;
         a.agg = g->agg.as<long long>();
         a.agg_cap = ENUM_AGG_WORDS;
         a.err = g->ctl.as<int>();
@@ -1295,6 +1297,7 @@ int capture_plan(tpg_cfg *g) {
     a.max_levels = g->max_levels;
     a.start_level = 1;
     a.seed_level1 = 1;
+    a.split = g->split;
     a.agg = g->agg.as<long long>();
     a.agg_cap = ENUM_AGG_WORDS;
     a.err = g->ctl.as<int>();
@@ -2076,6 +2079,13 @@ int tpg_set_tile_shape(tpg_cfg *g, int32_t block, int32_t items) {
     const EnumShape sh{block, items};
     if (!enum_shape_supported(g->W, sh)) return TPG_EINVAL;
     g->shape = sh;
+    return TPG_OK;
+}
+
+int tpg_set_work_split(tpg_cfg *g, int32_t split) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (split < 1 || split > 4) return TPG_EINVAL;
+    g->split = split;
     return TPG_OK;
 }
 

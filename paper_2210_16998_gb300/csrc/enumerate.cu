@@ -362,17 +362,29 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                 }
             }
         };
-        const int GW = G * NW, gw = b * NW + wid;
+        // Work units: part s of chunk c (SPLIT parts of sub paths) is unit
+        // c * SPLIT + s.  Warp wid of block b takes units wid * G + b, then
+        // + GW each time: the warps of one block (one SM's share of the issue
+        // slots) sample the whole level, so a costly region is spread over
+        // all SMs, and each warp averages over 2 * SPLIT units.  A part's
+        // offsets are its chunk's plus the children and PPs of the chunk's
+        // earlier parts, summed from their count words.
+        const int SPLIT = a.split < 1 ? 1 : (a.split > 4 ? 4 : a.split);
+        const int GW = G * NW, gw = wid * G + b;
+        const int nunit = nchk * SPLIT;
+        const int sub = ((chunk + SPLIT - 1) / SPLIT + 31) & ~31;
         long long ec, ep;
-        load_entries(gw, ec, ep);
-        for (int c = gw; c < nchk; c += GW) {
-            // the next chunk's entries load while this chunk is processed
+        load_entries(gw / SPLIT, ec, ep);
+        for (int u = gw; u < nunit; u += GW) {
+            const int c = u / SPLIT, part = u - c * SPLIT;
+            // the next unit's chunk entries load while this unit is processed
             long long ec_next, ep_next;
-            load_entries(c + GW, ec_next, ep_next);
+            load_entries((u + GW) / SPLIT, ec_next, ep_next);
             // offsets of chunk c: its group's prefix plus the chunks before it
-            // in the group; its own entry is checked when the chunk is done
+            // in the group; its own entry is checked when its last part is done
             const int grp = c / CPG;
-            const long long own_c = __ldcg(A.cc(s0) + c), own_p = __ldcg(A.cp(s0) + c);
+            const bool last_part = part == SPLIT - 1;
+            const long long own_c = last_part ? __ldcg(A.cc(s0) + c) : 0, own_p = last_part ? __ldcg(A.cp(s0) + c) : 0;
             long long xc = ec, xp = ep;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -380,8 +392,20 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                 xp += __shfl_xor_sync(0xffffffffu, xp, o);
             }
             const int pa = (int)(s_gpre[grp] + xc), pb = (int)(s_gpre[G + grp] + xp);
-            const int lo = (int)min((long long)c * chunk, count), hi = (int)min((long long)lo + chunk, count);
+            const int clo = (int)min((long long)c * chunk, count), chi = (int)min((long long)clo + chunk, count);
+            const int lo = min(clo + part * sub, chi), hi = min(lo + sub, chi);
             int pos_c = pa, pos_p = pb;
+            if (part > 0) {
+                unsigned sc = 0, sp = 0;
+#pragma unroll 4
+                for (int i = clo + lane; i < lo; i += 32) {
+                    const unsigned w = __ldcg(in_cnt + i);
+                    sc += (unsigned)cnt_children(w);
+                    sp += w >> 15;
+                }
+                pos_c += (int)__reduce_add_sync(0xffffffffu, sc);
+                pos_p += (int)__reduce_add_sync(0xffffffffu, sp);
+            }
 
             for (int t0 = lo; t0 < hi; t0 += WT) {
                 int first[ITEMS], last[ITEMS];
@@ -526,7 +550,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                 }
             }
             // the chunk must have produced exactly what its count promised
-            if (lane == 0 && (pos_c - pa != own_c || pos_p - pb != own_p)) atomicOr(a.err, ERR_INVAL);
+            if (last_part && lane == 0 && (pos_c - pa != own_c || pos_p - pb != own_p)) atomicOr(a.err, ERR_INVAL);
             ec = ec_next;
             ep = ep_next;
         }

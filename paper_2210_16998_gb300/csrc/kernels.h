@@ -56,6 +56,7 @@ struct EnumArgs {
     int max_levels;
     int start_level;         // first level processed by this launch
     int seed_level1;         // 1 on a fresh run: level 1 is written first (never on a resume)
+    int split;               // work units per chunk in the per-warp levels (1..4; results never depend on it)
     long long *agg;          // per-block level counts (no initialisation needed)
     long long agg_cap;       // int64 values in agg (enum_agg_words(grid) at least)
     int *err;                // error flags (zeroed)

@@ -202,6 +202,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     a.max_levels = n + 4;
     a.start_level = 1;
     a.seed_level1 = 1;
+    a.split = 1;
     a.agg = (long long *)(S + NA.agg);
     a.agg_cap = ENUM_AGG_WORDS;
     a.err = err;

@@ -131,6 +131,7 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_set_stream.argtypes = [P, P]
         lib.tpg_set_result_location.argtypes = [P, ctypes.c_int32]
         lib.tpg_set_tile_shape.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+        lib.tpg_set_work_split.argtypes = [P, ctypes.c_int32]
         lib.tpg_set_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         lib.tpg_set_output_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         lib.tpg_graph_capture.argtypes = [P]
@@ -170,7 +171,8 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_prime_paths_noalloc.restype = ctypes.c_int
         for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
                      "tpg_test_paths", "tpg_set_stream", "tpg_set_result_location", "tpg_set_allocator",
-                     "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_capacity", "tpg_set_output_capacity",
+                     "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_work_split", "tpg_set_capacity",
+                     "tpg_set_output_capacity",
                      "tpg_graph_capture", "tpg_graph_launch"):
             getattr(lib, name).restype = ctypes.c_int
         lib.tpg_release_cached_memory.argtypes = []
@@ -429,6 +431,16 @@ def tpg_release_cached_memory():
 
 def tpg_set_tile_shape(cfg: Cfg, block: int, items: int):
     _check(load_library().tpg_set_tile_shape(cfg.handle, int(block), int(items)), "tpg_set_tile_shape")
+
+
+def tpg_set_work_split(cfg: Cfg, split: int):
+    _check(load_library().tpg_set_work_split(cfg.handle, int(split)), "tpg_set_work_split")
+
+
+def set_tile(cfg: Cfg, tile):
+    """Apply a tuned tile: (block, items) or (block, items, split)."""
+    tpg_set_tile_shape(cfg, int(tile[0]), int(tile[1]))
+    tpg_set_work_split(cfg, int(tile[2]) if len(tile) > 2 else 1)
 
 
 def tpg_set_capacity(cfg: Cfg, nodes: int, level_nodes: int, prime_paths: int):

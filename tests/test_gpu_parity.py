@@ -283,6 +283,39 @@ def test_every_tile_shape(shape, config3_ref):
     assert (stats["tile_block"], stats["tile_items"]) == shape
 
 
+@pytest.fixture(scope="module")
+def chain20_ref():
+    return oracle.run_cfg(G.diamond_chain(20))
+
+
+@pytest.mark.parametrize("split", [1, 2, 3, 4])
+@pytest.mark.parametrize("which", ["config3", "chain20"])
+def test_every_work_split(split, which, config3_ref, chain20_ref):
+    """Cutting each chunk into `split` work units changes which warp does
+    what, never the result: C3's levels have one-tile chunks (later parts
+    empty), the k=20 chain's largest levels chunks of over a hundred paths."""
+    cfg, ref = (G.config3_cfg(), config3_ref) if which == "config3" else (G.diamond_chain(20), chain20_ref)
+    with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit) as h:
+        tpg.tpg_set_work_split(h, split)
+        pp = tpg.tpg_prime_paths(h)
+        _, off, vert = pp.host_arrays()
+        pp.free()
+        tp = tpg.tpg_test_paths(h)
+        _, toff, tvert = tp.host_arrays()
+        tp.free()
+    assert_paths_equal(off, vert, ref.pp_offsets, ref.pp_vertices, f"{which} split {split} PP")
+    assert_paths_equal(toff, tvert, ref.tp_offsets, ref.tp_vertices, f"{which} split {split} TP")
+
+
+def test_unsupported_work_split_rejected():
+    cfg = G.config1_cfg()
+    with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit) as h:
+        for bad in (0, 5, -1):
+            with pytest.raises(tpg.TPGError) as e:
+                tpg.tpg_set_work_split(h, bad)
+            assert e.value.code == tpg.TPG_EINVAL
+
+
 def test_unsupported_tile_shape_rejected():
     cfg = G.config1_cfg()
     with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit) as h:
