@@ -169,18 +169,21 @@ __device__ __forceinline__ void flush_counts(const AggSlots &A, int s, int own, 
 }
 
 // One persistent cooperative launch walks the levels.  Level k is cut into
-// NC = CPG * G equal contiguous chunks; warp w of the GW warps takes chunks
-// w, w + GW, w + 2GW, ..., so each warp's work is spread over the whole level
-// and a region of costly paths is shared by many warps.  Any chunk's
+// NC = CPG * G equal contiguous chunks, and each chunk into `split` work
+// units; warp w of block b takes units w * G + b, then every GW-th after it,
+// so each warp's and each block's (SM's) work is spread over the whole level
+// and a region of costly paths is shared by many warps and SMs.  Any chunk's
 // offsets in level k+1 and in the PP list are known before the level starts:
 // the count word of each path of level k (tcnt) was computed when that path
 // was written, and the writer added it to the entry of the chunk that owns
 // the path and to that chunk's group (CPG consecutive chunks).  After one
 // grid barrier per level each block scans the G group totals into shared
 // memory; a warp that claims chunk c adds the entries of the chunks before c
-// in its group.  The warp walks the chunk in tiles of 32 * ITEMS paths (lane
-// l owns paths j*32 + l, so every load is coalesced) with warp-level scans
-// only, and writes every child together with the child's own count word.
+// in its group (and, for a later unit of the chunk, the children and PPs of
+// the chunk's earlier units, summed from their count words).  The warp walks
+// its unit in tiles of 32 * ITEMS paths (lane l owns paths j*32 + l, so
+// every load is coalesced) with warp-level scans only, and writes every
+// child together with the child's own count word.
 // Each path is read once and written once.
 //
 // Slots rotate: level k reads slot k%3, accumulates into slot (k+1)%3, and
