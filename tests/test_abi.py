@@ -93,6 +93,8 @@ def test_null_handles(lib):
     assert lib.tpg_test_paths(None, ctypes.byref(out)) == tpg.TPG_EHANDLE
     assert lib.tpg_set_result_location(None, 0) == tpg.TPG_EHANDLE
     assert lib.tpg_get_stats(None, ctypes.byref(tpg._Stats())) == tpg.TPG_EHANDLE
+    assert lib.tpg_set_tile_shape(None, 512, 1) == tpg.TPG_EHANDLE
+    assert lib.tpg_set_work_split(None, 2) == tpg.TPG_EHANDLE
     lib.tpg_free(None)  # no-op
 
 
