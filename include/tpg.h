@@ -28,6 +28,18 @@
  *  - A handle is not to be used from two host threads at once.  Work is
  *    issued on the handle's CUDA stream (tpg_set_stream); calls return only
  *    after their results are complete.
+ *
+ * Typical use
+ *     tpg_cfg *g;
+ *     tpg_paths *pp, *tp;
+ *     if (tpg_load_cfg(n, row_ptr, col, entry, exit, &g) != TPG_OK) ...;
+ *     tpg_prime_paths(g, &pp);   // pp->offsets[0..P], pp->vertices[0..offsets[P])
+ *     tpg_test_paths(g, &tp);    // same layout; may share pp's storage
+ *     ...
+ *     tpg_free(tp); tpg_free(pp); tpg_free(g);
+ * Many graphs at once: tpg_load_cfg_batch (results grouped by graph through
+ * graph_path_ptr), and for repeated batches of one shape tpg_graph_capture /
+ * tpg_graph_launch, which replay the whole pipeline as one CUDA graph.
  */
 #ifndef TPG_H
 #define TPG_H
