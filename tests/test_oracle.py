@@ -110,6 +110,69 @@ def test_complete_digraph_cycles(n):
     assert all(p[0] == p[-1] for p in res.pp_list())
 
 
+# ---------------------------------------------------------------------------
+# per-root volumes (the sizer's labels and the count-only mode): closed forms
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 4, 9])
+def test_diamond_chain_per_root_counts(k):
+    # d_i = 3i, a_i = 3i+1, b_i = 3i+2.  From d_i a path ends at d_{i+j}
+    # (2^j ways, j = 0..k-i) or at a or b of diamond i+j (2^{j+1} ways,
+    # j = 0..k-i-1): 2^{k-i+2} - 3 paths.  From a_i or b_i: the one-vertex
+    # path plus the single arc into d_{i+1} followed by any path from
+    # d_{i+1}: 2^{k-i+1} - 2.  Only the 2^k entry-to-exit paths (2k+1
+    # vertices each, all rooted at d_0) are prime.
+    cfg = G.diamond_chain(k)
+    res = oracle.run_cfg(cfg, test_paths=False, want_paths=False)
+    paths = np.zeros(cfg.n, np.int64)
+    for i in range(k + 1):
+        paths[3 * i] = 2 ** (k - i + 2) - 3
+    for i in range(k):
+        paths[3 * i + 1] = paths[3 * i + 2] = 2 ** (k - i + 1) - 2
+    np.testing.assert_array_equal(res.root_paths, paths)
+    pps = np.zeros(cfg.n, np.int64)
+    pps[0] = 2 ** k
+    np.testing.assert_array_equal(res.root_pps, pps)
+    np.testing.assert_array_equal(res.root_pp_ints, pps * (2 * k + 1))
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 33])
+def test_ring_per_root_counts(n):
+    # from each root: n acyclic paths (1..n vertices) and the closed cycle;
+    # the cycle (n+1 vertices) is the root's only PP
+    res = oracle.run_cfg(G.ring(n), test_paths=False, want_paths=False)
+    np.testing.assert_array_equal(res.root_paths, np.full(n, n + 1))
+    np.testing.assert_array_equal(res.root_pps, np.ones(n))
+    np.testing.assert_array_equal(res.root_pp_ints, np.full(n, n + 1))
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 6])
+def test_complete_digraph_per_root_counts(n):
+    # from r: (n-1)!/(n-j)! acyclic paths of j vertices (j = 1..n); each with
+    # j >= 2 also closes a cycle of j+1 vertices, and those cycles are the
+    # root's PPs (every acyclic path can still close, so none is prime)
+    arr = [math.factorial(n - 1) // math.factorial(n - j) for j in range(1, n + 1)]
+    cyc = arr[1:]
+    res = oracle.run_cfg(G.complete_digraph(n), test_paths=False, want_paths=False)
+    np.testing.assert_array_equal(res.root_paths, np.full(n, sum(arr) + sum(cyc)))
+    np.testing.assert_array_equal(res.root_pps, np.full(n, sum(cyc)))
+    np.testing.assert_array_equal(res.root_pp_ints, np.full(n, sum((j + 1) * c for j, c in zip(range(2, n + 1), cyc))))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_per_root_counts_vs_literal(seed):
+    # brute force: group the literal oracle's simple paths and PPs by first vertex
+    cfg = G.random_digraph(6, 0.35, 1000 + seed, self_loops=(seed % 2 == 0))
+    succ = literal.succ_lists(cfg.n, cfg.row_ptr, cfg.col)
+    sp_all = literal.simple_paths(cfg.n, succ)
+    pps = literal.prime_paths(cfg.n, succ)
+    res = oracle.run(cfg.n, cfg.row_ptr, cfg.col, want_paths=False)
+    np.testing.assert_array_equal(res.root_paths, np.bincount([p[0] for p in sp_all], minlength=cfg.n))
+    np.testing.assert_array_equal(res.root_pps, np.bincount([p[0] for p in pps], minlength=cfg.n))
+    np.testing.assert_array_equal(res.root_pp_ints,
+                                  np.bincount([p[0] for p in pps], weights=[len(p) for p in pps],
+                                              minlength=cfg.n).astype(np.int64))
+
+
 def test_self_loop_and_isolated_vertex():
     # 0 -> 0 self-loop, 1 isolated: PPs are <0,0> and <1>
     rp, col = G.csr_from_arcs(2, [(0, 0)])
@@ -256,8 +319,29 @@ def test_test_paths_construction_fig1():
         match = [t for t in tps if len(t) == lens and
                  t[dist[cfg.entry, f]:dist[cfg.entry, f] + len(p)] == p]
         assert match, p
-    # TP count for the example is the deduplicated count
-    assert len(tps) == 10
+    # the TP set itself, derived by hand from the 13 arcs (golden file)
+    golden_map, golden_tps = load_fig1_tps()
+    assert res.tp_list() == golden_tps
+    assert [p for p, _ in golden_map] == res.pp_list()
+    for p, t in golden_map:
+        # each PP sits in its TP right after the shortest entry prefix
+        d = int(dist[cfg.entry, p[0]])
+        assert t[d:d + len(p)] == p and t in tps
+
+
+def load_fig1_tps():
+    pps, tps = [], []
+    with open(os.path.join(GOLDEN, "fig1_test_paths.txt")) as f:
+        for line in f:
+            parts = line.split()
+            if not parts or parts[0].startswith("#"):
+                continue
+            if parts[0] == "pp":
+                i = parts.index(":")
+                pps.append((tuple(int(x) for x in parts[1:i]), tuple(int(x) for x in parts[i + 1:])))
+            elif parts[0] == "tp":
+                tps.append(tuple(int(x) for x in parts[1:]))
+    return pps, tps
 
 
 def test_unreachable_pp_reports_error():
