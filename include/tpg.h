@@ -73,13 +73,14 @@ typedef struct tpg_paths {
     uint32_t magic;                 /* internal tag */
     int32_t num_graphs;             /* 1 for tpg_load_cfg handles */
     int64_t num_paths;              /* P */
-    int32_t location;               /* TPG_RESULT_HOST or TPG_RESULT_DEVICE */
-    int32_t reserved;
     const int64_t *graph_path_ptr;  /* [num_graphs+1]: paths of graph g are
                                        [graph_path_ptr[g], graph_path_ptr[g+1]) */
     const int64_t *offsets;         /* [P+1], offsets[0] = 0 */
     const int32_t *vertices;        /* [offsets[P]], graph-local vertex ids, canonical order per graph */
+    /* fields after the six above (which every caller may rely on) */
     int64_t num_vertices;           /* offsets[P], so that no read of a device array is needed */
+    int32_t location;               /* TPG_RESULT_HOST or TPG_RESULT_DEVICE */
+    int32_t reserved;
 } tpg_paths;
 
 /* Statistics of the last tpg_prime_paths call on a handle. */
@@ -230,10 +231,25 @@ int tpg_set_tile_shape(tpg_cfg *g, int32_t block, int32_t items);
 int tpg_set_work_split(tpg_cfg *g, int32_t split);
 
 /*
+ * Limit, in nanoseconds, of every wait at a grid-wide barrier of the
+ * handle's frontier launches (default 4 s; ns < 0 restores it).  The
+ * frontier kernel is one persistent launch whose blocks meet at a barrier
+ * after each level; a block that waits longer than this stops, the launch
+ * ends with its error flag set, and the call returns TPG_ETIMEOUT with the
+ * handle still usable.  A watchdog for callers that must never wait on a
+ * stalled GPU; with ns = 0 any wait at all times out, which is how the
+ * error path is tested.  Results never depend on it otherwise.
+ */
+int tpg_set_wait_limit(tpg_cfg *g, int64_t ns);
+
+/*
  * Initial capacities of the handle's path arena: total simple paths,
- * simple paths of one level, and prime paths.  The arena grows (and the
- * enumeration restarts from scratch) when one is exceeded, so results never
- * depend on them; a pre-sizing policy (e.g. the learned sizer) sets them.
+ * simple paths of one level, and prime paths.  When one is exceeded, the
+ * frontier launch stops after the exact size of the level that did not fit
+ * is known; the library adds an arena segment (or a larger frontier or PP
+ * list) and relaunches at that level, so finished levels are kept and
+ * results never depend on these values.  A pre-sizing policy (e.g. the
+ * learned sizer) sets them.
  */
 int tpg_set_capacity(tpg_cfg *g, int64_t nodes, int64_t level_nodes, int64_t prime_paths);
 
@@ -340,10 +356,11 @@ int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);
  * library.)
  *
  * For callers that cannot allocate memory when they need the result: code
- * issuing work while its stream is captured into a CUDA graph (cudaMalloc is
- * not permitted during capture), code working inside a memory budget fixed
- * in advance, and hosts whose framework owns every allocation.  The call
- * runs the same kernels as tpg_load_cfg + tpg_prime_paths, keeps every
+ * working inside a device-memory budget fixed in advance (where a
+ * cudaMalloc in mid-run could fail or break the budget), and hosts whose
+ * framework owns every allocation and hands the library only the buffers
+ * it reads and writes.  The call runs the same kernels as tpg_load_cfg +
+ * tpg_prime_paths, keeps every
  * temporary in one fixed-size device array built into the library (about
  * 33 MB, held by every GPU that loads the library until the process exits),
  * and writes into buffers the caller owns.  It calls no cudaMalloc,
@@ -364,7 +381,8 @@ int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);
  * *num_vertices set to the sizes needed.  TPG_EINVAL for a malformed CSR.
  *
  * The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current) and caches it.  The call waits on `stream` between
+ * its steps (it reads level sizes back to choose the next launches).
  * Every call reuses the same array and clears what must start at zero;
  * calls whose GPU work overlaps (e.g. on two streams at once) race on it.
  */

@@ -372,6 +372,7 @@ struct tpg_cfg {
     long long node_cap = 0, lvl_cap = 0, pp_cap = 0;
     EnumShape shape{0, 0};
     int split = 1;  // work units per chunk of the frontier kernel
+    unsigned long long spin_ns = SPIN_LIMIT_NS;  // limit of each grid-barrier wait of the frontier launch
     // generic scratch
     DevBuf s_keys[2], s_refs[2], s_len, s_tmp, s_i32[3], s_i64[4];
     DevBuf rank_cnt, rank_pre[2], rank_noff, rank_bsum;  // PP ranking scratch
@@ -744,6 +745,7 @@ int enumerate_levels(tpg_cfg *g) {
         a.stop_level = g->ctl.as<int>() + 1;
         a.bar = (unsigned *)(g->ctl.as<char>() + CTL_BAR_OFFSET);
         a.root_counts = g->root_counts;
+        a.spin_ns = g->spin_ns;
         int grid = 0;
         CK(cudaEventRecord(g->ev[0], s));
         CK(launch_enumerate(a, g->shape, g->num_sms, s, &grid));
@@ -1303,6 +1305,7 @@ int capture_plan(tpg_cfg *g) {
     a.err = g->ctl.as<int>();
     a.stop_level = g->ctl.as<int>() + 1;
     a.bar = (unsigned *)(g->ctl.as<char>() + CTL_BAR_OFFSET);
+    a.spin_ns = g->spin_ns;
 
     GmArgs m{};
     m.g = g->gd;
@@ -2086,6 +2089,12 @@ int tpg_set_work_split(tpg_cfg *g, int32_t split) {
     if (!is_cfg(g)) return TPG_EHANDLE;
     if (split < 1 || split > 4) return TPG_EINVAL;
     g->split = split;
+    return TPG_OK;
+}
+
+int tpg_set_wait_limit(tpg_cfg *g, int64_t ns) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    g->spin_ns = ns < 0 ? SPIN_LIMIT_NS : (unsigned long long)ns;
     return TPG_OK;
 }
 

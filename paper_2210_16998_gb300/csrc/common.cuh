@@ -121,12 +121,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
 // counts (all zero at launch; each counter is reset by its last arrival).
 // Arrivals on one address are serialised by the L2, so splitting them over
 // groups shortens the barrier from ~G to ~G/BAR_GROUPS + BAR_GROUPS steps.
-// Every wait is bounded by SPIN_LIMIT_NS (ERR_TIMEOUT, false on expiry).
-// Also false, on every block alike, if an error flag in `stop` was raised
-// before the barrier.
+// Every wait is bounded by `limit_ns` (default SPIN_LIMIT_NS; ERR_TIMEOUT,
+// false on expiry).  Also false, on every block alike, if an error flag in
+// `stop` was raised before the barrier.
 constexpr int BAR_GROUPS = 32;
 constexpr int BAR_WORDS = 2 + BAR_GROUPS;
-__device__ __forceinline__ bool grid_barrier_tree(unsigned *bar, int *err, int stop) {
+__device__ __forceinline__ bool grid_barrier_tree(unsigned *bar, int *err, int stop,
+                                                  unsigned long long limit_ns = SPIN_LIMIT_NS) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -152,7 +153,7 @@ __device__ __forceinline__ bool grid_barrier_tree(unsigned *bar, int *err, int s
             const unsigned long long t0 = global_ns();
             while (ld_acquire_u32(bar + 1) == gen) {
                 __nanosleep(64);
-                if (global_ns() - t0 > SPIN_LIMIT_NS) {
+                if (global_ns() - t0 > limit_ns) {
                     atomicOr(err, ERR_TIMEOUT);
                     ok = 0;
                     break;

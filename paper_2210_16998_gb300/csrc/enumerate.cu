@@ -28,6 +28,8 @@
 // finished level is ever recomputed or copied.  Frontier (ping-pong, two
 // buffers): node = {first, last} (int2) and the visited bitset stored as W
 // separate word arrays (word j of node i at j * lvl_cap + i).
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
             A.gc((k + 1) % 3)[b] = A.gp((k + 1) % 3)[b] = 0;
             A.gc((k + 2) % 3)[b] = A.gp((k + 2) % 3)[b] = 0;
         }
-        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT, a.spin_ns)) return;
     }
 
     // the level being processed; after the first, every block derives the
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
         }
         flush_counts(A, s1, cur_own, acc_c, acc_p);
         if (C == 0) break;  // nothing follows; the end of the launch orders the writes
-        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT | ERR_INVAL)) break;
+        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT | ERR_INVAL, a.spin_ns)) break;
         count = C;
         lnodes = next;
         lpp += P;
@@ -574,21 +576,35 @@ static cudaError_t launch_wbi(const EnumArgs &args, int num_sms, cudaStream_t s,
     // the group prefixes take 2 * grid int64 of shared memory; size it for
     // the largest grid this block size can have
     const size_t smem = sizeof(long long) * 2 * (size_t)num_sms * (2048 / BLOCK);
-    static int blocks_per_sm = -1;
-    if (blocks_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(enumerate_kernel<W, BLOCK, ITEMS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, enumerate_kernel<W, BLOCK, ITEMS>, BLOCK,
-                                                          smem);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
-        if (blocks_per_sm > 2048 / BLOCK) blocks_per_sm = 2048 / BLOCK;
+    // the shared-memory attribute and the occupancy are per device (and per
+    // shared-memory size): cached for each device id
+    constexpr int MAX_DEV = 64;
+    static std::mutex mu;
+    static size_t set_smem[MAX_DEV] = {};
+    static int set_bps[MAX_DEV] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
+    int blocks_per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (set_smem[dev] != smem) {
+            e = cudaFuncSetAttribute(enumerate_kernel<W, BLOCK, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+            int bps = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, enumerate_kernel<W, BLOCK, ITEMS>, BLOCK, smem);
+            if (e != cudaSuccess) return e;
+            if (bps < 1) return cudaErrorInvalidConfiguration;
+            set_bps[dev] = bps > 2048 / BLOCK ? 2048 / BLOCK : bps;
+            set_smem[dev] = smem;
+        }
+        blocks_per_sm = set_bps[dev];
     }
     const int grid = num_sms * blocks_per_sm;
     *grid_out = grid;
     if (args.agg_cap < enum_agg_words(grid)) return cudaErrorInvalidValue;
-    cudaError_t e;
     if (args.seed_level1) {
         if ((e = launch_seed_level1(args, s)) != cudaSuccess) return e;
     }

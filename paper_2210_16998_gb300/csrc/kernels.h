@@ -63,6 +63,7 @@ struct EnumArgs {
     int *stop_level;         // level whose next level did not fit (written with the flags)
     unsigned *bar;           // tree grid barrier, BAR_WORDS words (zeroed)
     unsigned long long *root_counts;  // optional [3*N]: per first vertex, simple paths, PPs, PP vertices
+    unsigned long long spin_ns;       // limit of every grid-barrier wait (SPIN_LIMIT_NS unless set)
 };
 
 // enumerate.cu

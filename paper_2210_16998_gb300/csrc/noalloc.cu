@@ -2,14 +2,14 @@
 // memory allocation.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// answer: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc is not allowed during capture), code that runs under a fixed
-// memory budget handed out up front, and code embedded in a host framework
-// that owns every allocation itself.  For them this entry point runs the same
-// kernels as tpg_load_cfg + tpg_prime_paths, but every temporary buffer (the
-// predecessor lists, the path arena, the frontier, the look-back flags, the
-// ordering buffers) lives in one file-scope __device__ array of fixed size,
-// and the results go to buffers the caller already owns.
+// answer: code that runs under a fixed memory budget handed out up front
+// (an allocation in mid-run could fail or break it), and code embedded in a
+// host framework that owns every allocation itself.  For them this entry
+// point runs the same kernels as tpg_load_cfg + tpg_prime_paths, but every
+// temporary buffer (the predecessor lists, the path arena, the frontier, the
+// per-chunk level counts, the ordering buffers) lives in one file-scope
+// __device__ array of fixed size, and the results go to buffers the caller
+// already owns.
 //
 // The array (NA_SCRATCH_BYTES, about 33 MB) is part of the library image:
 // every GPU that loads the library keeps it until the process exits.  All
@@ -208,6 +208,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     a.err = err;
     a.stop_level = err + 1;
     a.bar = (unsigned *)(S + NA.ctl + CTL_BAR_OFFSET);
+    a.spin_ns = SPIN_LIMIT_NS;
     NA_CK(cudaMemsetAsync(a.levels, 0, sizeof(LevelRec) * NA_MAX_LEVELS, s));
     NA_CK(cudaMemsetAsync(err, 0, CTL_BYTES, s));
     int num_sms = 1, dev = 0, grid = 0;

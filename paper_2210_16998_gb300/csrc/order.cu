@@ -9,6 +9,7 @@
 // upward: the run accumulated so far is keyed by each element's ancestor
 // index at the current level (one parent-link step per level), and merged
 // with that level's own PPs by key.  Keys of the two inputs never tie.
+#include <atomic>
 #include "common.cuh"
 #include "kernels.h"
 #include "paths_dev.cuh"
@@ -400,11 +401,18 @@ __global__ void __launch_bounds__(RANK_BLOCK) rank_pps_kernel(RankArgs a) {
 int rank_pps_grid(int num_sms) { return num_sms * 8; }
 
 cudaError_t rank_pps(const RankArgs &args, int num_sms, cudaStream_t s) {
-    static int per_sm = -1;
-    if (per_sm < 0) {
+    // occupancy per device id (0 = not yet asked)
+    static std::atomic<int> per_sm_dev[64];
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    int per_sm = per_sm_dev[dev].load();
+    if (per_sm <= 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rank_pps_kernel, RANK_BLOCK, 0);
         if (e != cudaSuccess) return e;
         per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+        per_sm_dev[dev].store(per_sm);
     }
     RankArgs a = args;
     void *params[] = {&a};

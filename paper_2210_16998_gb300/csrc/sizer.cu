@@ -15,6 +15,7 @@
 // BF16 tensor-core MMAs (mma.sync m16n8k16, FP32 accumulators); the
 // aggregation, head, weight gradients and optimiser are plain CUDA-core
 // kernels.
+#include <atomic>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -452,12 +453,17 @@ template <int K, int EPI>
 cudaError_t sz_gemm(SizerNet *n, const bf16 *A, long long M, const bf16 *Bt, int NC, const float *bias, bf16 *ob,
                     float *of) {
     const size_t smem = 2 * 64 * (K + 8) * sizeof(bf16);
-    static bool attr = false;
-    if (!attr) {
+    // the shared-memory attribute is set once per device id
+    static std::atomic<bool> attr[64];
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev].load()) {
         cudaError_t e = cudaFuncSetAttribute(sz_mma_gemm<K, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[dev].store(true);
     }
     dim3 grid((unsigned)((M + 63) / 64), (unsigned)((NC + 63) / 64));
     sz_mma_gemm<K, EPI><<<grid, 128, smem, n->s>>>(A, M, Bt, NC, bias, ob, of);

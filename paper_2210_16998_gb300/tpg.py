@@ -48,12 +48,12 @@ class _Paths(ctypes.Structure):
         ("magic", ctypes.c_uint32),
         ("num_graphs", ctypes.c_int32),
         ("num_paths", ctypes.c_int64),
-        ("location", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
         ("graph_path_ptr", ctypes.c_void_p),
         ("offsets", ctypes.c_void_p),
         ("vertices", ctypes.c_void_p),
         ("num_vertices", ctypes.c_int64),
+        ("location", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -133,6 +133,7 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_set_tile_shape.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
         lib.tpg_set_work_split.argtypes = [P, ctypes.c_int32]
         lib.tpg_set_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        lib.tpg_set_wait_limit.argtypes = [P, ctypes.c_int64]
         lib.tpg_set_output_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         lib.tpg_graph_capture.argtypes = [P]
         lib.tpg_root_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
@@ -443,6 +444,11 @@ def set_tile(cfg: Cfg, tile):
     tpg_set_work_split(cfg, int(tile[2]) if len(tile) > 2 else 1)
 
 
+def tpg_set_wait_limit(cfg: Cfg, ns: int):
+    """Limit of each grid-barrier wait of the handle's frontier launches (ns < 0: default)."""
+    _check(load_library().tpg_set_wait_limit(cfg.handle, int(ns)), "tpg_set_wait_limit")
+
+
 def tpg_set_capacity(cfg: Cfg, nodes: int, level_nodes: int, prime_paths: int):
     _check(load_library().tpg_set_capacity(cfg.handle, int(nodes), int(level_nodes), int(prime_paths)),
            "tpg_set_capacity")
@@ -502,10 +508,27 @@ def stats_dict(st) -> dict:
 def tpg_prime_paths_noalloc(n, m, row_ptr_dev, col_dev, offsets_dev, vertices_dev, stream=None):
     """Prime paths of one small graph into caller-owned device buffers, with no
     allocation inside the library (for callers that cannot allocate at call
-    time, e.g. during stream capture).  row_ptr_dev/col_dev/offsets_dev/
-    vertices_dev are CUDA tensors (int32, int32, int64, int32).  Returns
+    time: a memory budget fixed in advance, or a host framework that owns
+    every allocation).  row_ptr_dev / col_dev / offsets_dev / vertices_dev
+    are contiguous CUDA tensors on the current device of dtype int32 [n+1],
+    int32 [>= m], int64 [cap_paths+1] and int32 [cap_vertices].  Returns
     (rc, num_paths, num_vertices); rc is TPG_OK or a TPG_E* code (TPG_ETOOBIG
-    also when the output buffers are too small, with the sizes needed)."""
+    also when the output buffers are too small, with the sizes needed).
+    Arguments of the wrong dtype, device, layout or size give TPG_EINVAL
+    without calling the library."""
+    import torch
+
+    want = ((row_ptr_dev, torch.int32), (col_dev, torch.int32), (offsets_dev, torch.int64),
+            (vertices_dev, torch.int32))
+    for t, dt in want:
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            return TPG_EINVAL, 0, 0
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t, _ in want):
+        return TPG_EINVAL, 0, 0
+    if int(n) < 1 or int(m) < 0 or row_ptr_dev.numel() != int(n) + 1 or col_dev.numel() < int(m) \
+            or offsets_dev.numel() < 1:
+        return TPG_EINVAL, 0, 0
     lib = load_library()
     npaths, nverts = ctypes.c_int64(0), ctypes.c_int64(0)
     s = _current_stream() if stream is None else ctypes.c_void_p(stream)

@@ -95,6 +95,7 @@ def test_null_handles(lib):
     assert lib.tpg_get_stats(None, ctypes.byref(tpg._Stats())) == tpg.TPG_EHANDLE
     assert lib.tpg_set_tile_shape(None, 512, 1) == tpg.TPG_EHANDLE
     assert lib.tpg_set_work_split(None, 2) == tpg.TPG_EHANDLE
+    assert lib.tpg_set_wait_limit(None, 1000) == tpg.TPG_EHANDLE
     lib.tpg_free(None)  # no-op
 
 
@@ -113,3 +114,38 @@ def test_batch_load_rejects_bad_graph(lib):
     rc = lib_.tpg_load_cfg_batch(2, *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for a in arrs],
                                  ctypes.byref(h))
     assert rc == tpg.TPG_EINVAL and not h.value
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the header's field offsets and
+    sizes (compiled with the system C compiler against include/tpg.h)."""
+    import subprocess
+
+    structs = {"tpg_paths": tpg._Paths, "tpg_stats": tpg._Stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tpg.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    from paper_2210_16998_gb300 import build as B
+
+    subprocess.check_call(["gcc", "-I", B.INCLUDE, "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {}
+    for line in out:
+        if line:
+            s, f, v = line.split()
+            got[(s, f)] = int(v)
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+    # the first six fields of tpg_paths keep the order of the boundary's
+    # definition: magic, num_graphs, num_paths, graph_path_ptr, offsets, vertices
+    order = sorted(("magic", "num_graphs", "num_paths", "graph_path_ptr", "offsets", "vertices",
+                    "num_vertices", "location", "reserved"), key=lambda f: got[("tpg_paths", f)])
+    assert order[:6] == ["magic", "num_graphs", "num_paths", "graph_path_ptr", "offsets", "vertices"]
