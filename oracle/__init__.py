@@ -6,7 +6,9 @@ the CUDA library never does, and the oracle never imports the library.
 
 ``tpg_oracle.c`` is a plain single-threaded enumeration written from the
 paper's definitions (Sec. 2 simple path, Def. 1 prime path, Problem 1 output)
-and is compiled here with the system C compiler.  ``literal.py`` is a second,
+and is compiled here with the system C compiler.  Its root-parallel driver
+(``run_parallel``) runs the same enumeration root by root on every host core
+for the all-core CPU baseline.  ``literal.py`` is a second,
 quadratic oracle for tiny graphs that applies the definitions word for word.
 """
 from __future__ import annotations
@@ -42,7 +44,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
                            "-o", tmp, _SRC])
     os.replace(tmp, _SO)
     return _SO
@@ -58,6 +60,9 @@ def _load():
         i32p = ctypes.POINTER(ctypes.c_int32)
         lib.orc_prime_paths.restype = P
         lib.orc_prime_paths.argtypes = [ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int64]
+        lib.orc_run_parallel.restype = P
+        lib.orc_run_parallel.argtypes = [ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_test_paths.restype = ctypes.c_int
         lib.orc_test_paths.argtypes = [P, i32p, i32p, ctypes.c_int, ctypes.c_int]
         lib.orc_bfs_tables.restype = ctypes.c_int
@@ -130,32 +135,68 @@ def run(n, row_ptr, col, entry=None, exit=None, want_paths=True, limit=0,
     if not h:
         raise OracleError(ORC_ENOMEM, "prime_paths")
     try:
-        err = lib.orc_error(h)
-        if err:
-            raise OracleError(err, "prime_paths")
-        res = OracleResult(
-            n=int(n),
-            n_simple=int(lib.orc_n_simple(h)),
-            len_counts=_copy(lib.orc_len_counts(h), n + 3, np.int64),
-            pp_len_counts=_copy(lib.orc_pp_len_counts(h), n + 3, np.int64),
-            root_paths=_copy(lib.orc_root_paths(h), n, np.int64),
-            root_pp_ints=_copy(lib.orc_root_pp_ints(h), n, np.int64),
-            root_pps=_copy(lib.orc_root_pps(h), n, np.int64),
-        )
-        if want_paths or test_paths:
-            cnt = int(lib.orc_pp_count(h))
-            res.pp_offsets = _copy(lib.orc_pp_offsets(h), cnt + 1, np.int64)
-            res.pp_vertices = _copy(lib.orc_pp_vertices(h), int(lib.orc_pp_total(h)), np.int32)
+        res = _result(lib, h, n, want_paths or test_paths)
         if test_paths:
             rc = lib.orc_test_paths(h, rpp, clp, int(entry), int(exit))
             if rc:
                 raise OracleError(rc, "test_paths")
-            cnt = int(lib.orc_tp_count(h))
-            res.tp_offsets = _copy(lib.orc_tp_offsets(h), cnt + 1, np.int64)
-            res.tp_vertices = _copy(lib.orc_tp_vertices(h), int(lib.orc_tp_total(h)), np.int32)
+            _take_tps(lib, h, res)
         return res
     finally:
         lib.orc_free(h)
+
+
+def run_parallel(n, row_ptr, col, entry=None, exit=None, want_paths=True, test_paths=False,
+                 threads=None) -> OracleResult:
+    """The same result as run(), computed by the root-parallel driver on
+    `threads` host threads (default: every core)."""
+    lib = _load()
+    threads = int(threads or os.cpu_count() or 1)
+    rp, rpp = _i32(row_ptr)
+    cl, clp = _i32(col if len(col) else np.zeros(1, np.int32))
+    h = lib.orc_run_parallel(int(n), rpp, clp, int(entry if entry is not None else -1),
+                             int(exit if exit is not None else -1), 1 if want_paths else 0,
+                             1 if test_paths else 0, threads)
+    if not h:
+        raise OracleError(ORC_ENOMEM, "run_parallel")
+    try:
+        res = _result(lib, h, n, want_paths or test_paths)
+        if test_paths:
+            _take_tps(lib, h, res)
+        return res
+    finally:
+        lib.orc_free(h)
+
+
+def run_cfg_parallel(cfg, test_paths=True, want_paths=True, threads=None) -> OracleResult:
+    return run_parallel(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, want_paths=want_paths,
+                        test_paths=test_paths, threads=threads)
+
+
+def _take_tps(lib, h, res):
+    cnt = int(lib.orc_tp_count(h))
+    res.tp_offsets = _copy(lib.orc_tp_offsets(h), cnt + 1, np.int64)
+    res.tp_vertices = _copy(lib.orc_tp_vertices(h), int(lib.orc_tp_total(h)), np.int32)
+
+
+def _result(lib, h, n, with_paths):
+    err = lib.orc_error(h)
+    if err:
+        raise OracleError(err, "prime_paths")
+    res = OracleResult(
+        n=int(n),
+        n_simple=int(lib.orc_n_simple(h)),
+        len_counts=_copy(lib.orc_len_counts(h), n + 3, np.int64),
+        pp_len_counts=_copy(lib.orc_pp_len_counts(h), n + 3, np.int64),
+        root_paths=_copy(lib.orc_root_paths(h), n, np.int64),
+        root_pp_ints=_copy(lib.orc_root_pp_ints(h), n, np.int64),
+        root_pps=_copy(lib.orc_root_pps(h), n, np.int64),
+    )
+    if with_paths:
+        cnt = int(lib.orc_pp_count(h))
+        res.pp_offsets = _copy(lib.orc_pp_offsets(h), cnt + 1, np.int64)
+        res.pp_vertices = _copy(lib.orc_pp_vertices(h), int(lib.orc_pp_total(h)), np.int32)
+    return res
 
 
 def run_cfg(cfg, test_paths=True, want_paths=True, limit=0) -> OracleResult:

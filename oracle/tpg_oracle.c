@@ -33,6 +33,8 @@
  *     then p, then path(last p -> exit), joined at the shared endpoints; the
  *     TP set is the sorted, duplicate-free set of TP(p) over all PPs p.
  */
+#include <pthread.h>
+#include <stdatomic.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -64,6 +66,11 @@ typedef struct orc_result {
     int32_t *bfs_pred;      /* [n*n] or NULL */
     int err;
 } orc_result;
+
+void orc_free(orc_result *r);
+int orc_bfs_tables(int n, const int32_t *row_ptr, const int32_t *col, int32_t *dist, int32_t *pred);
+orc_result *orc_prime_paths_range(int n, const int32_t *row_ptr, const int32_t *col,
+                                  int want_paths, int64_t limit, int root_lo, int root_hi);
 
 static int sl_init(seqlist *s) {
     s->n = 0; s->cap = 1024; s->nv = 0; s->capv = 8192;
@@ -194,8 +201,8 @@ static int sort_unique(seqlist *s, int dedup) {
  * want_paths = 0 only counts.  limit > 0 aborts with ORC_ELIMIT once more
  * than `limit` simple paths have been visited.
  */
-orc_result *orc_prime_paths(int n, const int32_t *row_ptr, const int32_t *col,
-                            int want_paths, int64_t limit) {
+orc_result *orc_prime_paths_range(int n, const int32_t *row_ptr, const int32_t *col,
+                                  int want_paths, int64_t limit, int root_lo, int root_hi) {
     orc_result *r = (orc_result *)calloc(1, sizeof(orc_result));
     if (!r) return NULL;
     r->n = n;
@@ -216,7 +223,9 @@ orc_result *orc_prime_paths(int n, const int32_t *row_ptr, const int32_t *col,
         r->err = ORC_ENOMEM;
         goto done;
     }
-    for (int root = 0; root < n && !r->err; root++) {
+    if (root_lo < 0) root_lo = 0;
+    if (root_hi > n) root_hi = n;
+    for (int root = root_lo; root < root_hi && !r->err; root++) {
         int len = 1;
         path[0] = root;
         onpath[root] = 1;
@@ -301,6 +310,12 @@ done:
     return r;
 }
 
+/* Every root (step 1 over all of V). */
+orc_result *orc_prime_paths(int n, const int32_t *row_ptr, const int32_t *col,
+                            int want_paths, int64_t limit) {
+    return orc_prime_paths_range(n, row_ptr, col, want_paths, limit, 0, n);
+}
+
 /* All-pairs BFS with the lowest-id predecessor tie-break (step 4). */
 int orc_bfs_tables(int n, const int32_t *row_ptr, const int32_t *col,
                    int32_t *dist, int32_t *pred) {
@@ -348,6 +363,31 @@ static int bfs_path(int n, const int32_t *dist, const int32_t *pred, int a, int 
     return len;
 }
 
+/* TP(p) for the PPs i0..i1-1 of r (in that order) appended to `out`. */
+static int tp_build_range(const orc_result *r, const int32_t *dist, const int32_t *pred,
+                          int entry, int exitv, int64_t i0, int64_t i1, seqlist *out) {
+    int n = r->n;
+    int32_t *pre = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t *suf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * n + 4));
+    if (!pre || !suf || !buf) { free(pre); free(suf); free(buf); return ORC_ENOMEM; }
+    int rc = ORC_OK;
+    for (int64_t i = i0; i < i1 && rc == ORC_OK; i++) {
+        const int32_t *p = r->pp.v + r->pp.off[i];
+        int len = (int)(r->pp.off[i + 1] - r->pp.off[i]);
+        int lp = bfs_path(n, dist, pred, entry, p[0], pre);
+        int ls = bfs_path(n, dist, pred, p[len - 1], exitv, suf);
+        if (lp == 0 || ls == 0) { rc = ORC_EUNREACH; break; }
+        int k = 0;
+        for (int j = 0; j + 1 < lp; j++) buf[k++] = pre[j];   /* pre ends at p[0] */
+        for (int j = 0; j < len; j++) buf[k++] = p[j];
+        for (int j = 1; j < ls; j++) buf[k++] = suf[j];       /* suf starts at last */
+        if (sl_push(out, buf, k, -1)) rc = ORC_ENOMEM;
+    }
+    free(pre); free(suf); free(buf);
+    return rc;
+}
+
 int orc_test_paths(orc_result *r, const int32_t *row_ptr, const int32_t *col,
                    int entry, int exitv) {
     int n = r->n;
@@ -358,26 +398,156 @@ int orc_test_paths(orc_result *r, const int32_t *row_ptr, const int32_t *col,
     if (!r->bfs_dist || !r->bfs_pred) return ORC_ENOMEM;
     if (orc_bfs_tables(n, row_ptr, col, r->bfs_dist, r->bfs_pred)) return ORC_ENOMEM;
     if (sl_init(&r->tp)) return ORC_ENOMEM;
-    int32_t *pre = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
-    int32_t *suf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
-    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * n + 4));
-    if (!pre || !suf || !buf) { free(pre); free(suf); free(buf); return ORC_ENOMEM; }
-    int rc = ORC_OK;
-    for (int64_t i = 0; i < r->pp.n && rc == ORC_OK; i++) {
-        const int32_t *p = r->pp.v + r->pp.off[i];
-        int len = (int)(r->pp.off[i + 1] - r->pp.off[i]);
-        int lp = bfs_path(n, r->bfs_dist, r->bfs_pred, entry, p[0], pre);
-        int ls = bfs_path(n, r->bfs_dist, r->bfs_pred, p[len - 1], exitv, suf);
-        if (lp == 0 || ls == 0) { rc = ORC_EUNREACH; break; }
-        int k = 0;
-        for (int j = 0; j + 1 < lp; j++) buf[k++] = pre[j];   /* pre ends at p[0] */
-        for (int j = 0; j < len; j++) buf[k++] = p[j];
-        for (int j = 1; j < ls; j++) buf[k++] = suf[j];       /* suf starts at last */
-        if (sl_push(&r->tp, buf, k, -1)) rc = ORC_ENOMEM;
-    }
-    free(pre); free(suf); free(buf);
+    int rc = tp_build_range(r, r->bfs_dist, r->bfs_pred, entry, exitv, 0, r->pp.n, &r->tp);
     if (rc == ORC_OK) rc = sort_unique(&r->tp, 1);
     return rc;
+}
+
+/*
+ * Root-parallel driver, for the all-core CPU baseline.
+ *
+ * Every PP has exactly one first vertex, and the depth-first enumeration
+ * from one root never looks at another root's paths (simplicity and
+ * maximality, Sec. 2 and Def. 1, are properties of the path alone), so the
+ * roots are independent: `nthreads` threads take roots one at a time from a
+ * shared counter and run the enumeration above on each (step 1 restricted
+ * to one root).  The per-root lists are concatenated in root order and put
+ * in canonical order by the same sort (step 3).  TPs are built by the same
+ * construction (step 4) over contiguous ranges of the PP list, one range
+ * per thread, concatenated in order, then sorted and deduplicated.  The
+ * arithmetic is the serial oracle's; only the order of the work changes.
+ */
+typedef struct {
+    int n;
+    const int32_t *rp, *col;
+    int want_paths;
+    atomic_int next;
+    orc_result **per_root;
+} root_job;
+
+static void *root_worker(void *arg) {
+    root_job *j = (root_job *)arg;
+    for (;;) {
+        int r = atomic_fetch_add(&j->next, 1);
+        if (r >= j->n) break;
+        j->per_root[r] = orc_prime_paths_range(j->n, j->rp, j->col, j->want_paths, 0, r, r + 1);
+    }
+    return NULL;
+}
+
+typedef struct {
+    const orc_result *r;
+    int entry, exitv;
+    int64_t i0, i1;
+    seqlist out;
+    int rc;
+} tp_job;
+
+static void *tp_worker(void *arg) {
+    tp_job *j = (tp_job *)arg;
+    j->rc = sl_init(&j->out);
+    if (j->rc == ORC_OK)
+        j->rc = tp_build_range(j->r, j->r->bfs_dist, j->r->bfs_pred, j->entry, j->exitv, j->i0, j->i1, &j->out);
+    return NULL;
+}
+
+/* run fn(arg_t) on nthreads jobs: threads 1.. on new threads, job 0 here */
+static void run_jobs(void *(*fn)(void *), void *jobs, size_t stride, int njobs) {
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)(njobs > 0 ? njobs : 1));
+    int *ok = (int *)calloc((size_t)(njobs > 0 ? njobs : 1), sizeof(int));
+    for (int t = 1; t < njobs; t++)
+        ok[t] = th && ok && pthread_create(&th[t], NULL, fn, (char *)jobs + stride * (size_t)t) == 0;
+    fn(jobs);
+    for (int t = 1; t < njobs; t++) {
+        if (ok && ok[t]) pthread_join(th[t], NULL);
+        else fn((char *)jobs + stride * (size_t)t);  /* no thread: run it here */
+    }
+    free(th); free(ok);
+}
+
+orc_result *orc_run_parallel(int n, const int32_t *row_ptr, const int32_t *col, int entry,
+                             int exitv, int want_paths, int want_tp, int nthreads) {
+    if (want_tp) want_paths = 1;
+    if (n < 1) return orc_prime_paths_range(n, row_ptr, col, want_paths, 0, 0, 0);
+    if (nthreads < 1) nthreads = 1;
+    orc_result *out = (orc_result *)calloc(1, sizeof(orc_result));
+    orc_result **parts = (orc_result **)calloc((size_t)n, sizeof(orc_result *));
+    if (!out || !parts) { free(out); free(parts); return NULL; }
+    out->n = n;
+    root_job job;
+    job.n = n; job.rp = row_ptr; job.col = col; job.want_paths = want_paths;
+    atomic_init(&job.next, 0);
+    job.per_root = parts;
+    root_job *jobs = &job;
+    /* every thread shares the one job (the counter hands out the roots) */
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    int started = 0;
+    for (int t = 1; th && t < nthreads; t++)
+        if (pthread_create(&th[started], NULL, root_worker, jobs) == 0) started++;
+    root_worker(jobs);
+    for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
+    free(th);
+    /* merge in root order */
+    out->len_counts = (int64_t *)calloc((size_t)n + 3, sizeof(int64_t));
+    out->pp_len_counts = (int64_t *)calloc((size_t)n + 3, sizeof(int64_t));
+    out->root_paths = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    out->root_pp_ints = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    out->root_pps = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    if (!out->len_counts || !out->pp_len_counts || !out->root_paths || !out->root_pp_ints ||
+        !out->root_pps || sl_init(&out->pp))
+        out->err = ORC_ENOMEM;
+    for (int r = 0; r < n; r++) {
+        orc_result *q = parts[r];
+        if (!out->err) {
+            if (!q) out->err = ORC_ENOMEM;
+            else if (q->err) out->err = q->err;
+        }
+        if (!out->err) {
+            out->n_simple += q->n_simple;
+            for (int k = 0; k < n + 3; k++) {
+                out->len_counts[k] += q->len_counts[k];
+                out->pp_len_counts[k] += q->pp_len_counts[k];
+            }
+            out->root_paths[r] = q->root_paths[r];
+            out->root_pp_ints[r] = q->root_pp_ints[r];
+            out->root_pps[r] = q->root_pps[r];
+            for (int64_t i = 0; i < q->pp.n && !out->err; i++)
+                if (sl_push(&out->pp, q->pp.v + q->pp.off[i], (int)(q->pp.off[i + 1] - q->pp.off[i]), -1))
+                    out->err = ORC_ENOMEM;
+        }
+        orc_free(q);
+    }
+    free(parts);
+    if (!out->err && want_paths) out->err = sort_unique(&out->pp, 0);
+    if (out->err || !want_tp) return out;
+    /* TPs over PP ranges */
+    if (entry < 0 || entry >= n || exitv < 0 || exitv >= n) { out->err = ORC_EINVAL; return out; }
+    out->bfs_dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * (size_t)n);
+    out->bfs_pred = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * (size_t)n);
+    if (!out->bfs_dist || !out->bfs_pred ||
+        orc_bfs_tables(n, row_ptr, col, out->bfs_dist, out->bfs_pred) || sl_init(&out->tp)) {
+        out->err = ORC_ENOMEM;
+        return out;
+    }
+    tp_job *tj = (tp_job *)calloc((size_t)nthreads, sizeof(tp_job));
+    if (!tj) { out->err = ORC_ENOMEM; return out; }
+    int64_t P = out->pp.n;
+    for (int t = 0; t < nthreads; t++) {
+        tj[t].r = out; tj[t].entry = entry; tj[t].exitv = exitv;
+        tj[t].i0 = P * t / nthreads; tj[t].i1 = P * (t + 1) / nthreads;
+    }
+    run_jobs(tp_worker, tj, sizeof(tp_job), nthreads);
+    for (int t = 0; t < nthreads; t++) {
+        if (!out->err && tj[t].rc) out->err = tj[t].rc;
+        for (int64_t i = 0; i < tj[t].out.n && !out->err; i++)
+            if (sl_push(&out->tp, tj[t].out.v + tj[t].out.off[i],
+                        (int)(tj[t].out.off[i + 1] - tj[t].out.off[i]), -1))
+                out->err = ORC_ENOMEM;
+        sl_free(&tj[t].out);
+    }
+    free(tj);
+    if (!out->err) out->err = sort_unique(&out->tp, 1);
+    return out;
 }
 
 /* accessors for the ctypes wrapper */

@@ -378,3 +378,30 @@ def test_splitmix64_reference_values():
     assert r.next_u64() == 0xE220A8397B1DCDAF
     assert r.next_u64() == 0x6E789E6AA1B965F4
     assert r.next_u64() == 0x06C45D188009454F
+
+
+# ---------------------------------------------------------------------------
+# the root-parallel driver (all-core CPU baseline) gives the serial result
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("make", [G.config1_cfg, G.config3_cfg, lambda: G.diamond_chain(9),
+                                  lambda: fig1_cfg()[0], lambda: G.random_cfg(G.BATCH_SEED0 + 7)],
+                         ids=["config1", "config3", "chain9", "fig1", "random"])
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_parallel_driver_equals_serial(make, threads):
+    cfg = make()
+    a = oracle.run_cfg(cfg, test_paths=True)
+    b = oracle.run_cfg_parallel(cfg, test_paths=True, threads=threads)
+    for f in ("len_counts", "pp_len_counts", "root_paths", "root_pp_ints", "root_pps",
+              "pp_offsets", "pp_vertices", "tp_offsets", "tp_vertices"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+    assert a.n_simple == b.n_simple
+
+
+def test_parallel_driver_counts_only_and_digraphs():
+    for seed in range(5):
+        cfg = G.random_digraph(7, 0.35, 300 + seed, self_loops=True)
+        a = oracle.run(cfg.n, cfg.row_ptr, cfg.col)
+        b = oracle.run_parallel(cfg.n, cfg.row_ptr, cfg.col, threads=4)
+        assert a.pp_list() == b.pp_list()
+        c = oracle.run_parallel(cfg.n, cfg.row_ptr, cfg.col, want_paths=False, threads=4)
+        np.testing.assert_array_equal(a.root_pps, c.root_pps)
