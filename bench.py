@@ -188,7 +188,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
-    from paper_2210_16998_gb300 import tpg
+    from paper_2210_16998_gb300 import cfggen, tpg
 
     torch.cuda.set_device(local_rank)
     tpg.load_library(build=True)
@@ -248,17 +248,23 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = ms / args.steps
     value = world * total_pp / (ms / 1000.0)
 
-    # e2e through the C ABI with host buffers (H2D of the CSR, D2H of both results)
-    e2e_steps = 0 if args.no_e2e else max(3, args.steps // 4)
+    # e2e through the C ABI with host buffers (H2D of the CSR, D2H of both
+    # results), with a per-call breakdown
+    e2e_steps = 0 if args.no_e2e else args.steps
     bi = int(cfg.row_ptr.nbytes + cfg.col.nbytes)
-    bo = 0
 
     def e2e_step():
+        t0 = time.perf_counter()
         h = tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=tpg.TPG_RESULT_HOST)
         if shape:
             tpg.set_tile(h, shape)
+        t1 = time.perf_counter()
         pp = tpg.tpg_prime_paths(h)
+        t2 = time.perf_counter()
+        s1 = tpg.tpg_get_stats(h, as_dict=False)
         tp = tpg.tpg_test_paths(h)
+        t3 = time.perf_counter()
+        s2 = tpg.tpg_get_stats(h, as_dict=False)
         # bytes read back to the host: a TP list equal to the PP list shares
         # its host copy, so count every distinct buffer once
         bufs = {}
@@ -270,7 +276,13 @@ def run_ours(args, rank, world, local_rank):
         pp.free()
         tp.free()
         h.close()
-        return P, nbytes
+        t4 = time.perf_counter()
+        ph = {"load": 1e3 * (t1 - t0), "prime_paths_call": 1e3 * (t2 - t1), "test_paths_call": 1e3 * (t3 - t2),
+              "free": 1e3 * (t4 - t3), "enumerate": s1.t_enumerate_ms, "order_materialise": s1.t_order_ms,
+              "test_paths_device": s2.t_test_paths_ms,
+              "d2h": s1.t_result_copy_ms + s2.t_result_copy_ms,
+              "d2h_bytes": s1.result_copy_bytes + s2.result_copy_bytes}
+        return P, nbytes, ph
 
     if e2e_steps:
         e2e_step()  # warm the pinned pool
@@ -278,16 +290,33 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    e2e_pp = 0
+    e2e_pp, phases, bo = 0, [], 0
     for _ in range(e2e_steps):
-        P, bo = e2e_step()
+        P, bo, ph = e2e_step()
         e2e_pp += P
+        phases.append(ph)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     te = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * e2e_pp / float(te.item()) if e2e_steps else None
+    e2e_break = None
+    if phases:
+        e2e_break = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
+        e2e_break["step_ms"] = 1e3 * e2e_s / e2e_steps
+        d2h = e2e_break["d2h"]
+        e2e_break["d2h_gb_per_s"] = e2e_break["d2h_bytes"] / (d2h / 1e3) / 1e9 if d2h > 0 else None
+        e2e_break["host_other"] = e2e_break["step_ms"] - (e2e_break["enumerate"] + e2e_break["order_materialise"]
+                                                          + e2e_break["test_paths_device"] + d2h)
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra["config1"] = config_record(tpg, cfggen.config1_cfg(), "structured CFG, 24 vertices (4 if-else, "
+                                         "2 while, nesting <= 3, seed 1)", steps=max(args.steps, 20))
+        extra["config3"] = config_record(tpg, cfggen.config3_cfg(), "structured CFG, 120 vertices (10 while "
+                                         "nested <= 4, 3 switch x6, if-else), cyclic", steps=max(args.steps // 2, 5))
+        extra["batch4096"] = batch_record(tpg, cfggen, steps=max(args.steps // 2, 5))
 
     if rank != 0:
         return None
@@ -300,11 +329,10 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded diamond-chain CFG)",
-        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                               "tile": [stats[-1]["tile_block"], stats[-1]["tile_items"],
-                                        shape[2] if shape and len(shape) > 2 else 1]}),
+        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "tile": [stats[-1]["tile_block"], stats[-1]["tile_items"], shape[2] if shape and len(shape) > 2 else 1],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": int(bo),
-                "steps": e2e_steps},
+                "steps": e2e_steps, "phases_ms": e2e_break},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "enumerate_kernel", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -314,9 +342,129 @@ def run_ours(args, rank, world, local_rank):
                       "test_paths": statistics.mean(s["t_test_paths_ms"] for s in stats)},
         "clocks": clocks,
     }
+    line.update(extra)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_budget)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cfg, budget_s=args.cpu_budget / 2)
     return line
+
+
+def config_record(tpg, cfg, what, steps):
+    """One graph with device-resident inputs: load + PPs + TPs per step (CUDA
+    events over `steps` steps after warm-up), with the enumeration's volumes."""
+    import torch
+
+    rp = torch.as_tensor(cfg.row_ptr, device="cuda")
+    col = torch.as_tensor(cfg.col, device="cuda")
+
+    def one():
+        h = tpg.tpg_load_cfg_device(cfg.n, cfg.m, rp, col, cfg.entry, cfg.exit)
+        pp = tpg.tpg_prime_paths(h)
+        tp = tpg.tpg_test_paths(h)
+        st = tpg.tpg_get_stats(h, as_dict=False)
+        out = (pp.num_paths, tp.num_paths, st)
+        pp.free()
+        tp.free()
+        h.close()
+        return out
+
+    for _ in range(3):
+        one()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    sts = []
+    for _ in range(steps):
+        P, T, st = one()
+        sts.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    st = tpg.stats_dict(sts[-1])
+    rec_bytes = 8 + 2 + 4 * st["bitset_words"]  # {first, last}, count word, bitset per frontier path
+    return {"workload": what, "vertices": cfg.n, "arcs": cfg.m, "prime_paths": P, "test_paths": T,
+            "ms_per_step": ms, "pp_per_s": P / (ms / 1e3), "steps": steps,
+            "step": "load+validate+BFS tables, PPs, TPs (inputs resident)",
+            "simple_paths": st["simple_paths"], "levels": st["levels"],
+            "peak_level_paths": st["peak_level_nodes"],
+            "peak_frontier_bytes": st["peak_level_nodes"] * rec_bytes,
+            "arena_bytes_used": st["arena_bytes_used"], "arena_bytes_alloc": st["arena_bytes_alloc"],
+            "frontier_bytes_alloc": st["frontier_bytes_alloc"],
+            "device_ms": {"enumerate": statistics.median(s.t_enumerate_ms for s in sts),
+                          "order_materialise": statistics.median(s.t_order_ms for s in sts),
+                          "test_paths": statistics.median(s.t_test_paths_ms for s in sts)}}
+
+
+def batch_record(tpg, cfggen, steps, tile=(1024, 1, 1)):
+    """The 4096-graph batch: host-driven batched calls and graph-mode replays
+    on one handle (inputs and BFS tables resident; fixed tile shape)."""
+    import torch
+
+    cfgs = cfggen.batch_cfgs(4096)
+    ns, rp, col, ent, ext = cfggen.concat_batch(cfgs)
+    h = tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE)
+    tpg.set_tile(h, tile)
+    host_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pp = tpg.tpg_prime_paths(h)
+        tp = tpg.tpg_test_paths(h)
+        torch.cuda.synchronize()
+        host_ms.append(1e3 * (time.perf_counter() - t0))
+        P, T = pp.num_paths, tp.num_paths
+        pp.free()
+        tp.free()
+    st = tpg.tpg_get_stats(h)
+    tpg.tpg_graph_capture(h)
+    for _ in range(3):
+        a, b = tpg.tpg_graph_launch(h)
+        a.free()
+        b.free()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        a, b = tpg.tpg_graph_launch(h)
+        a.free()
+        b.free()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    rep_ms = ev0.elapsed_time(ev1) / steps
+    fb = tpg.tpg_get_stats(h)["graph_fallbacks"]
+    h.close()
+    return {"workload": "batch of 4096 seeded structured CFGs (n log-uniform 10-150, loop nesting 0-4, switch "
+                        "fan-out 2-6)", "graphs": len(cfgs), "vertices": int(ns.sum()), "prime_paths": P,
+            "test_paths": T, "simple_paths": st["simple_paths"], "tile": list(tile),
+            "graph_replay_ms": rep_ms, "graph_replay_pp_per_s": P / (rep_ms / 1e3), "replays": steps,
+            "graph_fallbacks": fb,
+            "host_driven_ms": min(host_ms), "host_driven_pp_per_s": P / (min(host_ms) / 1e3),
+            "host_driven_device_ms": {"enumerate": st["t_enumerate_ms"], "order_materialise": st["t_order_ms"],
+                                      "test_paths": st["t_test_paths_ms"]}}
+
+
+def cpu_baseline_all_cores(cfg, budget_s=6.0, min_runs=2):
+    """The oracle's root-parallel driver on every host core: PPs + TPs of the
+    same graph (the same enumeration per root; TPs built over PP ranges)."""
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    times, P = [], 0
+    t_start = time.perf_counter()
+    while len(times) < min_runs or time.perf_counter() - t_start < budget_s:
+        t0 = time.perf_counter()
+        r = oracle.run_cfg_parallel(cfg, test_paths=True, threads=threads)
+        times.append(time.perf_counter() - t0)
+        P = r.num_pp
+        if len(times) >= 50:
+            break
+    return {"value": P / statistics.mean(times), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"full workload (PPs + TPs of the k=22 diamond chain), {len(times)} runs, "
+                      f"mean {statistics.mean(times):.3f} s, root-parallel C -O2 on {threads} threads",
+            "host": host_cpu()}
 
 
 def cpu_baseline(cfg, budget_s=12.0, min_runs=2):
@@ -689,6 +837,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="chain: skip the structured-CFG and 4096-graph sub-records")
     ap.add_argument("--k", type=int, default=K_DIAMONDS, help="diamonds in the chain (22 = the benchmark workload)")
     ap.add_argument("--workload", choices=["chain", "batch", "sizer"], default="chain")
     ap.add_argument("--train-graphs", type=int, default=50000, help="sizer: training graphs")

@@ -109,6 +109,9 @@ typedef struct tpg_stats {
     int32_t graph_fallbacks;    /* of them, replays whose capacities were too small */
     int32_t graph_flags;        /* status word of the last replay (0 = complete) */
     int32_t graph_enum_error;   /* frontier-launch error word of the last replay */
+    float t_result_copy_ms;     /* device time of the device-to-host copies of the last host result
+                                   (0 when it shared an earlier copy or lives on the device) */
+    int64_t result_copy_bytes;  /* bytes those copies moved */
 } tpg_stats;
 
 /*

@@ -385,7 +385,7 @@ struct tpg_cfg {
     bool pp_valid = false;
 
     tpg_stats stats{};
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};  // [8], [9]: host-result copies
     long long last_tv0 = 0;  // TP vertices before dedup in the last tpg_test_paths
 
     // graph mode: the whole hot path captured in one CUDA graph
@@ -498,7 +498,7 @@ void destroy_cfg(tpg_cfg *g) {
     for (auto &b : g->pp_segs) release(g, b);
     cudaStreamSynchronize(g->stream);
     handle_pool().put_small(g->h_small);
-    handle_pool().put_events(g->device, g->ev, 8);
+    handle_pool().put_events(g->device, g->ev, 10);
     pinned().put(g->h_lvl_stage);
     g->magic = MAGIC_DEAD;
     delete g;
@@ -533,7 +533,7 @@ int new_cfg(void *stream, tpg_cfg **out) {
     g->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&g->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess ||
-        !(g->h_small = (int *)handle_pool().get_small()) || !handle_pool().get_events(g->device, g->ev, 8)) {
+        !(g->h_small = (int *)handle_pool().get_small()) || !handle_pool().get_events(g->device, g->ev, 10)) {
         cudaGetLastError();
         handle_pool().put_small(g->h_small);
         delete g;
@@ -953,11 +953,15 @@ int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, l
         r->pub.graph_path_ptr = (const int64_t *)gptr->p;
         r->pub.offsets = (const int64_t *)off->p;
         r->pub.vertices = (const int32_t *)vert->p;
+        g->stats.t_result_copy_ms = 0.f;
+        g->stats.result_copy_bytes = 0;
     } else {
         const size_t sz[3] = {sizeof(long long) * (g->G + 1), sizeof(long long) * (P + 1),
                               sizeof(int) * (size_t)std::max<long long>(V, 1)};
         Block *b[3] = {gptr, off, vert};
         bool copied = false;
+        size_t copy_bytes = 0;
+        cudaEventRecord(g->ev[8], g->stream);
         for (int i = 0; i < 3; ++i) {
             HostCopy *m = b[i]->mirror;
             if (m && m->bytes >= sz[i]) {
@@ -979,17 +983,25 @@ int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, l
             }
             r->host[i] = h;
             copied = true;
+            copy_bytes += sz[i];
             if (!m) {
                 h->refs.fetch_add(1);  // the block keeps it for later results
                 b[i]->mirror = h;
             }
         }
+        cudaEventRecord(g->ev[9], g->stream);
         if (copied && cudaStreamSynchronize(g->stream) != cudaSuccess) {
             cudaGetLastError();
             for (int j = 0; j < 3; ++j) host_copy_unref(r->host[j]);
             delete r;
             return TPG_ECUDA;
         }
+        g->stats.t_result_copy_ms = 0.f;
+        if (copied && cudaEventElapsedTime(&g->stats.t_result_copy_ms, g->ev[8], g->ev[9]) != cudaSuccess) {
+            cudaGetLastError();
+            g->stats.t_result_copy_ms = -1.f;
+        }
+        g->stats.result_copy_bytes = (int64_t)copy_bytes;
         r->pub.graph_path_ptr = (const int64_t *)r->host[0]->p;
         r->pub.offsets = (const int64_t *)r->host[1]->p;
         r->pub.vertices = (const int32_t *)r->host[2]->p;

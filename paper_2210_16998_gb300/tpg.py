@@ -83,6 +83,8 @@ class _Stats(ctypes.Structure):
         ("graph_fallbacks", ctypes.c_int32),
         ("graph_flags", ctypes.c_int32),
         ("graph_enum_error", ctypes.c_int32),
+        ("t_result_copy_ms", ctypes.c_float),
+        ("result_copy_bytes", ctypes.c_int64),
     ]
 
 
