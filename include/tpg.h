@@ -354,6 +354,21 @@ int tpg_sizer_load(tpg_sizer *z, const char *path);
 int tpg_get_stats(const tpg_cfg *g, tpg_stats *out);
 
 /*
+ * Per-level trace of the frontier launch (a profiling aid; the paper has no
+ * counterpart).  With tracing on, each tpg_prime_paths call records for
+ * every level k of the enumeration (paths of k vertices) four int64 values,
+ * out[4k .. 4k+3]: the level's start (the earliest block to start it) and
+ * the end of its last warp, in nanoseconds from the first level's start;
+ * the summed busy time of the warps that had work in the level; and the
+ * number of those warps.  tpg_get_level_trace copies up to max_levels
+ * levels of the last call's trace and sets *levels_out to the number of
+ * levels recorded (values -1 where a level recorded nothing).  Tracing adds
+ * a few atomics per warp and level; results never depend on it.
+ */
+int tpg_set_level_trace(tpg_cfg *g, int32_t on);
+int tpg_get_level_trace(const tpg_cfg *g, int64_t *out, int32_t max_levels, int32_t *levels_out);
+
+/*
  * tpg_prime_paths_noalloc -- prime paths of one small graph, allocating
  * nothing.  (The paper has no counterpart; this is a convenience of the
  * library.)

@@ -364,6 +364,7 @@ struct tpg_cfg {
 
     DevBuf rp, col, prp, pcol, vgraph, vbase, entry, exitv, tbl_base, dist, pred;
     DevBuf pre_len, suf_len, pre_off, suf_off, pre_seq, suf_seq;
+    DevBuf smask, pmask;  // successor / predecessor bitsets (bitsets of <= MASK_MAX_W words)
     GraphDev gd{};
 
     // enumeration workspace
@@ -405,6 +406,9 @@ struct tpg_cfg {
     } gp;
     long long out_cap[4] = {0, 0, 0, 0};  // explicit output capacities P, V, TV0, TV (0 = last run)
     unsigned long long *root_counts = nullptr;  // set while a counting run is in progress
+    bool trace_on = false;  // record a per-level trace of the frontier launches
+    DevBuf trace;
+    std::vector<long long> h_trace;  // the last call's trace, LEVEL_TRACE_WORDS per level
     std::vector<LevelRec> h_levels;
     int *h_small = nullptr;  // pinned staging for small read-backs (16 KB, see HandlePool)
     void *h_lvl_stage = nullptr;  // pinned staging for level tables too large for h_small
@@ -488,11 +492,13 @@ void destroy_cfg(tpg_cfg *g) {
     }
     DevBuf *all[] = {&g->rp, &g->col, &g->prp, &g->pcol, &g->vgraph, &g->vbase, &g->entry, &g->exitv,
                      &g->tbl_base, &g->dist, &g->pred, &g->pre_len, &g->suf_len, &g->pre_off, &g->suf_off,
+                     &g->smask, &g->pmask,
                      &g->pre_seq, &g->suf_seq, &g->tfl[0], &g->tfl[1], &g->tvis[0], &g->tvis[1], &g->tcnt[0], &g->tcnt[1],
                      &g->levels, &g->agg, &g->ctl, &g->s_keys[0], &g->s_keys[1],
                      &g->s_refs[0], &g->s_refs[1], &g->s_len, &g->s_tmp, &g->s_i32[0], &g->s_i32[1],
                      &g->s_i32[2], &g->s_i64[0], &g->s_i64[1], &g->s_i64[2], &g->s_i64[3], &g->rank_cnt,
-                     &g->rank_pre[0], &g->rank_pre[1], &g->rank_noff, &g->rank_bsum, &g->pp_ends, &g->tp_key_off, &g->tp_key};
+                     &g->rank_pre[0], &g->rank_pre[1], &g->rank_noff, &g->rank_bsum, &g->pp_ends, &g->tp_key_off, &g->tp_key,
+                     &g->trace};
     for (DevBuf *b : all) release(g, *b);
     for (auto &b : g->node_segs) release(g, b);
     for (auto &b : g->pp_segs) release(g, b);
@@ -564,6 +570,11 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h, bool valida
     RC(ensure(g, g->suf_len, sizeof(int) * g->N));
     RC(ensure(g, g->pre_off, sizeof(long long) * (g->N + 1)));
     RC(ensure(g, g->suf_off, sizeof(long long) * (g->N + 1)));
+    const bool masks = g->W <= MASK_MAX_W;
+    if (masks) {
+        RC(ensure(g, g->smask, sizeof(unsigned) * (size_t)g->N * g->W));
+        RC(ensure(g, g->pmask, sizeof(unsigned) * (size_t)g->N * g->W));
+    }
     if (small) {
         const long long bound = (long long)g->N * (g->N + 1) / 2;
         RC(ensure(g, g->pre_seq, sizeof(int) * bound));
@@ -599,13 +610,16 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h, bool valida
     d.suf_len = g->suf_len.as<int>();
     d.pre_off = g->pre_off.as<long long>();
     d.suf_off = g->suf_off.as<long long>();
+    d.smask = masks ? g->smask.as<unsigned>() : nullptr;
+    d.pmask = masks ? g->pmask.as<unsigned>() : nullptr;
 
     if (small) {
         d.pre_seq = g->pre_seq.as<int>();
         d.suf_seq = g->suf_seq.as<int>();
         if (!validate) CK(cudaMemsetAsync(g->ctl.p, 0, sizeof(int), s));
         CK(preprocess_small(d, g->prp.as<int>(), g->pcol.as<int>(), g->tbl_base.as<long long>(), validate, entry,
-                            exit, g->ctl.as<int>(), s));
+                            exit, g->ctl.as<int>(), s, masks ? g->smask.as<unsigned>() : nullptr,
+                            masks ? g->pmask.as<unsigned>() : nullptr));
         if (!validate) return TPG_OK;  // launch errors surfaced above; the next call's read-back sees the rest
         CK(cudaMemcpyAsync(g->h_small, g->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -620,6 +634,7 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h, bool valida
 
     CK(build_pred_csr(d, g->prp.as<int>(), g->pcol.as<int>(), g->s_i32[0].as<int>(), g->s_tmp.as<long long>(),
                       g->s_i64[0].as<long long>(), s));
+    if (masks) CK(build_vertex_masks(d, g->smask.as<unsigned>(), g->pmask.as<unsigned>(), nullptr, s));
     CK(bfs_all_pairs(d, s, nullptr, g->max_arcs));
     CK(tour_lengths(d, g->s_tmp.as<long long>(), s));
     long long *h = (long long *)g->h_small;
@@ -746,6 +761,13 @@ int enumerate_levels(tpg_cfg *g) {
         a.bar = (unsigned *)(g->ctl.as<char>() + CTL_BAR_OFFSET);
         a.root_counts = g->root_counts;
         a.spin_ns = g->spin_ns;
+        a.trace = nullptr;
+        if (g->trace_on) {
+            const size_t tb = sizeof(unsigned long long) * LEVEL_TRACE_WORDS * g->max_levels;
+            RC(ensure(g, g->trace, tb));
+            if (launch == 1) CK(cudaMemsetAsync(g->trace.p, 0, tb, s));
+            a.trace = g->trace.as<unsigned long long>();
+        }
         int grid = 0;
         CK(cudaEventRecord(g->ev[0], s));
         CK(launch_enumerate(a, g->shape, g->num_sms, s, &grid));
@@ -767,6 +789,10 @@ int enumerate_levels(tpg_cfg *g) {
         g->stats.t_enumerate_ms = total_ms;
         g->stats.attempts = launch;
         const int err = g->h_small[0];
+        if (g->trace_on) {
+            g->h_trace.assign((size_t)LEVEL_TRACE_WORDS * g->max_levels, 0);
+            CK(cudaMemcpy(g->h_trace.data(), g->trace.p, sizeof(long long) * g->h_trace.size(), cudaMemcpyDeviceToHost));
+        }
         if (err & ERR_TIMEOUT) return TPG_ETIMEOUT;
         if (err & ERR_INVAL) return TPG_ECUDA;  // a chunk's output disagreed with its count
         if (err & (ERR_OVF_COUNT | ERR_OVF_LEVELS)) return TPG_ETOOBIG;
@@ -2123,6 +2149,33 @@ int tpg_set_result_location(tpg_cfg *g, int32_t location) {
     if (!is_cfg(g)) return TPG_EHANDLE;
     if (location != TPG_RESULT_HOST && location != TPG_RESULT_DEVICE) return TPG_EINVAL;
     g->location = location;
+    return TPG_OK;
+}
+
+int tpg_set_level_trace(tpg_cfg *g, int32_t on) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    g->trace_on = on != 0;
+    g->h_trace.clear();
+    return TPG_OK;
+}
+
+int tpg_get_level_trace(const tpg_cfg *g, int64_t *out, int32_t max_levels, int32_t *levels_out) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (!out || max_levels < 0 || !levels_out) return TPG_EINVAL;
+    const int L = std::min<int>(max_levels, (int)(g->h_trace.size() / LEVEL_TRACE_WORDS));
+    int used = 0;
+    long long t0 = 0;
+    for (int k = 0; k < L; ++k) {
+        const long long *r = g->h_trace.data() + (size_t)LEVEL_TRACE_WORDS * k;
+        const long long start = r[0] ? (long long)~(unsigned long long)r[0] : 0;
+        if (r[0] && !t0) t0 = start;
+        out[4 * k + 0] = r[0] ? start - t0 : -1;
+        out[4 * k + 1] = r[1] ? r[1] - t0 : -1;
+        out[4 * k + 2] = r[2];
+        out[4 * k + 3] = r[3];
+        if (r[0]) used = k + 1;
+    }
+    *levels_out = used;
     return TPG_OK;
 }
 

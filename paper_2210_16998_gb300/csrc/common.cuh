@@ -57,7 +57,11 @@ struct GraphDev {
     int *pre_len, *suf_len;     // [N] vertex counts of path(entry->v), path(v->exit), 0 = none
     long long *pre_off, *suf_off;  // [N+1]
     int *pre_seq, *suf_seq;     // local ids
+    // successor and predecessor sets of every vertex as W-word bitsets of
+    // graph-local ids ([N][W]; built when W <= MASK_MAX_W, else null)
+    const unsigned *smask, *pmask;
 };
+constexpr int MASK_MAX_W = 8;
 
 // ---------------------------------------------------------------------------
 // memory-model helpers (PTX ISA: ld/st .relaxed.gpu, %globaltimer)

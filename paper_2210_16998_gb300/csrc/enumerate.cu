@@ -109,6 +109,44 @@ __device__ __forceinline__ unsigned eval_path(const GraphDev &g, int k, int firs
     return CNT_PP;
 }
 
+// With the vertex bitsets (bitsets of at most MASK_MAX_W words): the
+// successors of `last` that extend the path as a W-word bitset of local ids
+// (the successors not on the path, plus the first vertex when the arc to it
+// closes a cycle).  Ascending bit order is ascending successor id.
+template <int W>
+__device__ __forceinline__ void ext_mask(const GraphDev &g, int first, int last, int vb, const unsigned (&vis)[W],
+                                         unsigned (&m)[W]) {
+    const unsigned *sm = g.smask + (long long)last * W;
+    const int fb = first - vb;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const unsigned sj = __ldg(sm + j);
+        m[j] = (sj & ~vis[j]) | ((j == (fb >> 5)) ? (sj & (1u << (fb & 31))) : 0u);
+    }
+}
+
+// eval_path with the vertex bitsets, for a path whose visited set is `vis`
+// (last vertex included): the count word holds the number of extending
+// successors (CNT_WIDE form); with none, the path is prime iff every
+// predecessor of its first vertex is on it (the last vertex is never one
+// here: an arc last -> first would be an extension).
+template <int W>
+__device__ __forceinline__ unsigned eval_mask(const GraphDev &g, int k, int first, int last, int vb,
+                                              const unsigned (&vis)[W]) {
+    if (k >= 2 && first == last) return CNT_PP;
+    unsigned m[W];
+    ext_mask<W>(g, first, last, vb, vis, m);
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) c += __popc(m[j]);
+    if (c) return CNT_WIDE | c;
+    const unsigned *pm = g.pmask + (long long)first * W;
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+        if (__ldg(pm + j) & ~vis[j]) return 0u;
+    return CNT_PP;
+}
+
 // position of the (r+1)-th set bit of m (r = 0: the lowest); m has more than r set bits
 __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
     for (; r > 0; --r) m &= m - 1;
@@ -116,6 +154,13 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 }
 
 constexpr int CPG = ENUM_CPG;  // chunks per block: a level is cut into CPG * blocks chunks
+
+#ifndef TPG_ENUM_MASK
+#define TPG_ENUM_MASK 1  // evaluate paths with the vertex bitsets where they exist
+#endif
+#ifndef TPG_ENUM_LANEWISE
+#define TPG_ENUM_LANEWISE 1  // lane-wise child writing when it needs no more rounds than dealing
+#endif
 
 // paths per chunk of a level of `count` paths cut into nchk chunks:
 // ceil(count / nchk) rounded up to a multiple of 32
@@ -149,25 +194,17 @@ __device__ __forceinline__ void add_counts(const AggSlots &A, int s, int own, un
 }
 
 // Add (c, p) to chunk `own` of slot s (and to its group).  Lanes with nothing
-// to add pass own = -1.  One set of atomics per warp when all lanes share one
-// owner (the usual case), per lane otherwise.
-__device__ __forceinline__ void flush_counts(const AggSlots &A, int s, int own, unsigned long long c,
-                                             unsigned long long p) {
+// to add pass own = -1.  Lanes are grouped by owner and each group's leader
+// adds the group's sums, so a warp issues one set of atomics per distinct
+// owner (usually one).
+__device__ __forceinline__ void flush_counts(const AggSlots &A, int s, int own, unsigned c, unsigned p) {
     const bool mine = own >= 0 && (c | p);
-    const unsigned have = __ballot_sync(0xffffffffu, mine);
-    if (!have) return;
-    const int own0 = __shfl_sync(0xffffffffu, own, __ffs(have) - 1);
-    if (__all_sync(0xffffffffu, !mine || own == own0)) {
-        if (!mine) c = p = 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            p += __shfl_xor_sync(0xffffffffu, p, o);
-        }
-        if ((threadIdx.x & 31) == 0) add_counts(A, s, own0, c, p);
-    } else if (mine) {
-        add_counts(A, s, own, c, p);
-    }
+    if (!__any_sync(0xffffffffu, mine)) return;
+    const unsigned peers = __match_any_sync(0xffffffffu, mine ? own : -1);
+    // (32-bit sums: one chunk holds < 2^31 / NC + 32 paths of < 2^13 children each)
+    const unsigned sc = __reduce_add_sync(peers, mine ? c : 0u);
+    const unsigned sp = __reduce_add_sync(peers, mine ? p : 0u);
+    if (mine && (threadIdx.x & 31) == __ffs(peers) - 1) add_counts(A, s, own, sc, sp);
 }
 
 // One persistent cooperative launch walks the levels.  Level k is cut into
@@ -197,16 +234,21 @@ template <int W, int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_kernel(EnumArgs a) {
     constexpr int NW = BLOCK / 32;
     constexpr int F = CPG / NW;      // chunks per warp in the counting pass
+    constexpr bool MASK = TPG_ENUM_MASK && W <= MASK_MAX_W;  // successor / predecessor bitsets in g.smask, g.pmask
     constexpr int WT = 32 * ITEMS;  // paths per warp tile
     static_assert(CPG % NW == 0, "a block's warps split its chunks evenly");
     static_assert(CPG % 32 == 0 && CPG <= BLOCK, "lanes split a group's entries; threads clear them");
     extern __shared__ long long s_gpre[];  // [2 * G]: exclusive group prefixes (children, PPs)
     __shared__ long long s_wsum[NW][2];
     __shared__ long long s_tot[2];
+    __shared__ unsigned long long s_t0[NW];  // trace: start of each warp's work in the level
+    __shared__ unsigned long long s_tr[3];   // trace: the block's latest end, summed busy time, busy warps
+    __shared__ int s_next;                   // next of the block's units to claim in this level
     const GraphDev &g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int G = gridDim.x, b = blockIdx.x, NC = CPG * G;
     const unsigned lt_mask = (1u << lane) - 1u;
+    if (tid < 3) s_tr[tid] = 0ull;  // (read after the first level's __syncthreads)
     const AggSlots A{a.agg, NC, G};
 
     // ---- counting pass over the first level of this launch ----
@@ -233,7 +275,9 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
 #pragma unroll
                 for (int w = 0; w < W; ++w) vis[w] = __ldcg(in_vis + w * a.lvl_cap + i);
                 const int vb = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + fl.x)) : 0;
-                const unsigned cw = eval_path<W>(g, k, fl.x, fl.y, vb, vis, -1);
+                unsigned cw;
+                if constexpr (MASK) cw = eval_mask<W>(g, k, fl.x, fl.y, vb, vis);
+                else cw = eval_path<W>(g, k, fl.x, fl.y, vb, vis, -1);
                 cnt[i] = (unsigned short)cw;
                 c_sum += cnt_children(cw);
                 p_sum += cw >> 15;
@@ -310,11 +354,13 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                 s_tot[0] = tc;
                 s_tot[1] = tp;
                 A.gc(s2)[b] = A.gp(s2)[b] = 0;
+                s_next = NW;  // the block's units 0 .. NW-1 go to its warps in order
             }
             if (tid < CPG) A.cc(s2)[b * CPG + tid] = A.cp(s2)[b * CPG + tid] = 0;
             __syncthreads();
         }
         const long long C = s_tot[0], P = s_tot[1];
+        if (a.trace && tid == 0) atomicMax(a.trace + LEVEL_TRACE_WORDS * k, ~global_ns());
 
         // every block takes the same decision from the same counts
         int e = 0;
@@ -368,23 +414,30 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
             }
         };
         // Work units: part s of chunk c (SPLIT parts of sub paths) is unit
-        // c * SPLIT + s.  Warp wid of block b takes units wid * G + b, then
-        // + GW each time: the warps of one block (one SM's share of the issue
-        // slots) sample the whole level, so a costly region is spread over
-        // all SMs, and each warp averages over 2 * SPLIT units.  A part's
-        // offsets are its chunk's plus the children and PPs of the chunk's
-        // earlier parts, summed from their count words.
+        // c * SPLIT + s.  Block b owns units b, b + G, b + 2G, ...: every
+        // block (one SM's share of the issue slots) samples the whole level,
+        // so a costly region is spread over all SMs.  Its warps take its
+        // first NW units in order and then claim the rest one at a time from
+        // a shared-memory counter (claimed one unit ahead), so within the SM
+        // a warp whose units were cheap takes more of them.  A part's offsets
+        // are its chunk's plus the children and PPs of the chunk's earlier
+        // parts, summed from their count words, whichever warp takes it.
         const int SPLIT = a.split < 1 ? 1 : (a.split > 4 ? 4 : a.split);
-        const int GW = G * NW, gw = wid * G + b;
         const int nunit = nchk * SPLIT;
         const int sub = ((chunk + SPLIT - 1) / SPLIT + 31) & ~31;
         long long ec, ep;
-        load_entries(gw / SPLIT, ec, ep);
-        for (int u = gw; u < nunit; u += GW) {
+        int u = b + G * wid;
+        load_entries(u / SPLIT, ec, ep);
+        if (a.trace && lane == 0) s_t0[wid] = u < nunit ? global_ns() : 0ull;
+        while (u < nunit) {
             const int c = u / SPLIT, part = u - c * SPLIT;
-            // the next unit's chunk entries load while this unit is processed
+            // the next unit is claimed, and its chunk entries load, while
+            // this unit is processed
+            int i_next = 0;
+            if (lane == 0) i_next = atomicAdd(&s_next, 1);
+            const int u_next = b + G * __shfl_sync(0xffffffffu, i_next, 0);
             long long ec_next, ep_next;
-            load_entries((u + GW) / SPLIT, ec_next, ep_next);
+            load_entries(u_next / SPLIT, ec_next, ep_next);
             // offsets of chunk c: its group's prefix plus the chunks before it
             // in the group; its own entry is checked when its last part is done
             const int grp = c / CPG;
@@ -463,69 +516,31 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                             if (c2) atomicAdd(rc + 2, (unsigned long long)c2);
                         }
                     }
-                    // The item's children are dealt to lanes in output order:
-                    // child q of the warp (0 <= q < tot, at position pos_c + q)
-                    // goes to lane q % 32, which finds its parent lane (the last
-                    // lane whose first child is at or before q) and reads the
-                    // parent's path through shuffles.  A parent with many
-                    // children thus costs the warp one round per 32 children,
-                    // and the child records are stored contiguously.
                     const int excl = x - nch;
                     int vb_l = 0, e0_l = 0;
                     if (nch > 0) {
                         vb_l = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + first[j])) : 0;
-                        e0_l = __ldg(g.rp + last[j]);
+                        if constexpr (!MASK) e0_l = __ldg(g.rp + last[j]);
                     }
-                    for (int q0 = 0; q0 < tot; q0 += 32) {
-                        const int q = q0 + lane;
-                        int p = 0;
-#pragma unroll
-                        for (int step = 16; step > 0; step >>= 1) {
-                            const int cand = p + step;  // <= 31
-                            if (__shfl_sync(0xffffffffu, excl, cand) <= q) p = cand;
-                        }
-                        const int pf = __shfl_sync(0xffffffffu, first[j], p);
-                        const int pl = __shfl_sync(0xffffffffu, last[j], p);
-                        const int pvb = __shfl_sync(0xffffffffu, vb_l, p);
-                        const int pe0 = __shfl_sync(0xffffffffu, e0_l, p);
-                        const unsigned pcw = __shfl_sync(0xffffffffu, cw[j], p);
-                        const int rank = q - __shfl_sync(0xffffffffu, excl, p);
-                        unsigned pvis[W];
-#pragma unroll
-                        for (int ww = 0; ww < W; ++ww) pvis[ww] = __shfl_sync(0xffffffffu, vis[j][ww], p);
-                        if (q >= tot) continue;
-                        const int pi = t0 + j * 32 + p;
-                        // the rank-th successor of the parent's last vertex that extends it
-                        int w;
-                        if (!(pcw & CNT_WIDE)) {
-                            // (clamped: a wrong count word must not index past the arcs)
-                            const unsigned ci = (unsigned)(pe0 + nth_set_bit(pcw & CNT_BITS, rank));
-                            w = __ldg(g.col + min(ci, (unsigned)(g.M - 1)));
-                        } else {
-                            const int pe1 = __ldg(g.rp + pl + 1);
-                            int left = rank, e = pe0;
-                            for (; e < pe1; ++e) {
-                                const int v = __ldg(g.col + e);
-                                if (v == pf || !test_bit<W>(pvis, v - pvb)) {
-                                    if (left == 0) break;
-                                    --left;
-                                }
-                            }
-                            w = __ldg(g.col + (e < pe1 ? e : pe1 - 1));
-                        }
-                        const int cpos = pos_c + q;
+                    // one child record: arena node, frontier record with the
+                    // child's own count word (evaluated here), bitset, and its
+                    // share of the next level's chunk counts
+                    auto emit = [&](int w, int cpos, int pf, int pvb, const unsigned (&pvis)[W], int pi) {
                         const bool closes = (w == pf);
-                        const unsigned c2w = eval_path<W>(g, k + 1, pf, w, pvb, pvis, w);
+                        const int bb = w - pvb;
+                        unsigned cvis[W];  // the child's visited set
+#pragma unroll
+                        for (int ww = 0; ww < W; ++ww) cvis[ww] = pvis[ww] | ((ww == (bb >> 5)) ? (1u << (bb & 31)) : 0u);
+                        unsigned c2w;
+                        if constexpr (MASK) c2w = eval_mask<W>(g, k + 1, pf, w, pvb, cvis);
+                        else c2w = eval_path<W>(g, k + 1, pf, w, pvb, pvis, w);
                         if (cpos < C) {  // holds when the counts agree; C fits the segment and the frontier
                             next[cpos] = make_int2(w, pi);
                             out_fl[cpos] = make_int2(pf, w);
                             out_cnt[cpos] = (unsigned short)c2w;
                             if (!closes) {
-                                const int bb = w - pvb;
 #pragma unroll
-                                for (int ww = 0; ww < W; ++ww)
-                                    out_vis[ww * a.lvl_cap + cpos] =
-                                        pvis[ww] | ((ww == (bb >> 5)) ? (1u << (bb & 31)) : 0u);
+                                for (int ww = 0; ww < W; ++ww) out_vis[ww * a.lvl_cap + cpos] = cvis[ww];
                             }
                             if ((unsigned)cpos >= bound) {
                                 // the child belongs to a later chunk: the
@@ -540,6 +555,118 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                             }
                             acc_c += (unsigned)cnt_children(c2w);
                             acc_p += c2w >> 15;
+                        }
+                    };
+                    // Two ways to write the item's children.  Lane-wise: each
+                    // lane writes its own path's children, one per round, for
+                    // as many rounds as the busiest lane has children (no
+                    // shuffles; chosen when that is at most about as many
+                    // rounds as dealing needs).  Dealt: child q of the warp
+                    // (0 <= q < tot, at position pos_c + q) goes to lane q % 32,
+                    // which finds its parent lane (the last lane whose first
+                    // child is at or before q) and reads the parent's path
+                    // through shuffles, so a parent with many children costs
+                    // the warp one round per 32 children and the child records
+                    // are stored contiguously.
+                    const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)nch);
+                    // with the vertex bitsets, the extending successors as a
+                    // bitset (none when the count word says so: a closed cycle)
+                    unsigned xm[MASK ? W : 1];
+                    if constexpr (MASK) {
+                        if (nch > 0) {
+                            ext_mask<W>(g, first[j], last[j], vb_l, vis[j], xm);
+                        } else {
+#pragma unroll
+                            for (int ww = 0; ww < W; ++ww) xm[ww] = 0u;
+                        }
+                    }
+                    const bool lanewise = TPG_ENUM_LANEWISE &&
+                                          (TPG_ENUM_LANEWISE == 1 ? 3 * maxc <= 4 * ((tot + 31) >> 5)
+                                                                  : maxc <= ((tot + 31) >> 5)) &&
+                                          (MASK || !__any_sync(0xffffffffu, (cw[j] & CNT_WIDE) != 0u));
+                    if (lanewise) {
+                        const int pi = t0 + j * 32 + lane;
+                        if constexpr (MASK) {
+                            for (int r = 0; r < maxc; ++r) {
+                                // the next extending successor, ascending
+                                int w = -1;
+#pragma unroll
+                                for (int ww = 0; ww < W; ++ww)
+                                    if (w < 0 && xm[ww]) {
+                                        w = vb_l + 32 * ww + __ffs(xm[ww]) - 1;
+                                        xm[ww] &= xm[ww] - 1;
+                                    }
+                                if (w >= 0) emit(w, pos_c + excl + r, first[j], vb_l, vis[j], pi);
+                            }
+                        } else {
+                            unsigned m = cw[j] & CNT_BITS;
+                            for (int r = 0; r < maxc; ++r) {
+                                if (m) {
+                                    const int sidx = __ffs(m) - 1;
+                                    m &= m - 1;
+                                    // (clamped: a wrong count word must not index past the arcs)
+                                    const int w = __ldg(g.col + min((unsigned)(e0_l + sidx), (unsigned)(g.M - 1)));
+                                    emit(w, pos_c + excl + r, first[j], vb_l, vis[j], pi);
+                                }
+                            }
+                        }
+                    } else {
+                        for (int q0 = 0; q0 < tot; q0 += 32) {
+                            const int q = q0 + lane;
+                            int p = 0;
+#pragma unroll
+                            for (int step = 16; step > 0; step >>= 1) {
+                                const int cand = p + step;  // <= 31
+                                if (__shfl_sync(0xffffffffu, excl, cand) <= q) p = cand;
+                            }
+                            const int pf = __shfl_sync(0xffffffffu, first[j], p);
+                            const int pvb = __shfl_sync(0xffffffffu, vb_l, p);
+                            const int rank = q - __shfl_sync(0xffffffffu, excl, p);
+                            unsigned pvis[W];
+#pragma unroll
+                            for (int ww = 0; ww < W; ++ww) pvis[ww] = __shfl_sync(0xffffffffu, vis[j][ww], p);
+                            const int pi = t0 + j * 32 + p;
+                            if constexpr (MASK) {
+                                unsigned pm[W];
+#pragma unroll
+                                for (int ww = 0; ww < W; ++ww) pm[ww] = __shfl_sync(0xffffffffu, xm[ww], p);
+                                if (q >= tot) continue;
+                                // the rank-th extending successor of the parent
+                                int w = -1, rr = rank;
+#pragma unroll
+                                for (int ww = 0; ww < W; ++ww) {
+                                    const int c = __popc(pm[ww]);
+                                    if (w < 0) {
+                                        if (rr < c) w = pvb + 32 * ww + nth_set_bit(pm[ww], rr);
+                                        else rr -= c;
+                                    }
+                                }
+                                if (w >= 0) emit(w, pos_c + q, pf, pvb, pvis, pi);
+                                continue;
+                            }
+                            const int pl = __shfl_sync(0xffffffffu, last[j], p);
+                            const int pe0 = __shfl_sync(0xffffffffu, e0_l, p);
+                            const unsigned pcw = __shfl_sync(0xffffffffu, cw[j], p);
+                            if (q >= tot) continue;
+                            // the rank-th successor of the parent's last vertex that extends it
+                            int w;
+                            if (!(pcw & CNT_WIDE)) {
+                                // (clamped: a wrong count word must not index past the arcs)
+                                const unsigned ci = (unsigned)(pe0 + nth_set_bit(pcw & CNT_BITS, rank));
+                                w = __ldg(g.col + min(ci, (unsigned)(g.M - 1)));
+                            } else {
+                                const int pe1 = __ldg(g.rp + pl + 1);
+                                int left = rank, e = pe0;
+                                for (; e < pe1; ++e) {
+                                    const int v = __ldg(g.col + e);
+                                    if (v == pf || !test_bit<W>(pvis, v - pvb)) {
+                                        if (left == 0) break;
+                                        --left;
+                                    }
+                                }
+                                w = __ldg(g.col + (e < pe1 ? e : pe1 - 1));
+                            }
+                            emit(w, pos_c + q, pf, pvb, pvis, pi);
                         }
                     }
                     if (pp) {
@@ -556,10 +683,30 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
             }
             // the chunk must have produced exactly what its count promised
             if (last_part && lane == 0 && (pos_c - pa != own_c || pos_p - pb != own_p)) atomicOr(a.err, ERR_INVAL);
+            u = u_next;
             ec = ec_next;
             ep = ep_next;
         }
         flush_counts(A, s1, cur_own, acc_c, acc_p);
+        if (a.trace) {
+            // per block first (shared memory), then one set of atomics per block
+            if (lane == 0 && s_t0[wid]) {
+                const unsigned long long t_w1 = global_ns();
+                atomicMax(&s_tr[0], t_w1);
+                atomicAdd(&s_tr[1], t_w1 - s_t0[wid]);
+                atomicAdd(&s_tr[2], 1ull);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long *tr = a.trace + LEVEL_TRACE_WORDS * k;
+                if (s_tr[2]) {
+                    atomicMax(tr + 1, s_tr[0]);
+                    atomicAdd(tr + 2, s_tr[1]);
+                    atomicAdd(tr + 3, s_tr[2]);
+                }
+                s_tr[0] = s_tr[1] = s_tr[2] = 0ull;
+            }
+        }
         if (C == 0) break;  // nothing follows; the end of the launch orders the writes
         if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT | ERR_INVAL, a.spin_ns)) break;
         count = C;

@@ -16,7 +16,10 @@ inline void note_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_
 // ENUM_CPG chunks per block; 3 rotating slots of {children, PPs} per chunk
 // and per block.  ENUM_AGG_WORDS int64 values hold them for grids of up to
 // 2048 blocks.
-constexpr int ENUM_CPG = 32;
+#ifndef TPG_ENUM_CPG
+#define TPG_ENUM_CPG 64
+#endif
+constexpr int ENUM_CPG = TPG_ENUM_CPG;
 constexpr long long enum_agg_words(long long grid) { return 3 * (2 * ENUM_CPG * grid + 2 * grid) + 4; }
 constexpr long long ENUM_AGG_WORDS = enum_agg_words(2048);
 // frontier count word of a path: bits 0-12 are the mask of the successors of
@@ -64,7 +67,12 @@ struct EnumArgs {
     unsigned *bar;           // tree grid barrier, BAR_WORDS words (zeroed)
     unsigned long long *root_counts;  // optional [3*N]: per first vertex, simple paths, PPs, PP vertices
     unsigned long long spin_ns;       // limit of every grid-barrier wait (SPIN_LIMIT_NS unless set)
+    unsigned long long *trace;        // optional [LEVEL_TRACE_WORDS * max_levels] per-level timing
 };
+// per-level trace of a frontier launch, 4 words per level: ~(earliest block
+// start), latest warp end, summed busy time of the warps with work, number
+// of those warps (globaltimer nanoseconds; zeroed before the launch)
+constexpr int LEVEL_TRACE_WORDS = 4;
 
 // enumerate.cu
 struct EnumShape {
@@ -248,7 +256,10 @@ cudaError_t bfs_all_pairs(const GraphDev &g, cudaStream_t s, const int *gate, lo
 // launches; g.pre_seq / g.suf_seq must hold N(N+1)/2 entries each.
 constexpr int PREP_SMALL_N = 1024;
 cudaError_t preprocess_small(const GraphDev &g, int *prp, int *pcol, long long *tbl_base, bool validate, int entry,
-                             int exit, int *err, cudaStream_t s);
+                             int exit, int *err, cudaStream_t s, unsigned *smask = nullptr, unsigned *pmask = nullptr);
+// successor / predecessor bitsets of every vertex (GraphDev::smask, pmask),
+// W <= MASK_MAX_W; nothing is done while *gate is nonzero (gate optional)
+cudaError_t build_vertex_masks(const GraphDev &g, unsigned *smask, unsigned *pmask, const int *gate, cudaStream_t s);
 cudaError_t tour_lengths(const GraphDev &g, long long *scan_tmp, cudaStream_t s);
 cudaError_t tour_fill(const GraphDev &g, cudaStream_t s);
 

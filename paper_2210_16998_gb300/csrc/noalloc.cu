@@ -33,11 +33,15 @@ constexpr int NA_W = 4;
 constexpr EnumShape NA_SHAPE = {256, 1};  // tile of 256 paths
 constexpr int NA_TILE = 256;
 constexpr int NA_MAX_LEVELS = NA_MAXN + 4;
+// per-chunk level counts for the frontier launch of up to 8 blocks of 256
+// threads on each of up to 160 SMs (a GB300 has 152); a larger grid is
+// refused by the launch (TPG_ECUDA)
+constexpr long long NA_AGG_WORDS = enum_agg_words(8 * 160);
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NaLayout {
-    size_t prp, pcol, indeg, scanbuf, scantmp, vbase, levels, ctl, nodes, tfl0, tfl1, tvis0, tvis1, tcnt0, tcnt1, pprefs,
+    size_t prp, pcol, indeg, scanbuf, scantmp, vbase, smask, pmask, levels, ctl, nodes, tfl0, tfl1, tvis0, tvis1, tcnt0, tcnt1, pprefs,
         agg, keys0, keys1, refs0, refs1, len, ltmp, total;
 };
 
@@ -50,6 +54,8 @@ constexpr NaLayout na_layout() {
     L.scanbuf = o; o = align256(o + sizeof(long long) * (NA_MAXN + 2));
     L.scantmp = o; o = align256(o + sizeof(long long) * 64);
     L.vbase = o;   o = align256(o + sizeof(int) * 2);
+    L.smask = o;   o = align256(o + sizeof(unsigned) * NA_MAXN * NA_W);
+    L.pmask = o;   o = align256(o + sizeof(unsigned) * NA_MAXN * NA_W);
     L.levels = o;  o = align256(o + sizeof(LevelRec) * NA_MAX_LEVELS);
     L.ctl = o;     o = align256(o + CTL_BYTES);
     L.nodes = o;   o = align256(o + sizeof(int2) * NA_NODE_CAP);
@@ -60,7 +66,7 @@ constexpr NaLayout na_layout() {
     L.tcnt0 = o;   o = align256(o + sizeof(unsigned short) * NA_LVL_CAP);
     L.tcnt1 = o;   o = align256(o + sizeof(unsigned short) * NA_LVL_CAP);
     L.pprefs = o;  o = align256(o + sizeof(int) * NA_PP_CAP);
-    L.agg = o;     o = align256(o + sizeof(long long) * ENUM_AGG_WORDS);
+    L.agg = o;     o = align256(o + sizeof(long long) * NA_AGG_WORDS);
     L.keys0 = o;   o = align256(o + sizeof(int) * NA_PP_CAP);
     L.keys1 = o;   o = align256(o + sizeof(int) * NA_PP_CAP);
     L.refs0 = o;   o = align256(o + sizeof(long long) * NA_PP_CAP);
@@ -73,7 +79,7 @@ constexpr NaLayout na_layout() {
 
 constexpr NaLayout NA = na_layout();
 constexpr size_t NA_SCRATCH_BYTES = NA.total;
-static_assert(NA_SCRATCH_BYTES < (36u << 20), "no-allocation scratch stays under 36 MB");
+static_assert(NA_SCRATCH_BYTES < (40u << 20), "no-allocation scratch stays under 40 MB");
 
 // the scratch array shared by every call on a device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_SCRATCH_BYTES];
@@ -182,6 +188,10 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     d.vbase = (const int *)(S + NA.vbase);
     NA_CK(build_pred_csr(d, (int *)(S + NA.prp), (int *)(S + NA.pcol), (int *)(S + NA.indeg),
                          (long long *)(S + NA.scantmp), (long long *)(S + NA.scanbuf), s));
+    static_assert(NA_W <= MASK_MAX_W, "the vertex bitsets cover every supported bitset width");
+    d.smask = (const unsigned *)(S + NA.smask);
+    d.pmask = (const unsigned *)(S + NA.pmask);
+    NA_CK(build_vertex_masks(d, (unsigned *)(S + NA.smask), (unsigned *)(S + NA.pmask), nullptr, s));
 
     // 3. the frontier kernel over the scratch arena
     EnumArgs a{};
@@ -204,7 +214,7 @@ extern "C" int tpg_prime_paths_noalloc(int32_t n, int32_t m, const int32_t *row_
     a.seed_level1 = 1;
     a.split = 1;
     a.agg = (long long *)(S + NA.agg);
-    a.agg_cap = ENUM_AGG_WORDS;
+    a.agg_cap = NA_AGG_WORDS;
     a.err = err;
     a.stop_level = err + 1;
     a.bar = (unsigned *)(S + NA.ctl + CTL_BAR_OFFSET);

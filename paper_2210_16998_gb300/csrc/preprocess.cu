@@ -327,16 +327,53 @@ __global__ void __launch_bounds__(PREP_BLOCK) prep_small_kernel(GraphDev g, int 
     }
 }
 
+// Successor and predecessor bitsets of vertex v (graph-local bit ids, W
+// words each).  Ids outside the graph's W words are skipped, so a CSR that
+// failed validation cannot make it write elsewhere (it is never run on one).
+__device__ __forceinline__ void vertex_masks(const GraphDev &g, int v, unsigned *smask, unsigned *pmask) {
+    const int W = g.W;
+    const int vb = g.vgraph ? g.vbase[g.vgraph[v]] : 0;
+    for (int j = 0; j < W; ++j) {
+        unsigned sm = 0u, pm = 0u;
+        for (int e = g.rp[v]; e < g.rp[v + 1]; ++e) {
+            const int b = g.col[e] - vb;
+            if ((b >> 5) == j && b >= 0) sm |= 1u << (b & 31);
+        }
+        for (int e = g.prp[v]; e < g.prp[v + 1]; ++e) {
+            const int b = g.pcol[e] - vb;
+            if ((b >> 5) == j && b >= 0) pm |= 1u << (b & 31);
+        }
+        smask[(long long)v * W + j] = sm;
+        pmask[(long long)v * W + j] = pm;
+    }
+}
+
+__global__ void masks_kernel(GraphDev g, unsigned *smask, unsigned *pmask, const int *gate) {
+    if (gate && *gate) return;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N; v += (long long)gridDim.x * blockDim.x)
+        vertex_masks(g, (int)v, smask, pmask);
+}
+
+cudaError_t build_vertex_masks(const GraphDev &g, unsigned *smask, unsigned *pmask, const int *gate, cudaStream_t s) {
+    if (g.W > MASK_MAX_W) return cudaErrorInvalidValue;
+    masks_kernel<<<grid_for(g.N), 256, 0, s>>>(g, smask, pmask, gate);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // Tour lengths, their offsets and the tour sequences of one graph in one
 // block; pre_seq and suf_seq hold N(N+1)/2 entries each, an upper bound (the
 // i-th vertex in order of distance from the entry is at most i arcs away, so
 // its path has at most i + 1 vertices; the same toward the exit).  With
 // stage_pred the N x N predecessor table is first copied to dynamic shared
 // memory, so the path walks read shared memory.
-__global__ void __launch_bounds__(PREP_BLOCK) tour_small_kernel(GraphDev g, const int *gate, int stage_pred) {
+__global__ void __launch_bounds__(PREP_BLOCK) tour_small_kernel(GraphDev g, const int *gate, int stage_pred,
+                                                                unsigned *smask, unsigned *pmask) {
     extern __shared__ int pred_s[];
     if (*gate) return;
     const int N = g.N, tid = threadIdx.x;
+    if (smask)
+        for (int v = tid; v < N; v += PREP_BLOCK) vertex_masks(g, v, smask, pmask);
     if (stage_pred) {
         const long long nn = (long long)N * N;
         for (long long i = tid; i < nn; i += PREP_BLOCK) pred_s[i] = g.pred[i];
@@ -362,7 +399,7 @@ __global__ void __launch_bounds__(PREP_BLOCK) tour_small_kernel(GraphDev g, cons
 }
 
 cudaError_t preprocess_small(const GraphDev &g, int *prp, int *pcol, long long *tbl_base, bool validate, int entry,
-                             int exit, int *err, cudaStream_t s) {
+                             int exit, int *err, cudaStream_t s, unsigned *smask, unsigned *pmask) {
     if (g.G != 1 || g.N > PREP_SMALL_N) return cudaErrorInvalidValue;
     prep_small_kernel<<<1, PREP_BLOCK, sizeof(int) * (g.N + 1), s>>>(g, prp, pcol, tbl_base, validate ? 1 : 0,
                                                                      entry, exit, err);
@@ -377,7 +414,7 @@ cudaError_t preprocess_small(const GraphDev &g, int *prp, int *pcol, long long *
                                       (int)TOUR_STAGE_BYTES)) != cudaSuccess)
             return e;
     }
-    tour_small_kernel<<<1, PREP_BLOCK, stage ? pred_bytes : 0, s>>>(g, err, stage);
+    tour_small_kernel<<<1, PREP_BLOCK, stage ? pred_bytes : 0, s>>>(g, err, stage, smask, pmask);
     note_launch();
     return cudaGetLastError();
 }

@@ -136,6 +136,9 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_set_work_split.argtypes = [P, ctypes.c_int32]
         lib.tpg_set_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         lib.tpg_set_wait_limit.argtypes = [P, ctypes.c_int64]
+        lib.tpg_set_level_trace.argtypes = [P, ctypes.c_int32]
+        lib.tpg_get_level_trace.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32)]
         lib.tpg_set_output_capacity.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         lib.tpg_graph_capture.argtypes = [P]
         lib.tpg_root_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
@@ -449,6 +452,21 @@ def set_tile(cfg: Cfg, tile):
 def tpg_set_wait_limit(cfg: Cfg, ns: int):
     """Limit of each grid-barrier wait of the handle's frontier launches (ns < 0: default)."""
     _check(load_library().tpg_set_wait_limit(cfg.handle, int(ns)), "tpg_set_wait_limit")
+
+
+def tpg_set_level_trace(cfg: Cfg, on: bool = True):
+    """Record a per-level trace of the frontier launch on later tpg_prime_paths calls."""
+    _check(load_library().tpg_set_level_trace(cfg.handle, 1 if on else 0), "tpg_set_level_trace")
+
+
+def tpg_get_level_trace(cfg: Cfg, max_levels: int = 4200):
+    """The last call's trace: int64 [levels, 4] = (start ns, last warp end ns,
+    summed warp busy ns, warps with work) per level, level 1 in row 1."""
+    out = np.zeros((max_levels, 4), dtype=np.int64)
+    used = ctypes.c_int32(0)
+    _check(load_library().tpg_get_level_trace(cfg.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                              int(max_levels), ctypes.byref(used)), "tpg_get_level_trace")
+    return out[:used.value]
 
 
 def tpg_set_capacity(cfg: Cfg, nodes: int, level_nodes: int, prime_paths: int):

@@ -96,6 +96,9 @@ def test_null_handles(lib):
     assert lib.tpg_set_tile_shape(None, 512, 1) == tpg.TPG_EHANDLE
     assert lib.tpg_set_work_split(None, 2) == tpg.TPG_EHANDLE
     assert lib.tpg_set_wait_limit(None, 1000) == tpg.TPG_EHANDLE
+    assert lib.tpg_set_level_trace(None, 1) == tpg.TPG_EHANDLE
+    n = ctypes.c_int32(0)
+    assert lib.tpg_get_level_trace(None, (ctypes.c_int64 * 4)(), 1, ctypes.byref(n)) == tpg.TPG_EHANDLE
     lib.tpg_free(None)  # no-op
 
 
