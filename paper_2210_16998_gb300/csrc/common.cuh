@@ -172,6 +172,39 @@ __device__ __forceinline__ bool grid_barrier_tree(unsigned *bar, int *err, int s
     return s_ok != 0;
 }
 
+// Grid-wide barrier on one arrival counter that only grows: each block adds
+// 1 (a release reduction, no reply to wait for) and waits, polling with
+// acquire loads, until the counter reaches `target` (grid size times the
+// number of barriers so far in the launch; the counter is zero at launch).
+// The wait is bounded by `limit_ns` (ERR_TIMEOUT, false on expiry); false on
+// every block alike if an error flag in `stop` was raised before the barrier.
+__device__ __forceinline__ bool grid_barrier_count(unsigned *ctr, unsigned target, int *err, int stop,
+                                                   unsigned long long limit_ns = SPIN_LIMIT_NS) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+        if (ld_acquire_u32(ctr) < target) {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(ctr) < target) {
+                __nanosleep(32);
+                if (global_ns() - t0 > limit_ns) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (__ldcg(err) & stop) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // counts of one level saturate here (int32 path indices)
 constexpr unsigned long long MAX31 = (1ull << 31) - 1;
 

@@ -155,6 +155,9 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 
 constexpr int CPG = ENUM_CPG;  // chunks per block: a level is cut into CPG * blocks chunks
 
+#ifndef TPG_ENUM_TREE_BARRIER
+#define TPG_ENUM_TREE_BARRIER 0  // grid barrier: 0 = one growing counter, 1 = two-level tree
+#endif
 #ifndef TPG_ENUM_MASK
 #define TPG_ENUM_MASK 1  // evaluate paths with the vertex bitsets where they exist
 #endif
@@ -250,6 +253,13 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
     const unsigned lt_mask = (1u << lane) - 1u;
     if (tid < 3) s_tr[tid] = 0ull;  // (read after the first level's __syncthreads)
     const AggSlots A{a.agg, NC, G};
+    // the grid barrier between levels: one growing arrival counter, or the
+    // two-level tree (TPG_ENUM_TREE_BARRIER)
+    unsigned bar_target = 0;
+    auto enum_barrier = [&](unsigned target, int stop) -> bool {
+        if constexpr (TPG_ENUM_TREE_BARRIER) return grid_barrier_tree(a.bar, a.err, stop, a.spin_ns);
+        else return grid_barrier_count(a.bar, target, a.err, stop, a.spin_ns);
+    };
 
     // ---- counting pass over the first level of this launch ----
     {
@@ -313,7 +323,8 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
             A.gc((k + 1) % 3)[b] = A.gp((k + 1) % 3)[b] = 0;
             A.gc((k + 2) % 3)[b] = A.gp((k + 2) % 3)[b] = 0;
         }
-        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT, a.spin_ns)) return;
+        bar_target += G;
+        if (!enum_barrier(bar_target, ERR_TIMEOUT)) return;
     }
 
     // the level being processed; after the first, every block derives the
@@ -708,7 +719,8 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
             }
         }
         if (C == 0) break;  // nothing follows; the end of the launch orders the writes
-        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT | ERR_INVAL, a.spin_ns)) break;
+        bar_target += G;
+        if (!enum_barrier(bar_target, ERR_TIMEOUT | ERR_INVAL)) break;
         count = C;
         lnodes = next;
         lpp += P;

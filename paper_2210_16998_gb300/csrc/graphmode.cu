@@ -161,13 +161,14 @@ __global__ void __launch_bounds__(GMB) gm_pp_lengths(GmArgs a) {
 
 constexpr int GM_MAT_WARPS = 8;
 
+template <int CH, typename T>
 __global__ void __launch_bounds__(GM_MAT_WARPS * 32, 8) gm_materialize(GmArgs a) {
-    __shared__ unsigned short sbuf[GM_MAT_WARPS][MAT_BUF];
+    __shared__ T sbuf[GM_MAT_WARPS][MAT_BUF * CH];
     __shared__ int2 *s_nodes[MAT_MAX_LV];
     int2 *const *lv = cache_level_nodes(a.levels, a.max_levels, s_nodes);
     const long long P = gm_P(a);
-    materialize_warps<GM_MAT_WARPS>(a.refs[a.counts->pp_buf], nullptr, 0, P, a.pp_off, a.levels, a.g, a.pp_vert,
-                                    a.g.G > 1 ? a.pp_graph : nullptr, sbuf, lv);
+    materialize_warps<GM_MAT_WARPS, CH, T>(a.refs[a.counts->pp_buf], nullptr, 0, P, a.pp_off, a.levels, a.g,
+                                           a.pp_vert, a.g.G > 1 ? a.pp_graph : nullptr, sbuf, lv);
 }
 
 // graph_path_ptr from sorted graph ids (ids == nullptr: one graph)
@@ -428,7 +429,8 @@ cudaError_t gm_enqueue_pp(const GmArgs &a, cudaStream_t s) {
     note_launch();
     e = gm_scan<long long>(a.len, a.pp_off, &a.counts->P, a.P_cap, a.scan_tmp, nullptr, a.num_sms, s);
     if (e != cudaSuccess) return e;
-    gm_materialize<<<grid, GM_MAT_WARPS * 32, 0, s>>>(a);
+    if (a.g.maxn <= MAT_SMALL_N) gm_materialize<2, unsigned char><<<grid, GM_MAT_WARPS * 32, 0, s>>>(a);
+    else gm_materialize<1, unsigned short><<<grid, GM_MAT_WARPS * 32, 0, s>>>(a);
     gm_graph_ptr<<<grid, GMB, 0, s>>>(a.g.G > 1 ? a.pp_graph : nullptr, &a.counts->P, a.P_cap, a.g.G, a.pp_gptr,
                                       a.counts, GM_ENUM_FAILED | GM_OVF_PP | GM_OVF_PPV);
     note_launch(2);

@@ -134,26 +134,32 @@ cudaError_t pp_offsets_single_level(long long *off, long long n, int level, cuda
 
 constexpr int MAT_WARPS = 8;
 
+template <int CH, typename T>
 __global__ void __launch_bounds__(MAT_WARPS * 32, 8)
     pp_materialize_kernel(const long long *refs, const int *single_refs, int single_level, long long n,
                           const long long *offsets, const LevelRec *levels, int max_levels, GraphDev g,
                           int *out, int *out_graph, int2 *out_ends) {
-    __shared__ unsigned short buf[MAT_WARPS][MAT_BUF];
+    __shared__ T buf[MAT_WARPS][MAT_BUF * CH];
     __shared__ int2 *s_nodes[MAT_MAX_LV];
     int2 *const *lv = cache_level_nodes(levels, max_levels, s_nodes);
-    materialize_warps(refs, single_refs, single_level, n, offsets, levels, g, out, out_graph, buf, lv, out_ends);
+    materialize_warps<MAT_WARPS, CH, T>(refs, single_refs, single_level, n, offsets, levels, g, out, out_graph, buf,
+                                        lv, out_ends);
 }
 
 cudaError_t pp_materialize(const long long *refs, const int *single_refs, int single_level, long long n,
                            const long long *offsets, const LevelRec *levels, int max_levels, const GraphDev &g,
                            int *out_vertices, int *out_graph, cudaStream_t s, int2 *out_ends) {
     if (n <= 0) return cudaSuccess;
-    const long long warps = (n + 31) / 32;
+    const bool small = g.maxn <= MAT_SMALL_N;
+    const long long warps = (n + (small ? 63 : 31)) / (small ? 64 : 32);
     long long blocks = (warps + MAT_WARPS - 1) / MAT_WARPS;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    pp_materialize_kernel<<<(unsigned)blocks, MAT_WARPS * 32, 0, s>>>(refs, single_refs, single_level, n, offsets,
-                                                                     levels, max_levels, g, out_vertices, out_graph,
-                                                                     out_ends);
+    if (small)
+        pp_materialize_kernel<2, unsigned char><<<(unsigned)blocks, MAT_WARPS * 32, 0, s>>>(
+            refs, single_refs, single_level, n, offsets, levels, max_levels, g, out_vertices, out_graph, out_ends);
+    else
+        pp_materialize_kernel<1, unsigned short><<<(unsigned)blocks, MAT_WARPS * 32, 0, s>>>(
+            refs, single_refs, single_level, n, offsets, levels, max_levels, g, out_vertices, out_graph, out_ends);
     note_launch();
     return cudaGetLastError();
 }

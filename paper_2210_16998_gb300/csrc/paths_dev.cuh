@@ -31,20 +31,23 @@ __device__ __forceinline__ int key_cmp(long long a, long long b, const long long
     return key_cmp_same_graph(a, b, koff, key);
 }
 
-// Materialise PPs [0, n): one warp handles 32 consecutive PPs; each lane
-// walks its path's parent links from the last vertex back to the first,
-// writing into a per-warp shared-memory window that the warp then stores
-// contiguously (lanes store directly when the window does not fit).  The
-// window holds local ids as 16-bit values (a graph has at most TPG_MAX_N
-// vertices), so more warps fit an SM: the walk is latency-bound and the
-// number of walks in flight sets its speed.  A PP is
+// Materialise PPs [0, n): one warp handles 32 * CH consecutive PPs, CH per
+// lane (lane l takes PPs l, l + 32, ...); each lane walks its paths' parent
+// links from the last vertex back to the first, the CH walks interleaved so
+// that CH dependent loads are in flight per lane, writing into a per-warp
+// shared-memory window that the warp then stores contiguously (lanes store
+// directly when the window does not fit).  The window holds local ids as T
+// (8-bit for graphs of at most 256 vertices, else 16-bit: a graph has at most
+// TPG_MAX_N vertices), so more warps fit an SM: the walk is latency-bound and
+// the number of walks in flight sets its speed.  A PP is
 // refs[i] = (level << 32 | index in level), or, with refs == nullptr, index
 // single_refs[i] in level single_level.  out_graph (optional) receives the
 // graph id of each PP, out_ends (optional) its (first, last) local vertex.
 static_assert(TPG_MAX_N <= 65536, "local vertex ids fit 16 bits");
-constexpr int MAT_BUF = 1536;  // local vertex ids (uint16, < TPG_MAX_N) per warp: 32 PPs of up to 48 vertices
+constexpr int MAT_BUF = 1536;  // window entries per warp and per walk of a lane: 32 PPs of up to 48 vertices
 constexpr int MAT_MAX_LV = 256; // level-pointer table cached in shared memory up to this many levels
                                 // (2 KB: with a 24 KB window per 8 warps, 8 blocks fit an SM)
+constexpr int MAT_SMALL_N = 256;  // graphs up to this size use 8-bit windows and two walks per lane
 
 // Copy the levels' node pointers to shared memory (one dependent load per
 // parent-link step instead of two); returns nullptr when there are too many.
@@ -56,47 +59,68 @@ __device__ __forceinline__ int2 *const *cache_level_nodes(const LevelRec *levels
     return s_nodes;
 }
 
-template <int NWARPS>
+template <int NWARPS, int CH, typename T>
 __device__ __forceinline__ void materialize_warps(const long long *refs, const int *single_refs, int single_level,
                                                   long long n, const long long *offsets, const LevelRec *levels,
                                                   const GraphDev &g, int *out, int *out_graph,
-                                                  unsigned short (&buf)[NWARPS][MAT_BUF], int2 *const *lvl_nodes,
+                                                  T (&buf)[NWARPS][MAT_BUF * CH], int2 *const *lvl_nodes,
                                                   int2 *out_ends = nullptr) {
+    constexpr int TILE = 32 * CH;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long nwarps = (long long)gridDim.x * NWARPS;
-    for (long long w0 = (blockIdx.x * (long long)NWARPS + wid) * 32; w0 < n; w0 += nwarps * 32) {
-        const long long idx = w0 + lane;
-        const bool valid = idx < n;
-        int level = 0, rel = 0;
-        if (valid) {
-            if (refs) {
-                const long long r = refs[idx];
-                level = (int)(r >> 32);
-                rel = (int)(r & 0xffffffffll);
-            } else {
-                level = single_level;
-                rel = single_refs[idx];
+    for (long long w0 = (blockIdx.x * (long long)NWARPS + wid) * TILE; w0 < n; w0 += nwarps * TILE) {
+        int level[CH], node[CH], vb[CH], root[CH], first_loc[CH], last_loc[CH];
+        long long off[CH];
+        int jmax = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const long long idx = w0 + c * 32 + lane;
+            level[c] = 0;
+            node[c] = 0;
+            if (idx < n) {
+                if (refs) {
+                    const long long r = refs[idx];
+                    level[c] = (int)(r >> 32);
+                    node[c] = (int)(r & 0xffffffffll);
+                } else {
+                    level[c] = single_level;
+                    node[c] = single_refs[idx];
+                }
             }
+            off[c] = idx < n ? offsets[idx] : 0;
+            vb[c] = root[c] = first_loc[c] = last_loc[c] = 0;
+            jmax = level[c] > jmax ? level[c] : jmax;
         }
-        const long long w_end_idx = (w0 + 32 < n) ? w0 + 32 : n;
+        jmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)jmax);
+        const long long w_end_idx = (w0 + TILE < n) ? w0 + TILE : n;
         const long long start = offsets[w0];
         const long long span = offsets[w_end_idx] - start;
-        const long long off = valid ? offsets[idx] : 0;
-        const bool staged = span <= MAT_BUF;
-        int node = rel, root = 0, first_loc = 0, last_loc = 0;
-        for (int j = level; j >= 1; --j) {
-            const int2 rec = lvl_nodes ? lvl_nodes[j][node] : levels[j].nodes[node];
-            const int v = rec.x;
-            const int loc = g.vgraph ? v - g.vbase[g.vgraph[v]] : v;
-            if (staged) buf[wid][off - start + (j - 1)] = (unsigned short)loc;
-            else out[off + (j - 1)] = loc;
-            if (j == level) last_loc = loc;
-            first_loc = loc;
-            root = v;
-            node = rec.y;
+        const bool staged = span <= MAT_BUF * CH;
+        for (int j = jmax; j >= 1; --j) {
+            int2 rec[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (j <= level[c]) rec[c] = lvl_nodes ? lvl_nodes[j][node[c]] : levels[j].nodes[node[c]];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                if (j > level[c]) continue;
+                const int v = rec[c].x;
+                if (j == level[c] && g.vgraph) vb[c] = g.vbase[g.vgraph[v]];  // one graph per path
+                const int loc = v - vb[c];
+                if (staged) buf[wid][off[c] - start + (j - 1)] = (T)loc;
+                else out[off[c] + (j - 1)] = loc;
+                if (j == level[c]) last_loc[c] = loc;
+                first_loc[c] = loc;
+                root[c] = v;
+                node[c] = rec[c].y;
+            }
         }
-        if (valid && out_graph) out_graph[idx] = g.vgraph ? g.vgraph[root] : 0;
-        if (valid && out_ends) out_ends[idx] = make_int2(first_loc, last_loc);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const long long idx = w0 + c * 32 + lane;
+            if (idx < n && out_graph) out_graph[idx] = g.vgraph ? g.vgraph[root[c]] : 0;
+            if (idx < n && out_ends) out_ends[idx] = make_int2(first_loc[c], last_loc[c]);
+        }
         if (staged) {
             __syncwarp();
             for (long long t = lane; t < span; t += 32) out[start + t] = (int)buf[wid][t];
