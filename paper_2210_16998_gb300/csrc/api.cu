@@ -659,7 +659,7 @@ int preprocess(tpg_cfg *g, const std::vector<long long> &tbl_base_h, bool valida
 int alloc_fixed_workspace(tpg_cfg *g) {
     RC(ensure(g, g->levels, sizeof(LevelRec) * g->max_levels));
     RC(ensure(g, g->ctl, CTL_BYTES));
-    RC(ensure(g, g->agg, sizeof(long long) * ENUM_AGG_WORDS));
+    RC(ensure(g, g->agg, sizeof(long long) * enum_agg_words_max(g->num_sms)));
     return TPG_OK;
 }
 
@@ -755,7 +755,7 @@ int enumerate_levels(tpg_cfg *g) {
         a.seed_level1 = (launch == 1) ? 1 : 0;
         a.split = g->split;
         a.agg = g->agg.as<long long>();
-        a.agg_cap = ENUM_AGG_WORDS;
+        a.agg_cap = enum_agg_words_max(g->num_sms);
         a.err = g->ctl.as<int>();
         a.stop_level = g->ctl.as<int>() + 1;
         a.bar = (unsigned *)(g->ctl.as<char>() + CTL_BAR_OFFSET);
@@ -1339,7 +1339,7 @@ int capture_plan(tpg_cfg *g) {
     a.seed_level1 = 1;
     a.split = g->split;
     a.agg = g->agg.as<long long>();
-    a.agg_cap = ENUM_AGG_WORDS;
+    a.agg_cap = enum_agg_words_max(g->num_sms);
     a.err = g->ctl.as<int>();
     a.stop_level = g->ctl.as<int>() + 1;
     a.bar = (unsigned *)(g->ctl.as<char>() + CTL_BAR_OFFSET);

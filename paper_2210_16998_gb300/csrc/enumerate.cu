@@ -153,7 +153,6 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
     return __ffs(m) - 1;
 }
 
-constexpr int CPG = ENUM_CPG;  // chunks per block: a level is cut into CPG * blocks chunks
 
 #ifndef TPG_ENUM_TREE_BARRIER
 #define TPG_ENUM_TREE_BARRIER 0  // grid barrier: 0 = one growing counter, 1 = two-level tree
@@ -173,10 +172,12 @@ __device__ __forceinline__ int level_chunk(long long count, int nchk) {
 }
 
 // Per-chunk counts of one level.  Slot s holds, for every chunk and for every
-// group of CPG consecutive chunks, the children and the PPs it produces.
+// group of 2^lg consecutive chunks (one block's), the children and the PPs it
+// produces.
 struct AggSlots {
     long long *base;
     int NC, G;  // chunks, groups (= blocks)
+    int lg;     // log2 of the chunks per group
     __device__ long long *cc(int s) const { return base + s * (2ll * NC + 2ll * G); }
     __device__ long long *cp(int s) const { return cc(s) + NC; }
     __device__ long long *gc(int s) const { return cc(s) + 2ll * NC; }
@@ -188,11 +189,11 @@ __device__ __forceinline__ void add_counts(const AggSlots &A, int s, int own, un
     // (c, p) fit 32 bits for one lane; a warp sum is widened before it is added
     if (c) {
         atomicAdd((unsigned long long *)A.cc(s) + own, c);
-        atomicAdd((unsigned long long *)A.gc(s) + own / CPG, c);
+        atomicAdd((unsigned long long *)A.gc(s) + (own >> A.lg), c);
     }
     if (p) {
         atomicAdd((unsigned long long *)A.cp(s) + own, p);
-        atomicAdd((unsigned long long *)A.gp(s) + own / CPG, p);
+        atomicAdd((unsigned long long *)A.gp(s) + (own >> A.lg), p);
     }
 }
 
@@ -236,11 +237,14 @@ __device__ __forceinline__ void flush_counts(const AggSlots &A, int s, int own, 
 template <int W, int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_kernel(EnumArgs a) {
     constexpr int NW = BLOCK / 32;
+    constexpr int CPG = ENUM_UPW * NW;  // chunks per block: a level is cut into CPG * blocks chunks
+    constexpr int LG = CPG >= 256 ? 8 : CPG >= 128 ? 7 : CPG >= 64 ? 6 : 5;
     constexpr int F = CPG / NW;      // chunks per warp in the counting pass
     constexpr bool MASK = TPG_ENUM_MASK && W <= MASK_MAX_W;  // successor / predecessor bitsets in g.smask, g.pmask
     constexpr int WT = 32 * ITEMS;  // paths per warp tile
     static_assert(CPG % NW == 0, "a block's warps split its chunks evenly");
     static_assert(CPG % 32 == 0 && CPG <= BLOCK, "lanes split a group's entries; threads clear them");
+    static_assert(CPG == (1 << LG), "chunks per block: a power of two from 32 to 256");
     extern __shared__ long long s_gpre[];  // [2 * G]: exclusive group prefixes (children, PPs)
     __shared__ long long s_wsum[NW][2];
     __shared__ long long s_tot[2];
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
     const int G = gridDim.x, b = blockIdx.x, NC = CPG * G;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (tid < 3) s_tr[tid] = 0ull;  // (read after the first level's __syncthreads)
-    const AggSlots A{a.agg, NC, G};
+    const AggSlots A{a.agg, NC, G, LG};
     // the grid barrier between levels: one growing arrival counter, or the
     // two-level tree (TPG_ENUM_TREE_BARRIER)
     unsigned bar_target = 0;
@@ -763,7 +767,7 @@ static cudaError_t launch_wbi(const EnumArgs &args, int num_sms, cudaStream_t s,
     }
     const int grid = num_sms * blocks_per_sm;
     *grid_out = grid;
-    if (args.agg_cap < enum_agg_words(grid)) return cudaErrorInvalidValue;
+    if (args.agg_cap < enum_agg_words(grid, ENUM_UPW * (BLOCK / 32))) return cudaErrorInvalidValue;
     if (args.seed_level1) {
         if ((e = launch_seed_level1(args, s)) != cudaSuccess) return e;
     }

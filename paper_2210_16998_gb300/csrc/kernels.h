@@ -13,15 +13,19 @@ extern std::atomic<long long> g_kernel_launches;
 inline void note_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // per-chunk level counts of the frontier launch: a level is cut into
-// ENUM_CPG chunks per block; 3 rotating slots of {children, PPs} per chunk
-// and per block.  ENUM_AGG_WORDS int64 values hold them for grids of up to
-// 2048 blocks.
-#ifndef TPG_ENUM_CPG
-#define TPG_ENUM_CPG 64
+// ENUM_UPW chunks per warp of the launch (CPG = ENUM_UPW x warps per block
+// chunks per block); 3 rotating slots of {children, PPs} per chunk and per
+// block.  enum_agg_words(grid, CPG) int64 values hold them for one launch;
+// enum_agg_words_max(num_sms) for any tile shape on that GPU (at most 64
+// warps and 8 blocks per SM).
+#ifndef TPG_ENUM_UPW
+#define TPG_ENUM_UPW 4
 #endif
-constexpr int ENUM_CPG = TPG_ENUM_CPG;
-constexpr long long enum_agg_words(long long grid) { return 3 * (2 * ENUM_CPG * grid + 2 * grid) + 4; }
-constexpr long long ENUM_AGG_WORDS = enum_agg_words(2048);
+constexpr int ENUM_UPW = TPG_ENUM_UPW;
+constexpr long long enum_agg_words(long long grid, long long cpg) { return 3 * (2 * cpg * grid + 2 * grid) + 4; }
+constexpr long long enum_agg_words_max(long long num_sms) {
+    return 3 * (2 * ENUM_UPW * 64 * num_sms + 2 * 8 * num_sms) + 4;
+}
 // frontier count word of a path: bits 0-12 are the mask of the successors of
 // its last vertex that extend it (successor list position s -> bit s; lists
 // of at most CNT_MASK_DEG successors), or, with CNT_WIDE set, the number of
@@ -61,7 +65,7 @@ struct EnumArgs {
     int seed_level1;         // 1 on a fresh run: level 1 is written first (never on a resume)
     int split;               // work units per chunk in the per-warp levels (1..4; results never depend on it)
     long long *agg;          // per-block level counts (no initialisation needed)
-    long long agg_cap;       // int64 values in agg (enum_agg_words(grid) at least)
+    long long agg_cap;       // int64 values in agg (enum_agg_words(grid, chunks per block) at least)
     int *err;                // error flags (zeroed)
     int *stop_level;         // level whose next level did not fit (written with the flags)
     unsigned *bar;           // tree grid barrier, BAR_WORDS words (zeroed)

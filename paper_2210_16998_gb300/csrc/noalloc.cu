@@ -36,7 +36,7 @@ constexpr int NA_MAX_LEVELS = NA_MAXN + 4;
 // per-chunk level counts for the frontier launch of up to 8 blocks of 256
 // threads on each of up to 160 SMs (a GB300 has 152); a larger grid is
 // refused by the launch (TPG_ECUDA)
-constexpr long long NA_AGG_WORDS = enum_agg_words(8 * 160);
+constexpr long long NA_AGG_WORDS = enum_agg_words(8 * 160, ENUM_UPW * 8);
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -79,7 +79,7 @@ constexpr NaLayout na_layout() {
 
 constexpr NaLayout NA = na_layout();
 constexpr size_t NA_SCRATCH_BYTES = NA.total;
-static_assert(NA_SCRATCH_BYTES < (40u << 20), "no-allocation scratch stays under 40 MB");
+static_assert(NA_SCRATCH_BYTES < (36u << 20), "no-allocation scratch stays under 36 MB");
 
 // the scratch array shared by every call on a device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_SCRATCH_BYTES];
