@@ -311,6 +311,8 @@ def run_ours(args, rank, world, local_rank):
                                                           + e2e_break["test_paths_device"] + d2h)
 
     extra = {}
+    if args.level_trace and rank == 0:
+        extra["level_trace"] = level_trace(tpg, cfg, rp, col, shape)
     if not args.no_extra and rank == 0:
         extra["config1"] = config_record(tpg, cfggen.config1_cfg(), "structured CFG, 24 vertices (4 if-else, "
                                          "2 while, nesting <= 3, seed 1)", steps=max(args.steps, 20))
@@ -347,6 +349,30 @@ def run_ours(args, rank, world, local_rank):
         line["cpu_baseline"] = cpu_baseline(cfg, budget_s=args.cpu_budget)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cfg, budget_s=args.cpu_budget / 2)
     return line
+
+
+def level_trace(tpg, cfg, rp, col, shape):
+    """Per-level timing of one frontier launch (tpg_set_level_trace), after
+    two untraced calls: rows [level, duration us, last warp us, mean warp us,
+    warps with work]; the duration of a level runs to the next level's
+    start, so it includes the grid barrier and the prefix step."""
+    h = tpg.tpg_load_cfg_device(cfg.n, cfg.m, rp, col, cfg.entry, cfg.exit)
+    if shape:
+        tpg.set_tile(h, shape)
+    for _ in range(2):
+        tpg.tpg_prime_paths(h).free()
+    tpg.tpg_set_level_trace(h, True)
+    tpg.tpg_prime_paths(h).free()
+    tr = tpg.tpg_get_level_trace(h)
+    h.close()
+    rows = []
+    for k in range(1, len(tr)):
+        if tr[k, 0] < 0:
+            continue
+        nxt = tr[k + 1, 0] if k + 1 < len(tr) and tr[k + 1, 0] >= 0 else tr[k, 1]
+        rows.append([k, round((nxt - tr[k, 0]) / 1e3, 2), round((tr[k, 1] - tr[k, 0]) / 1e3, 2),
+                     round(tr[k, 2] / max(tr[k, 3], 1) / 1e3, 2), int(tr[k, 3])])
+    return rows
 
 
 def config_record(tpg, cfg, what, steps):
@@ -646,18 +672,6 @@ def run_batch(args, rank, world, local_rank):
     return line
 
 
-def lpt_groups(weights, k):
-    """Longest-processing-time packing: heaviest first, into the lightest group."""
-    order = np.argsort(-np.asarray(weights), kind="stable")
-    loads = np.zeros(k)
-    groups = [[] for _ in range(k)]
-    for i in order:
-        j = int(np.argmin(loads))
-        groups[j].append(int(i))
-        loads[j] += weights[i]
-    return [sorted(g) for g in groups], loads
-
-
 def run_sizer(args, rank, world, local_rank):
     import torch
 
@@ -722,13 +736,24 @@ def run_sizer(args, rank, world, local_rank):
             b.free()
         return P
 
-    # (c) graph mode pre-sized by the sizer, cold handle
-    def sized_graph(idx=None, margin=args.margin):
-        sub = held if idx is None else [held[i] for i in idx]
-        n_, r_, c_, e_, x_ = cfggen.concat_batch(sub)
+    # (c) host-driven calls pre-sized by the sizer, cold handle: the arena,
+    # frontier and PP list start at the predicted sizes (times the margin)
+    def sized_host(margin=args.margin):
+        with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE) as h:
+            tpg.set_tile(h, shape)
+            tpg.tpg_sizer_presize(z, h, margin)
+            a, b = tpg.tpg_prime_paths(h), tpg.tpg_test_paths(h)
+            st = tpg.tpg_get_stats(h)
+            P = a.num_paths
+            a.free()
+            b.free()
+        return P, st
+
+    # (d) graph mode pre-sized by the sizer, cold handle
+    def sized_graph(margin=args.margin):
         torch.cuda.synchronize()
         t_start = time.perf_counter()
-        with tpg.tpg_load_cfg_batch(n_, r_, c_, e_, x_, location=tpg.TPG_RESULT_DEVICE) as h:
+        with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE) as h:
             tpg.set_tile(h, shape)
             caps = tpg.tpg_sizer_presize(z, h, margin)
             tpg.tpg_graph_capture(h)
@@ -748,37 +773,30 @@ def run_sizer(args, rank, world, local_rank):
             b.free()
         return P, st, caps, rep, t_first
 
-    shape = (512, 2)
+    shape = (512, 1)
     plain_host()
     plain_graph()
+    sized_host()
     sized_graph()  # warm-up (allocator, module loading)
-    ta, (Pa, sta) = timed(plain_host)
+    ta, (Pa, sta) = min((timed(plain_host) for _ in range(3)), key=lambda r: r[0])
     tb, Pb = timed(plain_graph)
+    td, (Pd, std) = min((timed(sized_host) for _ in range(3)), key=lambda r: r[0])
     Pc, stc, caps, rep_s, tc = sized_graph()
-    assert Pa == Pb == Pc
+    assert Pa == Pb == Pc == Pd
     with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext) as h:
         pred, _ = tpg.tpg_sizer_predict(z, h, N)
     vol = np.expm1(np.maximum(pred.astype(np.float64), 0))
     est = np.array([vol[bounds[i]:bounds[i + 1]].sum(0) for i in range(len(held))])
     err = np.abs(np.log1p(est) - np.log1p(truth))
-    # LPT launch groups by predicted volume (the same sums the pre-sizing uses):
-    # retry rate per graph
-    groups, loads = lpt_groups(est[:, 0], args.groups)
-    retried, tg = 0, 0.0
-    for gidx in groups:
-        Pg, stg, _, _, t_ = sized_graph(gidx)
-        tg += t_
-        if stg["graph_fallbacks"]:
-            retried += len(gidx)
     used = truth[:, 0].sum() * 8
     line = {
-        "metric": METRIC, "value": Pc / tc, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
-        "ms_per_step": 1000 * tc, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": Pd / td, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
+        "ms_per_step": 1000 * td, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32 (sizer: bf16 weights, fp32 accumulate)", "data": "synthetic (seeded structured CFGs)",
         "config": {"workload": "learned sizer: train on 50k seeded CFGs (10-150 vertices), evaluate on a held-out "
                                "batch of 4096", "train_graphs": n_train, "epochs": args.epochs, "margin": args.margin,
                    "held_out_graphs": len(held), "vertices": N, "prime_paths": Pc,
-                   "step": "cold start of a new batch: load + (predict + presize) + capture + one replay"},
+                   "step": "cold start of a new batch: load + predict + presize + PPs + TPs (host-driven calls)"},
         "sizer": {"generate_s": gen_s, "label_s": label_s, "train_s": train_s,
                   "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                   "per_graph_abs_log_err_mean": [float(x) for x in err.mean(0)],
@@ -791,8 +809,9 @@ def run_sizer(args, rank, world, local_rank):
             "sizer_graph": {"pp_per_s": Pc / tc, "s": tc, "arena_alloc_bytes": int(caps[0]) * 8,
                             "arena_waste": 1 - used / max(int(caps[0]) * 8, 1),
                             "fallback": bool(stc["graph_fallbacks"]), "replay_pp_per_s": Pc / rep_s},
-            "sizer_lpt_groups": {"groups": args.groups, "retry_rate": retried / len(held), "s": tg,
-                                 "pp_per_s": Pc / tg, "predicted_loads": [float(x) for x in loads]},
+            "sizer_host_driven": {"pp_per_s": Pd / td, "s": td, "arena_alloc_bytes": std["arena_bytes_alloc"],
+                                  "arena_waste": 1 - used / max(std["arena_bytes_alloc"], 1),
+                                  "frontier_launches": std["attempts"]},
         },
     }
     z.close()
@@ -837,6 +856,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--level-trace", action="store_true",
+                    help="chain: add a per-level trace of one frontier launch")
     ap.add_argument("--no-extra", action="store_true",
                     help="chain: skip the structured-CFG and 4096-graph sub-records")
     ap.add_argument("--k", type=int, default=K_DIAMONDS, help="diamonds in the chain (22 = the benchmark workload)")
@@ -844,7 +865,6 @@ def main():
     ap.add_argument("--train-graphs", type=int, default=50000, help="sizer: training graphs")
     ap.add_argument("--epochs", type=int, default=40, help="sizer: training epochs")
     ap.add_argument("--margin", type=float, default=1.25, help="sizer: capacity margin over predictions")
-    ap.add_argument("--groups", type=int, default=8, help="sizer: LPT launch groups")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the per-graph plain launches")
     ap.add_argument("--tile", default="",
                     help="fixed frontier tile 'block,items' (batch: instead of the autotuner)")
