@@ -68,7 +68,7 @@ struct EnumArgs {
     long long agg_cap;       // int64 values in agg (enum_agg_words(grid, chunks per block) at least)
     int *err;                // error flags (zeroed)
     int *stop_level;         // level whose next level did not fit (written with the flags)
-    unsigned *bar;           // tree grid barrier, BAR_WORDS words (zeroed)
+    unsigned *bar;           // grid barrier: bar[0] is its arrival counter (zeroed)
     unsigned long long *root_counts;  // optional [3*N]: per first vertex, simple paths, PPs, PP vertices
     unsigned long long spin_ns;       // limit of every grid-barrier wait (SPIN_LIMIT_NS unless set)
     unsigned long long *trace;        // optional [LEVEL_TRACE_WORDS * max_levels] per-level timing
@@ -139,7 +139,7 @@ struct RankArgs {
     long long *bsum;      // [grid]
     long long *refs;      // [refs_cap]: the sorted PP references (level << 32 | index)
     long long refs_cap;
-    unsigned *bar;        // tree grid barrier, BAR_WORDS words (zeroed)
+    unsigned *bar;        // grid barrier: bar[0] is its arrival counter (zeroed)
     int *err;             // ERR_INVAL (a capacity too small), ERR_TIMEOUT
     const int *skip;      // optional: nothing is done when (*skip & skip_mask)
     int skip_mask;

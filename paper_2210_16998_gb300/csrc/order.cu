@@ -212,6 +212,12 @@ __global__ void __launch_bounds__(RANK_BLOCK) rank_pps_kernel(RankArgs a) {
     const unsigned full = 0xffffffffu;
     const int ml = a.max_levels;
     if (a.skip && (*a.skip & a.skip_mask)) return;  // the same on every block
+    // grid barrier on one growing arrival counter (a.bar[0], zero at launch)
+    unsigned bar_target = 0;
+    auto bar = [&](int stop) -> bool {
+        bar_target += (unsigned)G;
+        return grid_barrier_count(a.bar, bar_target, a.err, stop);
+    };
     long long *meta = a.noff + ml + 1;              // L, total nodes, P, largest level
 
     // node offsets of the levels and the totals (block 0), then everyone reads them
@@ -267,20 +273,20 @@ __global__ void __launch_bounds__(RANK_BLOCK) rank_pps_kernel(RankArgs a) {
             if (carry > a.cnt_cap || peak > a.pre_cap || pcarry > a.refs_cap) atomicOr(a.err, ERR_INVAL);
         }
     }
-    if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT | ERR_INVAL)) return;
+    if (!bar(ERR_TIMEOUT | ERR_INVAL)) return;
     const int L = (int)__ldcg(meta + 0);
     const long long total = __ldcg(meta + 1);
     if (L < 1) return;
 
     // counts: 0, then 1 at every PP
     for (long long i = gtid; i < total; i += T) a.cnt[i] = 0;
-    if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+    if (!bar(ERR_TIMEOUT)) return;
     for (int k = 1; k <= L; ++k) {
         const long long np = __ldcg(&a.levels[k].pp_count), o = __ldcg(a.noff + k);
         const int *pp = (const int *)__ldcg((const unsigned long long *)&a.levels[k].pp);
         for (long long i = gtid; i < np; i += T) a.cnt[o + pp[i]] = 1;
     }
-    if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+    if (!bar(ERR_TIMEOUT)) return;
 
     // bottom-up: add each node's count to its parent (consecutive nodes
     // mostly share a parent: one atomic per group of lanes)
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(RANK_BLOCK) rank_pps_kernel(RankArgs a) {
                 if (p[u] >= 0 && lane == __ffs(grp) - 1) atomicAdd(a.cnt + op + p[u], (int)sum);
             }
         }
-        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+        if (!bar(ERR_TIMEOUT)) return;
     }
 
     // level 1: rank = exclusive prefix sum of cnt (two passes over blocks)
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(RANK_BLOCK) rank_pps_kernel(RankArgs a) {
         long long tot;
         block_excl_scan_i64<RANK_BLOCK>(sum, tot);
         if (tid == 0) a.bsum[b] = tot;
-        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+        if (!bar(ERR_TIMEOUT)) return;
         long long off = 0;
         for (int j = tid; j < b; j += RANK_BLOCK) off += __ldcg(a.bsum + j);
         long long offt;
@@ -334,7 +340,7 @@ __global__ void __launch_bounds__(RANK_BLOCK) rank_pps_kernel(RankArgs a) {
             if (i < hi) a.pre[1][i] = (int)(run + ex);
             run += ttot;
         }
-        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+        if (!bar(ERR_TIMEOUT)) return;
     }
 
     // top-down: rank(v) = rank(parent) + counts of earlier siblings; the PPs
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(RANK_BLOCK) rank_pps_kernel(RankArgs a) {
             run_p = __shfl_sync(full, p, lastl);
             run_sum = __shfl_sync(full, sib + v, lastl);
         }
-        if (!grid_barrier_tree(a.bar, a.err, ERR_TIMEOUT)) return;
+        if (!bar(ERR_TIMEOUT)) return;
     }
 }
 
