@@ -301,12 +301,29 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * e2e_pp / float(te.item()) if e2e_steps else None
+    # the device-to-host link alone: the same byte count copied from device
+    # memory to page-locked host memory by the copy engine
+    link_gbps = None
+    if e2e_steps and bo > 0:
+        src = torch.empty(int(bo), dtype=torch.uint8, device="cuda")
+        dst = torch.empty(int(bo), dtype=torch.uint8, pin_memory=True)
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        link_gbps = 3 * int(bo) / (ea.elapsed_time(eb) / 1e3) / 1e9
+        del src, dst
     e2e_break = None
     if phases:
         e2e_break = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
         e2e_break["step_ms"] = 1e3 * e2e_s / e2e_steps
         d2h = e2e_break["d2h"]
         e2e_break["d2h_gb_per_s"] = e2e_break["d2h_bytes"] / (d2h / 1e3) / 1e9 if d2h > 0 else None
+        e2e_break["link_d2h_gb_per_s"] = link_gbps
         e2e_break["host_other"] = e2e_break["step_ms"] - (e2e_break["enumerate"] + e2e_break["order_materialise"]
                                                           + e2e_break["test_paths_device"] + d2h)
 

@@ -251,8 +251,9 @@ int tpg_set_wait_limit(tpg_cfg *g, int64_t ns);
  * frontier launch stops after the exact size of the level that did not fit
  * is known; the library adds an arena segment (or a larger frontier or PP
  * list) and relaunches at that level, so finished levels are kept and
- * results never depend on these values.  A pre-sizing policy (e.g. the
- * learned sizer) sets them.
+ * results never depend on these values.  Capacities whose buffers the
+ * allocator cannot give are halved until they fit.  A pre-sizing policy
+ * (e.g. the learned sizer) sets them.
  */
 int tpg_set_capacity(tpg_cfg *g, int64_t nodes, int64_t level_nodes, int64_t prime_paths);
 
@@ -323,8 +324,11 @@ int tpg_root_counts(tpg_cfg *g, int64_t *counts_host);
  * tpg_sizer_predict     per-vertex predictions pred_host[3*N] (optional) and
  *                       their expm1 sums totals_host[3] (optional).
  * tpg_sizer_presize     capacities of the handle's next graph capture from
- *                       the calibrated predicted totals times `margin` (>= 1); caps_out
- *                       (optional, 7 values) receives them.
+ *                       the calibrated predicted totals times `margin` (>= 1),
+ *                       scaled down so that the capture's buffers take at
+ *                       most half of the free device memory, each list below
+ *                       2^31 entries; caps_out (optional, 7 values) receives
+ *                       them.
  * tpg_sizer_features    the 8 features of every vertex (x_host[8*N]).
  * tpg_sizer_get_params / tpg_sizer_set_params   FP32 master weights
  *                       (tpg_sizer_num_params() floats).

@@ -100,6 +100,17 @@ struct DevCache {
             }
         }
         void *p = raw_alloc(f, c, s);
+        bool have_cached;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            have_cached = cached > 0;
+        }
+        if (!p && have_cached) {
+            // the allocator is out of memory while blocks sit in this cache:
+            // hand them all back and ask once more
+            flush();
+            p = raw_alloc(f, c, s);
+        }
         if (p) {
             std::lock_guard<std::mutex> lk(mu);
             size_of[p] = c;
@@ -695,6 +706,44 @@ int prepare_segments(tpg_cfg *g, std::vector<DevBuf> &segs, size_t elem, long lo
     return push_segment(g, segs, elem, (long long)(need / elem));
 }
 
+// The arena, PP list and frontier of a call at the handle's capacities.
+// The capacities are hints -- the arena grows by segments and the frontier
+// and PP list are enlarged when a level needs more -- so when the hinted
+// sizes do not fit in device memory they are halved (down to one vertex per
+// node, one frontier slot per vertex, one PP) until they do, and then once
+// more, which leaves the rest of the call (ordering and materialisation,
+// sized by the exact counts) as much room again.
+int alloc_enumeration_once(tpg_cfg *g) {
+    int rc = prepare_segments(g, g->node_segs, sizeof(int2), g->node_cap);
+    if (rc == TPG_OK) rc = prepare_segments(g, g->pp_segs, sizeof(int), g->pp_cap);
+    if (rc == TPG_OK) rc = alloc_frontier(g);
+    return rc;
+}
+
+int alloc_enumeration(tpg_cfg *g) {
+    bool shrunk = false;
+    for (;;) {
+        const int rc = alloc_enumeration_once(g);
+        if (rc == TPG_OK && !shrunk) return TPG_OK;
+        if (rc != TPG_OK && rc != TPG_ENOMEM) return rc;
+        if (g->node_cap <= g->N && g->lvl_cap <= round_frontier_cap(g->N) && g->pp_cap <= 1) return rc;
+        for (auto *segs : {&g->node_segs, &g->pp_segs}) {
+            for (auto &b : *segs) release(g, b);
+            segs->clear();
+        }
+        for (int b = 0; b < 2; ++b) {
+            release(g, g->tfl[b]);
+            release(g, g->tvis[b]);
+            release(g, g->tcnt[b]);
+        }
+        g->node_cap = std::max<long long>(g->node_cap / 2, g->N);
+        g->lvl_cap = round_frontier_cap(std::max<long long>(g->lvl_cap / 2, g->N));
+        g->pp_cap = std::max<long long>(g->pp_cap / 2, 1);
+        if (rc == TPG_OK) return alloc_enumeration_once(g);
+        shrunk = true;
+    }
+}
+
 // Page-locked staging for a level-table read-back of `bytes` (a pageable
 // destination would make the copy synchronous and slower); nullptr if none
 // can be had.
@@ -722,9 +771,7 @@ int enumerate_levels(tpg_cfg *g) {
     }
     g->lvl_cap = round_frontier_cap(std::max<long long>(g->lvl_cap, g->N));
     g->node_cap = std::max(g->node_cap, (long long)g->N);
-    RC(prepare_segments(g, g->node_segs, sizeof(int2), g->node_cap));
-    RC(prepare_segments(g, g->pp_segs, sizeof(int), g->pp_cap));
-    RC(alloc_frontier(g));
+    RC(alloc_enumeration(g));
     RC(alloc_fixed_workspace(g));
     if (!enum_shape_supported(g->W, g->shape)) g->shape = default_enum_shape(g->W);
     CK(cudaMemsetAsync(g->levels.p, 0, sizeof(LevelRec) * g->max_levels, s));
@@ -1983,13 +2030,34 @@ int tpg_sizer_presize(tpg_sizer *z, tpg_cfg *g, double margin, int64_t *caps_out
     const double nodes = tot[0] * z->calib[0] * margin + g->N, P = tot[1] * z->calib[1] * margin + 1,
                  V = tot[2] * z->calib[2] * margin + 1;
     const double rp = z->r_peak > 0 ? z->r_peak : 1.0;
-    g->node_cap = (long long)nodes;
-    g->lvl_cap = std::max<long long>((long long)(nodes * std::min(1.0, rp * margin)), g->N);
-    g->pp_cap = (long long)P;
-    g->out_cap[0] = (long long)P;
-    g->out_cap[1] = (long long)V;
-    g->out_cap[2] = (long long)(V * (z->r_tv0 > 0 ? z->r_tv0 : 2.0) * margin) + 1;
-    g->out_cap[3] = (long long)(V * (z->r_tv > 0 ? z->r_tv : 2.0) * margin) + 1;
+    const double lvl = nodes * std::min(1.0, rp * margin), TV0 = V * (z->r_tv0 > 0 ? z->r_tv0 : 2.0) * margin,
+                 TV = V * (z->r_tv > 0 ? z->r_tv : 2.0) * margin;
+    // a capture holds all of these at once: keep its buffers (per path: arena
+    // node and rank count, 12 bytes; per frontier slot: both ping-pong halves
+    // and rank prefixes; per PP: its reference and ~170 bytes of ordering, TP
+    // and output workspace; PP and TP vertices and TP merge keys; 25% growth
+    // slack of every buffer) within half of the free device memory; smaller
+    // capacities only cost a fallback to the exact path
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    const double bytes =
+        1.25 * (12.0 * nodes + (2.0 * (sizeof(int2) + 4.0 * g->W + sizeof(unsigned short)) + 8.0) * lvl +
+                (sizeof(int) + 170.0) * P + 4.0 * V + 6.0 * TV0 + 4.0 * TV);
+    const double f = free_b ? std::min(1.0, 0.5 * (double)free_b / bytes) : 1.0;
+    // list sizes also stay below 2^31 (a larger need falls back as well)
+    auto cap = [](double x, long long lo) {
+        return std::max<long long>(lo, (long long)std::min(x, (double)MAX31 - 1));
+    };
+    g->node_cap = std::max<long long>((long long)(f * nodes), g->N);
+    g->lvl_cap = cap(f * lvl, g->N);
+    g->pp_cap = cap(f * P, 1);
+    g->out_cap[0] = g->pp_cap;
+    g->out_cap[1] = cap(f * V, 1);
+    g->out_cap[2] = cap(f * TV0, 1);
+    g->out_cap[3] = cap(f * TV, 1);
     g->gp.ready = false;
     if (caps_out) {
         const long long c[7] = {g->node_cap, g->lvl_cap, g->pp_cap, g->out_cap[0], g->out_cap[1], g->out_cap[2],

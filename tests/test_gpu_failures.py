@@ -11,6 +11,10 @@ returns NULL after a given number of allocations.  Every failure point of a
 load + prime paths + test paths sequence must give TPG_ENOMEM (or succeed
 when the failure point is past the last allocation), hand back every block
 it obtained, and leave the library usable.
+
+(3) Capacity hints are hints: an allocator that refuses to hold more than
+256 MiB at once, and arena capacities of hundreds of GiB, still give the
+exact result (the hinted sizes are halved until they fit).
 """
 import numpy as np
 import pytest
@@ -124,3 +128,57 @@ def test_allocation_failure_at_every_point_gives_enomem_and_no_leak():
     (off, vert), (toff, tvert) = _run_sequence(cfg)
     assert_paths_equal(off, vert, ref.pp_offsets, ref.pp_vertices, "PPs after the sweep")
     assert_paths_equal(toff, tvert, ref.tp_offsets, ref.tp_vertices, "TPs after the sweep")
+
+
+class _CappedAllocator:
+    """Device blocks from torch's caching allocator while the bytes held stay
+    within `cap`; NULL for a request that would pass it."""
+
+    def __init__(self, cap):
+        self.cap = cap
+        self.live = {}
+        self.refused = 0
+
+    def alloc(self, nbytes, stream):
+        import torch
+
+        if sum(self.live.values()) + nbytes > self.cap:
+            self.refused += 1
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        self.live[p] = nbytes
+        return p
+
+    def release(self, ptr, stream):
+        import torch
+
+        if self.live.pop(ptr, None) is not None:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def test_capacity_hints_beyond_memory_are_halved_and_stay_exact():
+    import torch
+
+    cfg = G.diamond_chain(14)
+    ref = oracle.run_cfg(cfg, test_paths=True)
+    cap = 1 << 28
+    ca = _CappedAllocator(cap)
+    try:
+        tpg.tpg_set_allocator(ca.alloc, ca.release)
+        with tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit) as h:
+            # 512 GiB of arena, a 2^32-path frontier, 2^36 PP references
+            tpg.tpg_set_capacity(h, 1 << 36, 1 << 32, 1 << 36)
+            with tpg.tpg_prime_paths(h) as pp, tpg.tpg_test_paths(h) as tp:
+                off, vert = pp.host_arrays()[1:]
+                toff, tvert = tp.host_arrays()[1:]
+            st = tpg.tpg_get_stats(h)
+        assert_paths_equal(off, vert, ref.pp_offsets, ref.pp_vertices, "PPs")
+        assert_paths_equal(toff, tvert, ref.tp_offsets, ref.tp_vertices, "TPs")
+        assert ca.refused > 0
+        assert 0 < st["arena_bytes_alloc"] <= cap
+        torch.cuda.synchronize()
+        tpg.tpg_release_cached_memory()
+        assert not ca.live
+    finally:
+        tpg.tpg_set_allocator(None)
+        tpg._install_torch_allocator()

@@ -150,6 +150,42 @@ def test_presized_graph_capture_is_exact():
                 tp.free()
 
 
+def test_presize_keeps_capacities_within_free_memory():
+    # an absurd margin asks for far more than the device holds: the
+    # capacities are cut to half the free memory and the capture stays exact
+    import torch
+
+    train = [G.random_cfg(G.TRAIN_SEED0 + 7000 + i) for i in range(128)]
+    held = [G.random_cfg(G.HELDOUT_SEED0 + 3000 + i) for i in range(64)]
+    ns, rp, col, ent, ext = G.concat_batch(held)
+    with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext) as ref_h:
+        with tpg.tpg_prime_paths(ref_h) as pp, tpg.tpg_test_paths(ref_h) as tp:
+            ref_pp, ref_tp = pp.host_arrays(), tp.host_arrays()
+    with tpg.tpg_sizer_create(seed=4) as z:
+        h, _ = load_batch(train)
+        with h:
+            tpg.tpg_sizer_add_batch(z, h)
+        tpg.tpg_sizer_train(z, 5, 3e-3)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        free, _ = torch.cuda.mem_get_info()
+        with tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext) as h:
+            caps = tpg.tpg_sizer_presize(z, h, 1e12)
+            # the arena alone (8-byte nodes) stays within half the free memory
+            assert 8 * int(caps[0]) <= free // 2
+            tpg.tpg_graph_capture(h)
+            pp, tp = tpg.tpg_graph_launch(h)
+            for a, b in zip(pp.host_arrays(), ref_pp):
+                np.testing.assert_array_equal(a, b)
+            for a, b in zip(tp.host_arrays(), ref_tp):
+                np.testing.assert_array_equal(a, b)
+            pp.free()
+            tp.free()
+    torch.cuda.synchronize()
+    tpg.tpg_release_cached_memory()
+    torch.cuda.empty_cache()
+
+
 def test_checkpoint_round_trip(tmp_path):
     with tpg.tpg_sizer_create(seed=9) as a, tpg.tpg_sizer_create(seed=10) as b:
         pa = tpg.tpg_sizer_get_params(a)
