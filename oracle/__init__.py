@@ -10,6 +10,8 @@ and is compiled here with the system C compiler.  Its root-parallel driver
 (``run_parallel``) runs the same enumeration root by root on every host core
 for the all-core CPU baseline.  ``literal.py`` is a second,
 quadratic oracle for tiny graphs that applies the definitions word for word.
+``orc_test_paths_greedy`` (``run(..., greedy=True)``) is the longest-first
+touring of Sec. 7.3: a smaller TP set.
 """
 from __future__ import annotations
 
@@ -65,17 +67,19 @@ def _load():
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_test_paths.restype = ctypes.c_int
         lib.orc_test_paths.argtypes = [P, i32p, i32p, ctypes.c_int, ctypes.c_int]
+        lib.orc_test_paths_greedy.restype = ctypes.c_int
+        lib.orc_test_paths_greedy.argtypes = [P, i32p, i32p, ctypes.c_int, ctypes.c_int]
         lib.orc_bfs_tables.restype = ctypes.c_int
         lib.orc_bfs_tables.argtypes = [ctypes.c_int, i32p, i32p, i32p, i32p]
         for name in ("orc_n_simple", "orc_pp_count", "orc_pp_total",
-                     "orc_tp_count", "orc_tp_total"):
+                     "orc_tp_count", "orc_tp_total", "orc_gtp_count", "orc_gtp_total"):
             getattr(lib, name).restype = ctypes.c_int64
             getattr(lib, name).argtypes = [P]
-        for name in ("orc_pp_offsets", "orc_tp_offsets", "orc_len_counts",
+        for name in ("orc_pp_offsets", "orc_tp_offsets", "orc_gtp_offsets", "orc_len_counts",
                      "orc_pp_len_counts", "orc_root_paths", "orc_root_pp_ints", "orc_root_pps"):
             getattr(lib, name).restype = ctypes.POINTER(ctypes.c_int64)
             getattr(lib, name).argtypes = [P]
-        for name in ("orc_pp_vertices", "orc_tp_vertices"):
+        for name in ("orc_pp_vertices", "orc_tp_vertices", "orc_gtp_vertices"):
             getattr(lib, name).restype = ctypes.POINTER(ctypes.c_int32)
             getattr(lib, name).argtypes = [P]
         lib.orc_error.restype = ctypes.c_int
@@ -110,6 +114,8 @@ class OracleResult:
     pp_vertices: np.ndarray | None = None
     tp_offsets: np.ndarray | None = None
     tp_vertices: np.ndarray | None = None
+    gtp_offsets: np.ndarray | None = None   # longest-first touring
+    gtp_vertices: np.ndarray | None = None
 
     @property
     def num_pp(self) -> int:
@@ -123,24 +129,36 @@ class OracleResult:
         o, v = self.tp_offsets, self.tp_vertices
         return [tuple(int(x) for x in v[o[i]:o[i + 1]]) for i in range(len(o) - 1)]
 
+    def gtp_list(self):
+        o, v = self.gtp_offsets, self.gtp_vertices
+        return [tuple(int(x) for x in v[o[i]:o[i + 1]]) for i in range(len(o) - 1)]
+
 
 def run(n, row_ptr, col, entry=None, exit=None, want_paths=True, limit=0,
-        test_paths=False) -> OracleResult:
-    """Run the oracle on one graph (int32 CSR, ascending adjacency)."""
+        test_paths=False, greedy=False) -> OracleResult:
+    """Run the oracle on one graph (int32 CSR, ascending adjacency).  With
+    `greedy`, also the longest-first touring TP set (gtp_*)."""
     lib = _load()
     rp, rpp = _i32(row_ptr)
     cl, clp = _i32(col if len(col) else np.zeros(1, np.int32))
-    h = lib.orc_prime_paths(int(n), rpp, clp, 1 if (want_paths or test_paths) else 0,
-                            int(limit))
+    paths = want_paths or test_paths or greedy
+    h = lib.orc_prime_paths(int(n), rpp, clp, 1 if paths else 0, int(limit))
     if not h:
         raise OracleError(ORC_ENOMEM, "prime_paths")
     try:
-        res = _result(lib, h, n, want_paths or test_paths)
+        res = _result(lib, h, n, paths)
         if test_paths:
             rc = lib.orc_test_paths(h, rpp, clp, int(entry), int(exit))
             if rc:
                 raise OracleError(rc, "test_paths")
             _take_tps(lib, h, res)
+        if greedy:
+            rc = lib.orc_test_paths_greedy(h, rpp, clp, int(entry), int(exit))
+            if rc:
+                raise OracleError(rc, "test_paths_greedy")
+            cnt = int(lib.orc_gtp_count(h))
+            res.gtp_offsets = _copy(lib.orc_gtp_offsets(h), cnt + 1, np.int64)
+            res.gtp_vertices = _copy(lib.orc_gtp_vertices(h), int(lib.orc_gtp_total(h)), np.int32)
         return res
     finally:
         lib.orc_free(h)
@@ -199,9 +217,9 @@ def _result(lib, h, n, with_paths):
     return res
 
 
-def run_cfg(cfg, test_paths=True, want_paths=True, limit=0) -> OracleResult:
+def run_cfg(cfg, test_paths=True, want_paths=True, limit=0, greedy=False) -> OracleResult:
     return run(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit,
-               want_paths=want_paths, limit=limit, test_paths=test_paths)
+               want_paths=want_paths, limit=limit, test_paths=test_paths, greedy=greedy)
 
 
 def bfs_tables(n, row_ptr, col):

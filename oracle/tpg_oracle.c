@@ -32,6 +32,13 @@
  *     backwards from b through P[a][.].  TP(p) = path(entry -> first p),
  *     then p, then path(last p -> exit), joined at the shared endpoints; the
  *     TP set is the sorted, duplicate-free set of TP(p) over all PPs p.
+ *  5. A smaller TP set by longest-first touring (Ammann and Offutt's method
+ *     as Sec. 7.3 describes it): take the longest PP that no chosen TP
+ *     covers yet, extend it to the entry and the exit (its TP(p) of step 4),
+ *     and repeat until every PP is covered.  A PP is covered when it is a
+ *     contiguous subpath (Sec. 2) of a chosen TP.  Readings: "longest" counts
+ *     vertices; equal lengths go in canonical order; the result is put in
+ *     canonical order.  orc_test_paths_greedy.
  */
 #include <pthread.h>
 #include <stdatomic.h>
@@ -56,6 +63,7 @@ typedef struct {
 typedef struct orc_result {
     int n;
     seqlist pp, tp;
+    seqlist gtp;            /* longest-first touring (step 5) */
     int64_t n_simple;       /* simple paths visited, cycles included */
     int64_t *len_counts;    /* [n+2] simple paths by vertex count */
     int64_t *pp_len_counts; /* [n+2] PPs by vertex count */
@@ -403,6 +411,123 @@ int orc_test_paths(orc_result *r, const int32_t *row_ptr, const int32_t *col,
     return rc;
 }
 
+/* ---- step 5: longest-first touring ---- */
+
+/* 64-bit FNV-1a over a vertex sequence (never 0: 0 marks an empty slot) */
+static uint64_t seq_hash(const int32_t *s, int64_t k) {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t i = 0; i < k; i++) {
+        uint32_t x = (uint32_t)s[i];
+        for (int b = 0; b < 4; b++) { h ^= (x >> (8 * b)) & 0xffu; h *= 1099511628211ull; }
+    }
+    return h ? h : 1;
+}
+
+/* An open-addressing set of the PP list: slot -> PP index + 1 (0 = empty). */
+typedef struct {
+    int64_t mask;
+    int64_t *slot;
+    uint64_t *key;
+} pp_set;
+
+static int pp_set_build(pp_set *t, const seqlist *pp) {
+    int64_t size = 16;
+    while (size < 2 * pp->n) size *= 2;
+    t->mask = size - 1;
+    t->slot = (int64_t *)calloc((size_t)size, sizeof(int64_t));
+    t->key = (uint64_t *)calloc((size_t)size, sizeof(uint64_t));
+    if (!t->slot || !t->key) return ORC_ENOMEM;
+    for (int64_t i = 0; i < pp->n; i++) {
+        uint64_t h = seq_hash(pp->v + pp->off[i], pp->off[i + 1] - pp->off[i]);
+        int64_t j = (int64_t)(h & (uint64_t)t->mask);
+        while (t->slot[j]) j = (j + 1) & t->mask;
+        t->slot[j] = i + 1;
+        t->key[j] = h;
+    }
+    return ORC_OK;
+}
+
+/* index of the PP equal to s[0..k), or -1 */
+static int64_t pp_set_find(const pp_set *t, const seqlist *pp, const int32_t *s, int64_t k) {
+    uint64_t h = seq_hash(s, k);
+    for (int64_t j = (int64_t)(h & (uint64_t)t->mask); t->slot[j]; j = (j + 1) & t->mask) {
+        int64_t i = t->slot[j] - 1;
+        if (t->key[j] == h && seq_cmp(pp->v + pp->off[i], pp->off[i + 1] - pp->off[i], s, k) == 0) return i;
+    }
+    return -1;
+}
+
+static const seqlist *g_len_list;
+/* longest first; equal lengths in list (canonical) order */
+static int cmp_len_desc(const void *x, const void *y) {
+    int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;
+    const seqlist *s = g_len_list;
+    int64_t la = s->off[a + 1] - s->off[a], lb = s->off[b + 1] - s->off[b];
+    if (la != lb) return la > lb ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+int orc_test_paths_greedy(orc_result *r, const int32_t *row_ptr, const int32_t *col,
+                          int entry, int exitv) {
+    int n = r->n;
+    if (r->err) return r->err;
+    if (entry < 0 || entry >= n || exitv < 0 || exitv >= n) return ORC_EINVAL;
+    if (!r->bfs_dist) {
+        r->bfs_dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * (size_t)n);
+        r->bfs_pred = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * (size_t)n);
+        if (!r->bfs_dist || !r->bfs_pred) return ORC_ENOMEM;
+        if (orc_bfs_tables(n, row_ptr, col, r->bfs_dist, r->bfs_pred)) return ORC_ENOMEM;
+    }
+    sl_free(&r->gtp);
+    if (sl_init(&r->gtp)) return ORC_ENOMEM;
+    const seqlist *pp = &r->pp;
+    const int64_t P = pp->n;
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P > 0 ? P : 1));
+    char *covered = (char *)calloc((size_t)(P > 0 ? P : 1), 1);
+    int32_t *mark = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    seqlist one = {0, 0, NULL, 0, 0, NULL};
+    pp_set set = {0, NULL, NULL};
+    int rc = (order && covered && mark && sl_init(&one) == ORC_OK) ? pp_set_build(&set, pp) : ORC_ENOMEM;
+    if (rc == ORC_OK) {
+        for (int64_t i = 0; i < P; i++) order[i] = i;
+        g_len_list = pp;
+        qsort(order, (size_t)P, sizeof(int64_t), cmp_len_desc);
+    }
+    for (int64_t oi = 0; oi < P && rc == ORC_OK; oi++) {
+        const int64_t p = order[oi];
+        if (covered[p]) continue;
+        /* TP(p), step 4 */
+        one.n = 0; one.nv = 0;
+        rc = tp_build_range(r, r->bfs_dist, r->bfs_pred, entry, exitv, p, p + 1, &one);
+        if (rc) break;
+        const int32_t *t = one.v;
+        const int64_t L = one.nv;
+        if (sl_push(&r->gtp, t, (int)L, -1)) { rc = ORC_ENOMEM; break; }
+        /* every window t[i..j] that is a simple path, looked up among the PPs
+         * (a window that is not simple cannot be a PP) */
+        for (int64_t i = 0; i < L; i++) {
+            int64_t j = i;
+            for (; j < L; j++) {
+                if (j > i && t[j] == t[i]) {           /* closes a simple cycle */
+                    int64_t q = pp_set_find(&set, pp, t + i, j - i + 1);
+                    if (q >= 0) covered[q] = 1;
+                    break;
+                }
+                if (mark[t[j]]) break;                 /* a repeat inside: not simple */
+                mark[t[j]] = 1;
+                int64_t q = pp_set_find(&set, pp, t + i, j - i + 1);
+                if (q >= 0) covered[q] = 1;
+            }
+            for (int64_t x = i; x < j && x < L; x++) mark[t[x]] = 0;
+        }
+        if (!covered[p]) { rc = ORC_EINVAL; break; }   /* TP(p) contains p */
+    }
+    if (rc == ORC_OK) rc = sort_unique(&r->gtp, 1);
+    free(order); free(covered); free(mark); free(set.slot); free(set.key);
+    if (one.off) sl_free(&one);
+    return rc;
+}
+
 /*
  * Root-parallel driver, for the all-core CPU baseline.
  *
@@ -557,6 +682,10 @@ int64_t orc_pp_count(const orc_result *r) { return r->pp.n; }
 int64_t orc_pp_total(const orc_result *r) { return r->pp.nv; }
 const int64_t *orc_pp_offsets(const orc_result *r) { return r->pp.off; }
 const int32_t *orc_pp_vertices(const orc_result *r) { return r->pp.v; }
+int64_t orc_gtp_count(const orc_result *r) { return r->gtp.n; }
+int64_t orc_gtp_total(const orc_result *r) { return r->gtp.nv; }
+const int64_t *orc_gtp_offsets(const orc_result *r) { return r->gtp.off; }
+const int32_t *orc_gtp_vertices(const orc_result *r) { return r->gtp.v; }
 int64_t orc_tp_count(const orc_result *r) { return r->tp.n; }
 int64_t orc_tp_total(const orc_result *r) { return r->tp.nv; }
 const int64_t *orc_tp_offsets(const orc_result *r) { return r->tp.off; }
@@ -571,6 +700,7 @@ void orc_free(orc_result *r) {
     if (!r) return;
     sl_free(&r->pp);
     sl_free(&r->tp);
+    sl_free(&r->gtp);
     free(r->len_counts); free(r->pp_len_counts);
     free(r->root_paths); free(r->root_pp_ints); free(r->root_pps);
     free(r->bfs_dist); free(r->bfs_pred);
