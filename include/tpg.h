@@ -112,6 +112,10 @@ typedef struct tpg_stats {
     float t_result_copy_ms;     /* device time of the device-to-host copies of the last host result
                                    (0 when it shared an earlier copy or lives on the device) */
     int64_t result_copy_bytes;  /* bytes those copies moved */
+    float t_touring_ms;         /* device time of the last tpg_test_paths_greedy after its one-per-PP
+                                   TP list: hash tables, touring launch, compaction */
+    int32_t touring_warps;      /* warps per block of that touring launch */
+    int64_t touring_test_paths; /* TPs it chose */
 } tpg_stats;
 
 /*
@@ -183,6 +187,22 @@ int tpg_prime_paths(tpg_cfg *g, tpg_paths **out);
  * TPG_EUNREACH if some PP cannot be toured.
  */
 int tpg_test_paths(tpg_cfg *g, tpg_paths **out);
+
+/*
+ * tpg_test_paths_greedy -- a smaller TP set by longest-first touring: the
+ * construction Sec. 7.3 credits to Ammann and Offutt (take the longest PP,
+ * extend it to the entry and the exit, repeat with the longest PP that no
+ * chosen TP covers yet).  Here the extension of p is TP(p) as in
+ * tpg_test_paths, a PP is covered when it is a contiguous subpath of a
+ * chosen TP, PPs of equal length are taken in canonical order, and the
+ * chosen TPs are returned in canonical order: a subset of tpg_test_paths's
+ * list that still tours every PP.  Graphs of a batch are toured
+ * independently (num_graphs and graph_path_ptr as for tpg_test_paths).
+ * Runs tpg_prime_paths and the one-per-PP TP pipeline internally.
+ * TPG_EUNREACH if some PP cannot be toured; TPG_ETOOBIG if the PP or TP
+ * list holds 2^31 paths or more.
+ */
+int tpg_test_paths_greedy(tpg_cfg *g, tpg_paths **out);
 
 /* Release a tpg_cfg*, tpg_paths* or tpg_sizer* (tag-checked).  NULL is a no-op. */
 void tpg_free(void *handle);

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "testpaths.h"
+#include "touring.h"
 
 using namespace tpg;
 
@@ -397,7 +398,7 @@ struct tpg_cfg {
     bool pp_valid = false;
 
     tpg_stats stats{};
-    cudaEvent_t ev[10] = {};  // [8], [9]: host-result copies
+    cudaEvent_t ev[12] = {};  // [8], [9]: host-result copies; [10], [11]: touring
     long long last_tv0 = 0;  // TP vertices before dedup in the last tpg_test_paths
 
     // graph mode: the whole hot path captured in one CUDA graph
@@ -515,7 +516,7 @@ void destroy_cfg(tpg_cfg *g) {
     for (auto &b : g->pp_segs) release(g, b);
     cudaStreamSynchronize(g->stream);
     handle_pool().put_small(g->h_small);
-    handle_pool().put_events(g->device, g->ev, 10);
+    handle_pool().put_events(g->device, g->ev, 12);
     pinned().put(g->h_lvl_stage);
     g->magic = MAGIC_DEAD;
     delete g;
@@ -550,7 +551,7 @@ int new_cfg(void *stream, tpg_cfg **out) {
     g->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&g->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess ||
-        !(g->h_small = (int *)handle_pool().get_small()) || !handle_pool().get_events(g->device, g->ev, 10)) {
+        !(g->h_small = (int *)handle_pool().get_small()) || !handle_pool().get_events(g->device, g->ev, 12)) {
         cudaGetLastError();
         handle_pool().put_small(g->h_small);
         delete g;
@@ -1746,6 +1747,147 @@ int tpg_test_paths(tpg_cfg *g, tpg_paths **out) {
     long long T = 0, TV = 0;
     RC(run_test_paths(g, &off, &vert, &gptr, &T, &TV));
     const int rc = make_result(g, off, vert, gptr, T, TV, out);
+    block_unref(off);
+    block_unref(vert);
+    block_unref(gptr);
+    return rc;
+}
+
+// Longest-first touring over the one-per-PP TP list (toff, tvert, tgptr; T
+// TPs): hash tables of the PP and TP lists, the touring launch, and the
+// chosen TPs gathered in their (canonical) order.
+static int run_touring(tpg_cfg *g, Block *toff, Block *tvert, Block *tgptr, long long T, long long TV, tpg_paths **out) {
+    cudaStream_t s = g->stream;
+    const long long P = g->P;
+    if (P == 0 || T == 0) return make_result(g, toff, tvert, tgptr, T, TV, out);
+    if (P >= (long long)MAX31 || T >= (long long)MAX31) return TPG_ETOOBIG;
+    const int G = g->G;
+    // graphs in claim order: most PPs first
+    std::vector<long long> gp(G + 1);
+    CK(cudaMemcpyAsync(gp.data(), g->pp_gptr->p, sizeof(long long) * (G + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int> order(G);
+    for (int i = 0; i < G; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return gp[x + 1] - gp[x] > gp[y + 1] - gp[y]; });
+    int smem_optin = 0;
+    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
+    const int warps = tour_warps(g->maxn, (size_t)std::max(smem_optin - 1024, 0));
+    if (tour_smem_bytes(g->maxn, warps) + 1024 > (size_t)smem_optin) return TPG_ETOOBIG;
+
+    const long long Spp = tour_table_slots(P), Stp = tour_table_slots(T);
+    DevBuf ord, cov, sel, ppk, ppi, tpk, tpi, gord, tpg, ctl, keep_len, keep_off, keep_rank, perm, tmp, fgraph;
+    int rc = TPG_OK;
+    Block *f_off = nullptr, *f_vert = nullptr, *f_gptr = nullptr;
+    long long T2 = 0, TV2 = 0;
+    do {
+        if ((rc = ensure(g, ord, sizeof(int) * P)) || (rc = ensure(g, cov, P)) ||
+            (rc = ensure(g, sel, sizeof(int) * T)) || (rc = ensure(g, ppk, sizeof(unsigned long long) * Spp)) ||
+            (rc = ensure(g, ppi, sizeof(int) * Spp)) || (rc = ensure(g, tpk, sizeof(unsigned long long) * Stp)) ||
+            (rc = ensure(g, tpi, sizeof(int) * Stp)) || (rc = ensure(g, gord, sizeof(int) * G)) ||
+            (rc = ensure(g, tpg, sizeof(int) * T)) || (rc = ensure(g, ctl, 2 * sizeof(int))) ||
+            (rc = ensure(g, keep_len, sizeof(long long) * T)) ||
+            (rc = ensure(g, keep_off, sizeof(long long) * (T + 1))) ||
+            (rc = ensure(g, keep_rank, sizeof(long long) * (T + 1))) ||
+            (rc = ensure(g, perm, sizeof(long long) * T)) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(T + 1))))
+            break;
+        if (cudaEventRecord(g->ev[10], s) || cudaMemsetAsync(cov.p, 0, P, s) ||
+            cudaMemsetAsync(sel.p, 0, sizeof(int) * T, s) ||
+            cudaMemsetAsync(ppk.p, 0, sizeof(unsigned long long) * Spp, s) ||
+            cudaMemsetAsync(tpk.p, 0, sizeof(unsigned long long) * Stp, s) ||
+            cudaMemsetAsync(ctl.p, 0, 2 * sizeof(int), s) ||
+            cudaMemcpyAsync(gord.p, order.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s)) {
+            rc = cuda_err(cudaGetLastError());
+            break;
+        }
+        const PathTable pp_tab{ppk.as<unsigned long long>(), ppi.as<int>(), Spp - 1};
+        const PathTable tp_tab{tpk.as<unsigned long long>(), tpi.as<int>(), Stp - 1};
+        const long long *pp_off = (const long long *)g->pp_off->p;
+        const int *pp_vert = (const int *)g->pp_vert->p;
+        const int *pp_graph = g->pp_graph ? (const int *)g->pp_graph->p : nullptr;
+        if ((rc = cuda_err(tour_table_build(pp_tab, pp_off, pp_vert, pp_graph, nullptr, G, P, s))) ||
+            (rc = cuda_err(tour_graph_ids((const long long *)tgptr->p, G, T, tpg.as<int>(), s))) ||
+            (rc = cuda_err(tour_table_build(tp_tab, (const long long *)toff->p, (const int *)tvert->p, tpg.as<int>(),
+                                            nullptr, G, T, s))))
+            break;
+        TourArgs a{};
+        a.g = g->gd;
+        a.pp_off = pp_off;
+        a.pp_vert = pp_vert;
+        a.pp_gptr = (const long long *)g->pp_gptr->p;
+        a.pp_tab = pp_tab;
+        a.tp_off = (const long long *)toff->p;
+        a.tp_vert = (const int *)tvert->p;
+        a.tp_gptr = (const long long *)tgptr->p;
+        a.tp_tab = tp_tab;
+        a.gorder = gord.as<int>();
+        a.claim = ctl.as<int>();
+        a.err = ctl.as<int>() + 1;
+        a.ord = ord.as<int>();
+        a.cov = cov.as<unsigned char>();
+        a.sel = sel.as<int>();
+        a.maxn = g->maxn;
+        if ((rc = cuda_err(tour_greedy(a, G, warps, g->num_sms, s)))) break;
+        // the chosen TPs, in list order
+        long long *klen = keep_len.as<long long>(), *koff = keep_off.as<long long>(), *krank = keep_rank.as<long long>();
+        if ((rc = cuda_err(tour_keep_lengths(sel.as<int>(), (const long long *)toff->p, T, klen, s))) ||
+            (rc = cuda_err(scan_i64(klen, koff, T, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(scan_i32_to_i64(sel.as<int>(), krank, T, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(tp_iota(perm.as<long long>(), T, s))))
+            break;
+        long long *h = (long long *)g->h_small;
+        if (cudaMemcpyAsync(h, krank + T, sizeof(long long), cudaMemcpyDeviceToHost, s) ||
+            cudaMemcpyAsync(h + 1, koff + T, sizeof(long long), cudaMemcpyDeviceToHost, s) ||
+            cudaMemcpyAsync(h + 2, a.err, sizeof(int), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s)) {
+            rc = cuda_err(cudaGetLastError());
+            break;
+        }
+        T2 = h[0];
+        TV2 = h[1];
+        const int err = ((int *)(h + 2))[0];
+        if (err & ERR_UNREACH) { rc = TPG_EUNREACH; break; }
+        if (err) { rc = TPG_ECUDA; break; }  // a TP or PP the touring built was not in its list
+        f_off = block_new(g->fns, sizeof(long long) * (T2 + 1), s);
+        f_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV2, 1), s);
+        f_gptr = block_new(g->fns, sizeof(long long) * (G + 1), s);
+        if (!f_off || !f_vert || !f_gptr) { rc = TPG_ENOMEM; break; }
+        if ((rc = ensure(g, fgraph, sizeof(int) * std::max<long long>(T2, 1)))) break;
+        h[3] = TV2;
+        if ((rc = cuda_err(tp_gather(perm.as<long long>(), sel.as<int>(), krank, T, (const long long *)toff->p,
+                                     (const int *)tvert->p, tpg.as<int>(), koff, (long long *)f_off->p,
+                                     (int *)f_vert->p, fgraph.as<int>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync((long long *)f_off->p + T2, h + 3, sizeof(long long),
+                                           cudaMemcpyHostToDevice, s))) ||
+            (rc = cuda_err(graph_ptr_from_ids(fgraph.as<int>(), T2, G, (long long *)f_gptr->p, s))))
+            break;
+        if (cudaEventRecord(g->ev[11], s) || cudaStreamSynchronize(s)) {
+            rc = cuda_err(cudaGetLastError());
+            break;
+        }
+        cudaEventElapsedTime(&g->stats.t_touring_ms, g->ev[10], g->ev[11]);
+        g->stats.touring_warps = warps;
+        g->stats.touring_test_paths = T2;
+    } while (false);
+    if (rc != TPG_OK) cudaStreamSynchronize(s);  // nothing of this call left in flight on the scratch
+    for (DevBuf *b : {&ord, &cov, &sel, &ppk, &ppi, &tpk, &tpi, &gord, &tpg, &ctl, &keep_len, &keep_off, &keep_rank,
+                      &perm, &tmp, &fgraph})
+        release(g, *b);
+    if (rc == TPG_OK) rc = make_result(g, f_off, f_vert, f_gptr, T2, TV2, out);
+    block_unref(f_off);
+    block_unref(f_vert);
+    block_unref(f_gptr);
+    return rc;
+}
+
+int tpg_test_paths_greedy(tpg_cfg *g, tpg_paths **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    Block *off = nullptr, *vert = nullptr, *gptr = nullptr;
+    long long T = 0, TV = 0;
+    RC(run_test_paths(g, &off, &vert, &gptr, &T, &TV));
+    const int rc = run_touring(g, off, vert, gptr, T, TV, out);
     block_unref(off);
     block_unref(vert);
     block_unref(gptr);

@@ -85,6 +85,9 @@ class _Stats(ctypes.Structure):
         ("graph_enum_error", ctypes.c_int32),
         ("t_result_copy_ms", ctypes.c_float),
         ("result_copy_bytes", ctypes.c_int64),
+        ("t_touring_ms", ctypes.c_float),
+        ("touring_warps", ctypes.c_int32),
+        ("touring_test_paths", ctypes.c_int64),
     ]
 
 
@@ -128,6 +131,7 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_load_cfg_batch.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.POINTER(P)]
         lib.tpg_prime_paths.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_test_paths.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
+        lib.tpg_test_paths_greedy.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_free.argtypes = [P]
         lib.tpg_free.restype = None
         lib.tpg_set_stream.argtypes = [P, P]
@@ -176,7 +180,8 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
                                                 ctypes.POINTER(ctypes.c_int64)]
         lib.tpg_prime_paths_noalloc.restype = ctypes.c_int
         for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
-                     "tpg_test_paths", "tpg_set_stream", "tpg_set_result_location", "tpg_set_allocator",
+                     "tpg_test_paths", "tpg_test_paths_greedy", "tpg_set_stream", "tpg_set_result_location",
+                     "tpg_set_allocator",
                      "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_work_split", "tpg_set_capacity",
                      "tpg_set_output_capacity",
                      "tpg_graph_capture", "tpg_graph_launch"):
@@ -411,6 +416,13 @@ def tpg_prime_paths(cfg: Cfg) -> Paths:
 def tpg_test_paths(cfg: Cfg) -> Paths:
     out = ctypes.POINTER(_Paths)()
     _check(load_library().tpg_test_paths(cfg.handle, ctypes.byref(out)), "tpg_test_paths")
+    return Paths(out)
+
+
+def tpg_test_paths_greedy(cfg: Cfg) -> Paths:
+    """The longest-first touring TP set (a subset of tpg_test_paths's list)."""
+    out = ctypes.POINTER(_Paths)()
+    _check(load_library().tpg_test_paths_greedy(cfg.handle, ctypes.byref(out)), "tpg_test_paths_greedy")
     return Paths(out)
 
 
