@@ -336,6 +336,7 @@ def run_ours(args, rank, world, local_rank):
         extra["config3"] = config_record(tpg, cfggen.config3_cfg(), "structured CFG, 120 vertices (10 while "
                                          "nested <= 4, 3 switch x6, if-else), cyclic", steps=max(args.steps // 2, 5))
         extra["batch4096"] = batch_record(tpg, cfggen, steps=max(args.steps // 2, 5))
+        extra["touring"] = touring_record(tpg, cfggen, steps=3, with_cpu=not args.no_cpu_baseline)
 
     if rank != 0:
         return None
@@ -486,6 +487,76 @@ def batch_record(tpg, cfggen, steps, tile=(1024, 1, 1)):
             "host_driven_ms": min(host_ms), "host_driven_pp_per_s": P / (min(host_ms) / 1e3),
             "host_driven_device_ms": {"enumerate": st["t_enumerate_ms"], "order_materialise": st["t_order_ms"],
                                       "test_paths": st["t_test_paths_ms"]}}
+
+
+def touring_record(tpg, cfggen, steps, with_cpu):
+    """Longest-first touring (tpg_test_paths_greedy) after the one-per-PP TP
+    list, on the 4096-graph batch and the 120-vertex CFG: TP counts and the
+    touring's device time (hash tables, touring launch, compaction)."""
+    import torch
+
+    out = {}
+    cases = [("batch4096", cfggen.batch_cfgs(4096)), ("config3", [cfggen.config3_cfg()])]
+    for name, cfgs in cases:
+        ns, rp, col, ent, ext = cfggen.concat_batch(cfgs)
+        h = tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE)
+        with tpg.tpg_test_paths(h) as tp:
+            T = tp.num_paths
+        dev, call = [], []
+        for i in range(steps + 2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gt = tpg.tpg_test_paths_greedy(h)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            GT = gt.num_paths
+            gt.free()
+            st = tpg.tpg_get_stats(h)
+            if i >= 2:
+                dev.append(st["t_touring_ms"])
+                call.append(1e3 * el)
+        P = st["prime_paths"]
+        rec = {"graphs": len(cfgs), "prime_paths": P, "one_per_pp_test_paths": T, "touring_test_paths": GT,
+               "touring_device_ms": statistics.median(dev), "call_ms": statistics.median(call),
+               "decision_sweeps": st["touring_sweeps"], "cover_edges": st["touring_edges"], "steps": steps,
+               "call": "tpg_test_paths_greedy on a handle whose PPs are cached: one-per-PP TP pipeline, then "
+                       "touring (device_ms covers the touring alone)"}
+        h.close()
+        if with_cpu:
+            import oracle
+
+            oracle.build()
+            t0 = time.perf_counter()
+            k = 0
+            while k < len(cfgs) and (k == 0 or time.perf_counter() - t0 < 10.0):
+                oracle.run_cfg(cfgs[k], test_paths=False, greedy=True)
+                k += 1
+            el = time.perf_counter() - t0
+            rec["cpu_baseline"] = {"kind": "oracle", "cores": 1, "graphs": k, "s": el,
+                                   "sample": f"PPs + touring of the first {k} of {len(cfgs)} graphs, "
+                                             f"single-threaded C -O2"}
+        out[name] = rec
+    return out
+
+
+def run_touring(args, rank, world, local_rank):
+    """Only the touring sub-record (longest-first TP sets of the 4096-graph
+    batch and the 120-vertex CFG)."""
+    import torch
+
+    from paper_2210_16998_gb300 import cfggen, tpg
+
+    torch.cuda.set_device(local_rank)
+    tpg.load_library(build=True)
+    rec = touring_record(tpg, cfggen, steps=max(args.steps, 1), with_cpu=not args.no_cpu_baseline)
+    if rank != 0:
+        return None
+    P = rec["batch4096"]["prime_paths"]
+    ms = rec["batch4096"]["touring_device_ms"]
+    return {"metric": "prime paths toured/sec (longest-first touring)", "value": P / (ms / 1e3), "unit": "PP/s",
+            "n_gpus": world, "steps": args.steps, "higher_is_better": True, "dtype": "int32",
+            "data": "synthetic (seeded structured CFGs)",
+            "config": {"workload": "longest-first touring of the 4096-graph batch"}, "touring": rec}
 
 
 def cpu_baseline_all_cores(cfg, budget_s=6.0, min_runs=2):
@@ -878,7 +949,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="chain: skip the structured-CFG and 4096-graph sub-records")
     ap.add_argument("--k", type=int, default=K_DIAMONDS, help="diamonds in the chain (22 = the benchmark workload)")
-    ap.add_argument("--workload", choices=["chain", "batch", "sizer"], default="chain")
+    ap.add_argument("--workload", choices=["chain", "batch", "sizer", "touring"], default="chain")
     ap.add_argument("--train-graphs", type=int, default=50000, help="sizer: training graphs")
     ap.add_argument("--epochs", type=int, default=40, help="sizer: training epochs")
     ap.add_argument("--margin", type=float, default=1.25, help="sizer: capacity margin over predictions")
@@ -899,7 +970,8 @@ def main():
 
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-        line = {"batch": run_batch, "sizer": run_sizer}.get(args.workload, run_ours)(args, rank, world, local_rank)
+        line = {"batch": run_batch, "sizer": run_sizer, "touring": run_touring}.get(args.workload, run_ours)(
+            args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist
 

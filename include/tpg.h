@@ -113,9 +113,10 @@ typedef struct tpg_stats {
                                    (0 when it shared an earlier copy or lives on the device) */
     int64_t result_copy_bytes;  /* bytes those copies moved */
     float t_touring_ms;         /* device time of the last tpg_test_paths_greedy after its one-per-PP
-                                   TP list: hash tables, touring launch, compaction */
-    int32_t touring_warps;      /* warps per block of that touring launch */
+                                   TP list: PP hash table, cover edges, decision sweeps, gather */
+    int32_t touring_sweeps;     /* decision sweeps it took */
     int64_t touring_test_paths; /* TPs it chose */
+    int64_t touring_edges;      /* cover edges (TP(p) holds q, q after p in the order) */
 } tpg_stats;
 
 /*

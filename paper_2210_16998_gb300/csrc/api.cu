@@ -398,6 +398,7 @@ struct tpg_cfg {
     bool pp_valid = false;
 
     tpg_stats stats{};
+    long long last_edges = 0;  // cover edges of the last touring call
     cudaEvent_t ev[12] = {};  // [8], [9]: host-result copies; [10], [11]: touring
     long long last_tv0 = 0;  // TP vertices before dedup in the last tpg_test_paths
 
@@ -1087,7 +1088,10 @@ int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, l
 // ---------------------------------------------------------------------------
 // test paths
 // ---------------------------------------------------------------------------
-int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, long long *oT, long long *oTV) {
+// pp_to_tp (optional, device int[P]) receives the index in the returned list
+// of every PP's TP(p).
+int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, long long *oT, long long *oTV,
+                   int *pp_to_tp = nullptr) {
     cudaStream_t s = g->stream;
     if (!g->pp_valid) RC(run_prime_paths(g));
     const long long P = g->P;
@@ -1168,6 +1172,7 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
             f_gptr = g->pp_gptr;
             T = P;
             FTV = TV;
+            if (pp_to_tp && cuda_err(tp_index_map(nullptr, nullptr, nullptr, P, pp_to_tp, s))) rc = TPG_ECUDA;
             break;
         }
         tp_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
@@ -1199,6 +1204,7 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
             }
             T = P;
             FTV = TV;
+            if (pp_to_tp && cuda_err(tp_index_map(nullptr, nullptr, nullptr, P, pp_to_tp, s))) rc = TPG_ECUDA;
             break;
         }
         // merge rounds over the runs inside every graph (a graph has at most
@@ -1249,7 +1255,8 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
         if (cuda_err(tp_dedup_flags_keys(perm[cp], P, (const long long *)tp_off->p, key_off, key, tp_graph, keep_len,
                                          keep, s)) ||
             cuda_err(scan_i64(keep_len, keep_off, P, g->s_tmp.as<long long>(), s)) ||
-            cuda_err(scan_i32_to_i64(keep, keep_rank, P, g->s_tmp.as<long long>(), s))) {
+            cuda_err(scan_i32_to_i64(keep, keep_rank, P, g->s_tmp.as<long long>(), s)) ||
+            (pp_to_tp && cuda_err(tp_index_map(perm[cp], keep, keep_rank, P, pp_to_tp, s)))) {
             rc = TPG_ECUDA;
             break;
         }
@@ -1753,101 +1760,129 @@ int tpg_test_paths(tpg_cfg *g, tpg_paths **out) {
     return rc;
 }
 
-// Longest-first touring over the one-per-PP TP list (toff, tvert, tgptr; T
-// TPs): hash tables of the PP and TP lists, the touring launch, and the
-// chosen TPs gathered in their (canonical) order.
-static int run_touring(tpg_cfg *g, Block *toff, Block *tvert, Block *tgptr, long long T, long long TV, tpg_paths **out) {
+// Longest-first touring: the PP hash table, the cover edges of every PP's
+// TP, the decision sweeps, and the chosen TPs gathered from the one-per-PP
+// list (toff, tvert, tgptr; T TPs; map[p] = index of TP(p) in it).
+static int run_touring(tpg_cfg *g, Block *toff, Block *tvert, Block *tgptr, long long T, long long TV,
+                       const int *map, tpg_paths **out) {
     cudaStream_t s = g->stream;
     const long long P = g->P;
     if (P == 0 || T == 0) return make_result(g, toff, tvert, tgptr, T, TV, out);
     if (P >= (long long)MAX31 || T >= (long long)MAX31) return TPG_ETOOBIG;
     const int G = g->G;
-    // graphs in claim order: most PPs first
-    std::vector<long long> gp(G + 1);
+    // per-graph hash tables
+    std::vector<long long> gp(G + 1), tb(G + 1);
     CK(cudaMemcpyAsync(gp.data(), g->pp_gptr->p, sizeof(long long) * (G + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    std::vector<int> order(G);
-    for (int i = 0; i < G; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return gp[x + 1] - gp[x] > gp[y + 1] - gp[y]; });
-    int smem_optin = 0;
-    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
-    const int warps = tour_warps(g->maxn, (size_t)std::max(smem_optin - 1024, 0));
-    if (tour_smem_bytes(g->maxn, warps) + 1024 > (size_t)smem_optin) return TPG_ETOOBIG;
-
-    const long long Spp = tour_table_slots(P), Stp = tour_table_slots(T);
-    DevBuf ord, cov, sel, ppk, ppi, tpk, tpi, gord, tpg, ctl, keep_len, keep_off, keep_rank, perm, tmp, fgraph;
-    int rc = TPG_OK;
+    const long long slots = tour_table_layout(gp.data(), G, tb.data());
+    const int LM = tour_max_tp(g->maxn);
+    DevBuf tkey, tidx, tbase, pw, ctl, edges, indeg, in_off, in_src, state, sel, keep_len, keep_off, keep_rank, perm,
+        tmp, tpg, fgraph;
+    int rc = TPG_OK, warps = 0, sweeps = 0;
     Block *f_off = nullptr, *f_vert = nullptr, *f_gptr = nullptr;
     long long T2 = 0, TV2 = 0;
+    long long *h = (long long *)g->h_small;
+    // cover edges: the last call's count, else 8 per PP (a second pass with
+    // the exact count if that is short)
+    long long edge_cap = std::max(g->last_edges, 8 * P + 1024);
     do {
-        if ((rc = ensure(g, ord, sizeof(int) * P)) || (rc = ensure(g, cov, P)) ||
-            (rc = ensure(g, sel, sizeof(int) * T)) || (rc = ensure(g, ppk, sizeof(unsigned long long) * Spp)) ||
-            (rc = ensure(g, ppi, sizeof(int) * Spp)) || (rc = ensure(g, tpk, sizeof(unsigned long long) * Stp)) ||
-            (rc = ensure(g, tpi, sizeof(int) * Stp)) || (rc = ensure(g, gord, sizeof(int) * G)) ||
-            (rc = ensure(g, tpg, sizeof(int) * T)) || (rc = ensure(g, ctl, 2 * sizeof(int))) ||
+        if ((rc = ensure(g, tkey, sizeof(unsigned long long) * slots)) || (rc = ensure(g, tidx, sizeof(int) * slots)) ||
+            (rc = ensure(g, tbase, sizeof(long long) * (G + 1))) ||
+            (rc = ensure(g, pw, sizeof(unsigned long long) * (LM + 1))) ||
+            (rc = ensure(g, ctl, sizeof(unsigned long long) * 2 + sizeof(int))) ||
+            (rc = ensure(g, indeg, sizeof(int) * P)) || (rc = ensure(g, in_off, sizeof(long long) * (P + 1))) ||
+            (rc = ensure(g, state, P)) || (rc = ensure(g, sel, sizeof(int) * T)) ||
             (rc = ensure(g, keep_len, sizeof(long long) * T)) ||
             (rc = ensure(g, keep_off, sizeof(long long) * (T + 1))) ||
-            (rc = ensure(g, keep_rank, sizeof(long long) * (T + 1))) ||
-            (rc = ensure(g, perm, sizeof(long long) * T)) ||
-            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(T + 1))))
+            (rc = ensure(g, keep_rank, sizeof(long long) * (T + 1))) || (rc = ensure(g, perm, sizeof(long long) * T)) ||
+            (rc = ensure(g, tpg, sizeof(int) * T)) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(std::max(P, T) + 1))))
             break;
-        if (cudaEventRecord(g->ev[10], s) || cudaMemsetAsync(cov.p, 0, P, s) ||
-            cudaMemsetAsync(sel.p, 0, sizeof(int) * T, s) ||
-            cudaMemsetAsync(ppk.p, 0, sizeof(unsigned long long) * Spp, s) ||
-            cudaMemsetAsync(tpk.p, 0, sizeof(unsigned long long) * Stp, s) ||
-            cudaMemsetAsync(ctl.p, 0, 2 * sizeof(int), s) ||
-            cudaMemcpyAsync(gord.p, order.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s)) {
-            rc = cuda_err(cudaGetLastError());
-            break;
-        }
-        const PathTable pp_tab{ppk.as<unsigned long long>(), ppi.as<int>(), Spp - 1};
-        const PathTable tp_tab{tpk.as<unsigned long long>(), tpi.as<int>(), Stp - 1};
+        unsigned long long *ecount = ctl.as<unsigned long long>(), *undecided = ecount + 1;
+        int *err = (int *)(ecount + 2);
         const long long *pp_off = (const long long *)g->pp_off->p;
         const int *pp_vert = (const int *)g->pp_vert->p;
         const int *pp_graph = g->pp_graph ? (const int *)g->pp_graph->p : nullptr;
-        if ((rc = cuda_err(tour_table_build(pp_tab, pp_off, pp_vert, pp_graph, nullptr, G, P, s))) ||
-            (rc = cuda_err(tour_graph_ids((const long long *)tgptr->p, G, T, tpg.as<int>(), s))) ||
-            (rc = cuda_err(tour_table_build(tp_tab, (const long long *)toff->p, (const int *)tvert->p, tpg.as<int>(),
-                                            nullptr, G, T, s))))
+        const PathTable tab{tkey.as<unsigned long long>(), tidx.as<int>(), tbase.as<long long>()};
+        if ((rc = cuda_err(cudaEventRecord(g->ev[10], s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(tbase.p, tb.data(), sizeof(long long) * (G + 1), cudaMemcpyHostToDevice,
+                                           s))) ||
+            (rc = cuda_err(cudaMemsetAsync(tkey.p, 0, sizeof(unsigned long long) * slots, s))) ||
+            (rc = cuda_err(tour_powers(pw.as<unsigned long long>(), LM, s))) ||
+            (rc = cuda_err(tour_table_build(tab, pp_off, pp_vert, pp_graph, P, s))))
             break;
-        TourArgs a{};
-        a.g = g->gd;
-        a.pp_off = pp_off;
-        a.pp_vert = pp_vert;
-        a.pp_gptr = (const long long *)g->pp_gptr->p;
-        a.pp_tab = pp_tab;
-        a.tp_off = (const long long *)toff->p;
-        a.tp_vert = (const int *)tvert->p;
-        a.tp_gptr = (const long long *)tgptr->p;
-        a.tp_tab = tp_tab;
-        a.gorder = gord.as<int>();
-        a.claim = ctl.as<int>();
-        a.err = ctl.as<int>() + 1;
-        a.ord = ord.as<int>();
-        a.cov = cov.as<unsigned char>();
-        a.sel = sel.as<int>();
-        a.maxn = g->maxn;
-        if ((rc = cuda_err(tour_greedy(a, G, warps, g->num_sms, s)))) break;
-        // the chosen TPs, in list order
+        // 1. cover edges (again with the exact edge count if the first guess was short)
+        long long E = 0;
+        for (int attempt = 0; attempt < 2 && rc == TPG_OK; ++attempt) {
+            if ((rc = ensure(g, edges, sizeof(int2) * edge_cap)) ||
+                (rc = cuda_err(cudaMemsetAsync(ctl.p, 0, sizeof(unsigned long long) * 2 + sizeof(int), s))))
+                break;
+            TourEdgeArgs a{};
+            a.g = g->gd;
+            a.pp_off = pp_off;
+            a.pp_vert = pp_vert;
+            a.pp_graph = pp_graph;
+            a.pp_gptr = (const long long *)g->pp_gptr->p;
+            a.P = P;
+            a.tab = tab;
+            a.pw = pw.as<unsigned long long>();
+            a.edges = edges.as<int2>();
+            a.edge_cap = edge_cap;
+            a.edge_count = ecount;
+            a.err = err;
+            a.maxn = g->maxn;
+            if ((rc = cuda_err(tour_edges(a, g->num_sms, &warps, s)))) break;
+            if ((rc = cuda_err(cudaMemcpyAsync(h, ecount, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(h + 1, err, sizeof(int), cudaMemcpyDeviceToHost, s))) ||
+                (rc = cuda_err(cudaStreamSynchronize(s))))
+                break;
+            E = h[0];
+            g->last_edges = E;
+            const int e = ((int *)(h + 1))[0];
+            if (e & ERR_UNREACH) { rc = TPG_EUNREACH; break; }
+            if (e) { rc = TPG_ECUDA; break; }
+            if (E <= edge_cap) break;
+            edge_cap = E;
+            if (attempt == 1) rc = TPG_ECUDA;
+        }
+        if (rc) break;
+        // 2. the edges by target
+        if ((rc = ensure(g, in_src, sizeof(int) * std::max<long long>(E, 1))) ||
+            (rc = cuda_err(cudaMemsetAsync(indeg.p, 0, sizeof(int) * P, s))) ||
+            (rc = cuda_err(tour_indegrees(edges.as<int2>(), E, indeg.as<int>(), s))) ||
+            (rc = cuda_err(scan_i32_to_i64(indeg.as<int>(), in_off.as<long long>(), P, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(tour_group_edges(edges.as<int2>(), E, in_off.as<long long>(), indeg.as<int>(),
+                                            in_src.as<int>(), s))))
+            break;
+        // 3. decision sweeps until every PP is chosen or covered
+        if ((rc = cuda_err(cudaMemsetAsync(state.p, 0, P, s)))) break;
+        for (;;) {
+            ++sweeps;
+            if ((rc = cuda_err(cudaMemsetAsync(undecided, 0, sizeof(unsigned long long), s))) ||
+                (rc = cuda_err(tour_sweep(in_off.as<long long>(), in_src.as<int>(), P, state.as<unsigned char>(),
+                                          undecided, s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(h, undecided, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+                (rc = cuda_err(cudaStreamSynchronize(s))))
+                break;
+            if (h[0] == 0) break;
+            if (sweeps > P) { rc = TPG_ECUDA; break; }  // every sweep decides a PP: cannot happen
+        }
+        if (rc) break;
+        // 4. the chosen TPs, in list order
         long long *klen = keep_len.as<long long>(), *koff = keep_off.as<long long>(), *krank = keep_rank.as<long long>();
-        if ((rc = cuda_err(tour_keep_lengths(sel.as<int>(), (const long long *)toff->p, T, klen, s))) ||
+        if ((rc = cuda_err(cudaMemsetAsync(sel.p, 0, sizeof(int) * T, s))) ||
+            (rc = cuda_err(tour_select(state.as<unsigned char>(), map, P, sel.as<int>(), s))) ||
+            (rc = cuda_err(tour_keep_lengths(sel.as<int>(), (const long long *)toff->p, T, klen, s))) ||
             (rc = cuda_err(scan_i64(klen, koff, T, tmp.as<long long>(), s))) ||
             (rc = cuda_err(scan_i32_to_i64(sel.as<int>(), krank, T, tmp.as<long long>(), s))) ||
-            (rc = cuda_err(tp_iota(perm.as<long long>(), T, s))))
+            (rc = cuda_err(tp_iota(perm.as<long long>(), T, s))) ||
+            (rc = cuda_err(tour_graph_ids((const long long *)tgptr->p, G, T, tpg.as<int>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(h, krank + T, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(h + 1, koff + T, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaStreamSynchronize(s))))
             break;
-        long long *h = (long long *)g->h_small;
-        if (cudaMemcpyAsync(h, krank + T, sizeof(long long), cudaMemcpyDeviceToHost, s) ||
-            cudaMemcpyAsync(h + 1, koff + T, sizeof(long long), cudaMemcpyDeviceToHost, s) ||
-            cudaMemcpyAsync(h + 2, a.err, sizeof(int), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s)) {
-            rc = cuda_err(cudaGetLastError());
-            break;
-        }
         T2 = h[0];
         TV2 = h[1];
-        const int err = ((int *)(h + 2))[0];
-        if (err & ERR_UNREACH) { rc = TPG_EUNREACH; break; }
-        if (err) { rc = TPG_ECUDA; break; }  // a TP or PP the touring built was not in its list
         f_off = block_new(g->fns, sizeof(long long) * (T2 + 1), s);
         f_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV2, 1), s);
         f_gptr = block_new(g->fns, sizeof(long long) * (G + 1), s);
@@ -1859,19 +1894,18 @@ static int run_touring(tpg_cfg *g, Block *toff, Block *tvert, Block *tgptr, long
                                      (int *)f_vert->p, fgraph.as<int>(), s))) ||
             (rc = cuda_err(cudaMemcpyAsync((long long *)f_off->p + T2, h + 3, sizeof(long long),
                                            cudaMemcpyHostToDevice, s))) ||
-            (rc = cuda_err(graph_ptr_from_ids(fgraph.as<int>(), T2, G, (long long *)f_gptr->p, s))))
+            (rc = cuda_err(graph_ptr_from_ids(fgraph.as<int>(), T2, G, (long long *)f_gptr->p, s))) ||
+            (rc = cuda_err(cudaEventRecord(g->ev[11], s))) || (rc = cuda_err(cudaStreamSynchronize(s))))
             break;
-        if (cudaEventRecord(g->ev[11], s) || cudaStreamSynchronize(s)) {
-            rc = cuda_err(cudaGetLastError());
-            break;
-        }
         cudaEventElapsedTime(&g->stats.t_touring_ms, g->ev[10], g->ev[11]);
-        g->stats.touring_warps = warps;
+        g->stats.touring_sweeps = sweeps;
         g->stats.touring_test_paths = T2;
+        g->stats.touring_edges = E;
+        (void)warps;
     } while (false);
     if (rc != TPG_OK) cudaStreamSynchronize(s);  // nothing of this call left in flight on the scratch
-    for (DevBuf *b : {&ord, &cov, &sel, &ppk, &ppi, &tpk, &tpi, &gord, &tpg, &ctl, &keep_len, &keep_off, &keep_rank,
-                      &perm, &tmp, &fgraph})
+    for (DevBuf *b : {&tkey, &tidx, &tbase, &pw, &ctl, &edges, &indeg, &in_off, &in_src, &state, &sel, &keep_len, &keep_off,
+                      &keep_rank, &perm, &tmp, &tpg, &fgraph})
         release(g, *b);
     if (rc == TPG_OK) rc = make_result(g, f_off, f_vert, f_gptr, T2, TV2, out);
     block_unref(f_off);
@@ -1884,13 +1918,17 @@ int tpg_test_paths_greedy(tpg_cfg *g, tpg_paths **out) {
     if (!out) return TPG_EINVAL;
     *out = nullptr;
     if (!is_cfg(g)) return TPG_EHANDLE;
+    if (!g->pp_valid) RC(run_prime_paths(g));
+    DevBuf map;
+    RC(ensure(g, map, sizeof(int) * std::max<long long>(g->P, 1)));
     Block *off = nullptr, *vert = nullptr, *gptr = nullptr;
     long long T = 0, TV = 0;
-    RC(run_test_paths(g, &off, &vert, &gptr, &T, &TV));
-    const int rc = run_touring(g, off, vert, gptr, T, TV, out);
+    int rc = run_test_paths(g, &off, &vert, &gptr, &T, &TV, map.as<int>());
+    if (rc == TPG_OK) rc = run_touring(g, off, vert, gptr, T, TV, map.as<int>(), out);
     block_unref(off);
     block_unref(vert);
     block_unref(gptr);
+    release(g, map);
     return rc;
 }
 

@@ -324,6 +324,23 @@ cudaError_t tp_dedup_flags_keys(const long long *perm, long long P, const long l
     return cudaGetLastError();
 }
 
+__global__ void index_map_kernel(const long long *perm, const int *keep, const long long *keep_rank, long long P,
+                                 int *map) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!perm) map[i] = (int)i;
+        else map[perm[i]] = (int)(keep[i] ? keep_rank[i] : keep_rank[i] - 1);
+    }
+}
+
+cudaError_t tp_index_map(const long long *perm, const int *keep, const long long *keep_rank, long long P, int *map,
+                         cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    index_map_kernel<<<grid_for(P), 256, 0, s>>>(perm, keep, keep_rank, P, map);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // one warp per kept TP: copy into its final slot
 __global__ void tp_gather_kernel(const long long *perm, const int *keep, const long long *keep_rank, long long P,
                                  const long long *off, const int *vert, const int *graph,

@@ -33,4 +33,10 @@ cudaError_t tp_dedup_flags_keys(const long long *perm, long long P, const long l
                                 const unsigned long long *key, const int *tp_graph, long long *keep_len, int *keep,
                                 cudaStream_t s);
 
+// map[perm[i]] = the final index of sorted TP i (keep_rank[i] if it is kept,
+// else that of the kept TP it duplicates, keep_rank[i] - 1); with perm null
+// the identity map[i] = i
+cudaError_t tp_index_map(const long long *perm, const int *keep, const long long *keep_rank, long long P, int *map,
+                         cudaStream_t s);
+
 }  // namespace tpg

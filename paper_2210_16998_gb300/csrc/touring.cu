@@ -6,28 +6,32 @@
 // is TP(p) of the one-per-PP construction (lowest-id BFS prefix and suffix),
 // a PP is covered when it is a contiguous subpath of a chosen TP, equal
 // lengths go in canonical order, and the chosen TPs are returned in canonical
-// order -- so the result is a subset of the one-per-PP TP list.
+// order -- a subset of the one-per-PP TP list.
 //
-// GPU design.  The rule is sequential inside a graph, so graphs run in
-// parallel: persistent blocks claim whole graphs, those with the most PPs
-// first.  A block orders its graph's PPs longest first (counting sort on the
-// length, stable) and then runs rounds.  In a round warp 0 collects the next
-// NW uncovered PPs in that order; every warp builds its candidate's TP in
-// shared memory and finds the PPs that are windows of it; thread 0 takes the
-// candidates in order and keeps each one that no kept candidate of the round
-// covers -- the sequential rule exactly, since the candidates follow each
-// other in the greedy order among the uncovered PPs -- and the warps of the
-// kept candidates mark what their TPs cover.
+// The rule reads sequentially (a PP's turn depends on the TPs chosen before
+// it), but its outcome has a description that parallelises: in the order
+// (longer first, then canonical), p is chosen iff no chosen PP before p
+// covers p with its TP.  So, over all graphs at once:
+//  1. every PP p (a warp each) builds TP(p) in shared memory, finds the PPs
+//     that are windows of it, and emits an edge p -> q for each such q that
+//     comes after p in the order;
+//  2. the edges are grouped by target;
+//  3. sweeps decide the PPs: q is covered once a chosen source reaches it,
+//     and chosen once all its sources are covered (or it has none).  The
+//     first undecided PP in the order has only decided sources, so each
+//     sweep decides at least one PP; sweeps repeat until none is left;
+//  4. the chosen PPs' TPs are taken from the one-per-PP TP list.
 //
 // Which windows of a TP t can be PPs: a PP q at position i of t is the
 // longest window t[i..j] that is a simple path (a simple t[i..j+1] would
 // extend an acyclic q; a cycle q ends where t[i] comes back).  With nxt[k]
-// the next position of t[k]'s vertex after k, and S(i) the minimum of nxt
-// over [i, L): if nxt[i] < S(i+1) the window is the cycle t[i..nxt[i]],
-// else t[i..S(i)-1] (t[i..L-1] when nothing repeats).  t is a prefix path, p
-// and a suffix path, each simple, so nxt comes from two per-vertex position
-// tables (of p's part and of the suffix part).  Each window is looked up in
-// an open-addressing hash table of the PP list and checked vertex by vertex.
+// the next position of t[k]'s vertex after k and S(i) the minimum of nxt over
+// [i, L): if S(i) < S(i+1) (then S(i) = nxt[i]) the window is the cycle
+// t[i..S(i)], else t[i..S(i)-1] (t[i..L-1] when nothing repeats).  t is a
+// prefix path, p and a suffix path, each simple, so nxt comes from two
+// per-vertex position tables (of p's part and of the suffix part).  Each
+// window's hash comes from prefix hashes of t in O(1); it is looked up in an
+// open-addressing table of the PP list and checked vertex by vertex.
 #include <algorithm>
 
 #include "common.cuh"
@@ -38,8 +42,13 @@ namespace tpg {
 
 namespace {
 
-constexpr int TOUR_MAXW = 16;
+constexpr int TOUR_WARPS = 8;  // warps per block of the edge launch (fewer if shared memory is short)
 constexpr unsigned TOUR_INF = 0xFFFFu;
+// polynomial hash of a sequence: raw = sum (s_k + 1) B^(len-1-k) mod 2^64,
+// key = MurmurHash3's 64-bit finaliser of raw mixed with graph and length
+constexpr unsigned long long HB = 0x9E3779B97F4A7C15ull;
+constexpr unsigned long long HG = 0xD6E8FEB86659FD93ull;
+constexpr unsigned long long HL = 0xA0761D6478BD642Full;
 
 unsigned grid_for(long long n, int block = 256) {
     long long b = (n + block - 1) / block;
@@ -48,15 +57,8 @@ unsigned grid_for(long long n, int block = 256) {
     return (unsigned)b;
 }
 
-// (graph, local vertex sequence) -> 64-bit key, never 0: FNV-style mixing of
-// each vertex, then the MurmurHash3 64-bit finaliser
-__device__ __forceinline__ unsigned long long hash_begin(int gid) {
-    return 0xcbf29ce484222325ull ^ ((unsigned long long)(unsigned)gid * 0x9E3779B97F4A7C15ull);
-}
-__device__ __forceinline__ unsigned long long hash_step(unsigned long long h, int v) {
-    return (h ^ (unsigned long long)(unsigned)(v + 1)) * 0x100000001b3ull;
-}
-__device__ __forceinline__ unsigned long long hash_end(unsigned long long h) {
+__device__ __forceinline__ unsigned long long hash_key(unsigned long long raw, int gid, int len) {
+    unsigned long long h = raw ^ ((unsigned long long)(unsigned)(gid + 1) * HG) ^ ((unsigned long long)len * HL);
     h ^= h >> 33;
     h *= 0xff51afd7ed558ccdull;
     h ^= h >> 33;
@@ -65,289 +67,258 @@ __device__ __forceinline__ unsigned long long hash_end(unsigned long long h) {
     return h ? h : 1ull;
 }
 
-// index in [lo, hi) of the path equal to s[0..len) (graph gid), or -1
-template <typename T>
-__device__ long long table_find(const PathTable &tab, const long long *off, const int *vert, long long lo,
-                                long long hi, int gid, const T *s, int len) {
-    unsigned long long h = hash_begin(gid);
-    for (int k = 0; k < len; ++k) h = hash_step(h, (int)s[k]);
-    h = hash_end(h);
-    long long j = (long long)(h & (unsigned long long)tab.mask);
-    for (long long probes = 0; probes <= tab.mask; ++probes, j = (j + 1) & tab.mask) {
-        const unsigned long long k = tab.key[j];
-        if (k == 0ull) return -1;
-        if (k != h) continue;
-        const long long i = tab.idx[j];
-        if (i < lo || i >= hi) continue;
-        const long long o = off[i];
-        if (off[i + 1] - o != len) continue;
-        int e = 0;
-        while (e < len && vert[o + e] == (int)s[e]) ++e;
-        if (e == len) return i;
+// v[0..len) == s[0..len), eight independent loads at a time
+__device__ __forceinline__ bool same_seq(const int *v, const unsigned short *s, int len) {
+    int e = 0;
+    for (; e + 8 <= len; e += 8) {
+        int x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = v[e + u];
+        bool ok = true;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ok &= x[u] == (int)s[e + u];
+        if (!ok) return false;
     }
-    return -1;
+    for (; e < len; ++e)
+        if (v[e] != (int)s[e]) return false;
+    return true;
 }
 
-__device__ __forceinline__ int graph_of_index(const long long *gptr, int G, long long i) {
-    int lo = 0, hi = G;  // the last g with gptr[g] <= i
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (gptr[mid] <= i) lo = mid;
-        else hi = mid;
+__global__ void powers_kernel(unsigned long long *pw, int n) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long x = 1ull;
+        for (int k = 0; k <= n; ++k) {
+            pw[k] = x;
+            x *= HB;
+        }
     }
-    return lo;
 }
 
 __global__ void table_build_kernel(PathTable t, const long long *off, const int *vert, const int *graph_of,
-                                   const long long *gptr, int G, long long n) {
+                                   long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int gid = graph_of ? graph_of[i] : (gptr ? graph_of_index(gptr, G, i) : 0);
-        const long long o = off[i], len = off[i + 1] - o;
-        unsigned long long h = hash_begin(gid);
-        for (long long k = 0; k < len; ++k) h = hash_step(h, vert[o + k]);
-        h = hash_end(h);
-        long long j = (long long)(h & (unsigned long long)t.mask);
-        for (long long probes = 0; probes <= t.mask; ++probes, j = (j + 1) & t.mask) {
-            if (atomicCAS(t.key + j, 0ull, h) == 0ull) {
-                t.idx[j] = (int)i;
+        const long long o = off[i];
+        const int len = (int)(off[i + 1] - o);
+        unsigned long long raw = 0ull;
+        for (int k = 0; k < len; ++k) raw = raw * HB + (unsigned long long)(unsigned)(vert[o + k] + 1);
+        const int gid = graph_of ? graph_of[i] : 0;
+        const unsigned long long h = hash_key(raw, gid, len);
+        const long long t0 = t.tbase[gid], mask = t.tbase[gid + 1] - t0 - 1;
+        long long j = (long long)(h & (unsigned long long)mask);
+        for (long long probes = 0; probes <= mask; ++probes, j = (j + 1) & mask) {
+            if (atomicCAS(t.key + t0 + j, 0ull, h) == 0ull) {
+                t.idx[t0 + j] = (int)i;
                 break;
             }
         }
     }
 }
 
-__global__ void graph_ids_kernel(const long long *gptr, int G, long long n, int *ids) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        ids[i] = graph_of_index(gptr, G, i);
-}
-
-// shared memory: [block] hist, cursor (maxn + 3 ints each); [per warp] t,
-// nxt, S (LM u16 each), posP, posB (maxn shorts each), cover list (LM ints)
+// shared memory of one warp: t (u16), S (u16), hit list (int), position
+// tables of p's part and of the suffix part (short), prefix hashes (u64)
 struct TourLayout {
-    size_t block_bytes, warp_bytes, o_nxt, o_s, o_posp, o_posb, o_cover;
+    size_t warp_bytes, o_s, o_hit, o_posp, o_posb, o_pf;
     int lm;
 };
 __host__ __device__ inline TourLayout tour_layout(int maxn) {
     TourLayout l;
     l.lm = 3 * maxn + 2;
     const size_t LM = (size_t)l.lm;
-    l.block_bytes = (2 * sizeof(int) * (size_t)(maxn + 3) + 15) & ~(size_t)15;
-    l.o_nxt = LM * sizeof(unsigned short);
-    l.o_s = 2 * LM * sizeof(unsigned short);
-    l.o_posp = 3 * LM * sizeof(unsigned short);
+    l.o_s = (LM * sizeof(unsigned short) + 15) & ~(size_t)15;
+    l.o_hit = l.o_s + ((LM * sizeof(unsigned short) + 15) & ~(size_t)15);
+    l.o_posp = l.o_hit + ((LM * sizeof(int) + 15) & ~(size_t)15);
     l.o_posb = l.o_posp + (size_t)maxn * sizeof(short);
-    l.o_cover = (l.o_posb + (size_t)maxn * sizeof(short) + 15) & ~(size_t)15;
-    l.warp_bytes = (l.o_cover + LM * sizeof(int) + 15) & ~(size_t)15;
+    l.o_pf = (l.o_posb + (size_t)maxn * sizeof(short) + 15) & ~(size_t)15;
+    l.warp_bytes = (l.o_pf + (LM + 1) * sizeof(unsigned long long) + 15) & ~(size_t)15;
     return l;
 }
 
-__global__ void __launch_bounds__(32 * TOUR_MAXW) tour_greedy_kernel(TourArgs a, int G, int NW) {
+__global__ void __launch_bounds__(32 * TOUR_WARPS) tour_edges_kernel(TourEdgeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_cand[TOUR_MAXW];
-    __shared__ unsigned s_M[TOUR_MAXW];
-    __shared__ int s_ncov[TOUR_MAXW];
-    __shared__ int s_ncand, s_cur, s_graph;
-    __shared__ unsigned s_picked;
+    __shared__ int s_nhit[TOUR_WARPS];
     const GraphDev &g = a.g;
     const int maxn = a.maxn;
     const TourLayout lay = tour_layout(maxn);
     const int LM = lay.lm;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    int *hist = (int *)smem;
-    int *cursor = hist + (maxn + 3);
-    unsigned char *wb = smem + lay.block_bytes + (size_t)wid * lay.warp_bytes;
+    unsigned char *wb = smem + (size_t)wid * lay.warp_bytes;
     unsigned short *t = (unsigned short *)wb;
-    unsigned short *nxt = (unsigned short *)(wb + lay.o_nxt);
-    unsigned short *Sm = (unsigned short *)(wb + lay.o_s);
+    unsigned short *S = (unsigned short *)(wb + lay.o_s);
+    int *hit = (int *)(wb + lay.o_hit);
     short *posP = (short *)(wb + lay.o_posp);
     short *posB = (short *)(wb + lay.o_posb);
-    int *cover = (int *)(wb + lay.o_cover);
+    unsigned long long *Pf = (unsigned long long *)(wb + lay.o_pf);
     for (int i = lane; i < maxn; i += 32) posP[i] = posB[i] = -1;
-
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int c = atomicAdd(a.claim, 1);
-            s_graph = c < G ? a.gorder[c] : -1;
-        }
-        __syncthreads();
-        const int gi = s_graph;
-        if (gi < 0) break;
-        const long long base = a.pp_gptr[gi];
-        const int Pg = (int)(a.pp_gptr[gi + 1] - base);
-        if (Pg <= 0) continue;
+    __syncwarp();
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long p = blockIdx.x * (long long)(blockDim.x >> 5) + wid; p < a.P; p += nw) {
+        const int gi = a.pp_graph ? a.pp_graph[p] : 0;
+        const long long lo = a.pp_gptr[gi], hi = a.pp_gptr[gi + 1];
         const int vb = g.vbase[gi];
-        const long long tlo = a.tp_gptr[gi], thi = a.tp_gptr[gi + 1];
-
-        // ---- the graph's PPs, longest first (stable counting sort) ----
-        for (int i = threadIdx.x; i < maxn + 3; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
-        for (int i = threadIdx.x; i < Pg; i += blockDim.x) {
-            const long long len = a.pp_off[base + i + 1] - a.pp_off[base + i];
-            atomicAdd(&hist[len < 0 ? 0 : (len > maxn + 1 ? maxn + 1 : (int)len)], 1);
+        const long long t0 = a.tab.tbase[gi], tmask = a.tab.tbase[gi + 1] - t0 - 1;
+        const unsigned long long *tkey = a.tab.key + t0;
+        const int *tidx = a.tab.idx + t0;
+        const long long po = a.pp_off[p];
+        const int plen = (int)(a.pp_off[p + 1] - po);
+        const int *pv = a.pp_vert + po;
+        const int f = plen > 0 ? pv[0] : 0, l = plen > 0 ? pv[plen - 1] : 0;
+        const int pl = g.pre_len[vb + f], sl = g.suf_len[vb + l];
+        if (plen < 1 || pl == 0 || sl == 0 || pl - 1 + plen + sl - 1 > LM) {
+            if (lane == 0) atomicOr(a.err, (plen >= 1 && (pl == 0 || sl == 0)) ? ERR_UNREACH : ERR_INVAL);
+            continue;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int l = maxn + 1; l >= 0; --l) {
-                cursor[l] = run;
-                run += hist[l];
-            }
-            s_cur = 0;
+        const int A = pl - 1, L = A + plen + sl - 1;
+        // TP(p): the prefix path without its last vertex (p's first), p, the
+        // suffix path without its first vertex (p's last)
+        const int *pre = g.pre_seq + g.pre_off[vb + f];
+        const int *suf = g.suf_seq + g.suf_off[vb + l];
+        for (int k = lane; k < L; k += 32)
+            t[k] = (unsigned short)(k < A ? pre[k] : (k < A + plen ? pv[k - A] : suf[k - A - plen + 1]));
+        __syncwarp();
+        const bool cyc = plen > 1 && t[A] == t[A + plen - 1];
+        for (int k = A + lane; k < L; k += 32) {
+            if (k >= A + plen) posB[t[k]] = (short)k;
+            else if (!(cyc && k == A + plen - 1)) posP[t[k]] = (short)k;
         }
-        __syncthreads();
-        if (wid == 0) {
-            for (int i0 = 0; i0 < Pg; i0 += 32) {
-                const int i = i0 + lane;
-                int len = -1;
-                if (i < Pg) {
-                    const long long l = a.pp_off[base + i + 1] - a.pp_off[base + i];
-                    len = l < 0 ? 0 : (l > maxn + 1 ? maxn + 1 : (int)l);
-                }
-                const unsigned peers = __match_any_sync(0xffffffffu, len);
-                const int rank = __popc(peers & lt_mask);
-                const int pos = i < Pg ? cursor[len] + rank : 0;
-                __syncwarp();
-                if (i < Pg && rank == 0) cursor[len] += __popc(peers);
-                __syncwarp();
-                if (i < Pg) a.ord[base + pos] = i;
+        __syncwarp();
+        // nxt into S, then S = suffix minimum, chunk by chunk from the end
+        unsigned carry = TOUR_INF;
+        for (int c = (L - 1) >> 5; c >= 0; --c) {
+            const int k = c * 32 + lane;
+            unsigned x = TOUR_INF;
+            if (k < L) {
+                const int v = t[k];
+                if (k < A) x = posP[v] >= 0 ? (unsigned)posP[v] : (posB[v] >= 0 ? (unsigned)posB[v] : TOUR_INF);
+                else if (k < A + plen)
+                    x = (cyc && k == A) ? (unsigned)(A + plen - 1) : (posB[v] >= 0 ? (unsigned)posB[v] : TOUR_INF);
             }
-        }
-        __syncthreads();
-
-        // ---- rounds of up to NW candidates ----
-        for (;;) {
-            if (wid == 0) {
-                int got = 0, i0 = s_cur, last = -1;
-                while (got < NW && i0 < Pg) {
-                    const int i = i0 + lane;
-                    const int q = i < Pg ? a.ord[base + i] : -1;
-                    const bool unc = q >= 0 && !a.cov[base + q];
-                    const unsigned m = __ballot_sync(0xffffffffu, unc);
-                    unsigned take = m;
-                    for (int extra = __popc(m) - (NW - got); extra > 0; --extra)
-                        take &= ~(1u << (31 - __clz(take)));  // keep the lowest NW - got
-                    if (take & (1u << lane)) s_cand[got + __popc(take & lt_mask)] = q;
-                    if (take) last = i0 + 31 - __clz(take);
-                    got += __popc(take);
-                    i0 += 32;
-                }
-                if (lane == 0) {
-                    s_ncand = got;
-                    s_cur = got == NW ? last + 1 : Pg;
-                }
-            }
-            __syncthreads();
-            const int nc = s_ncand;
-            if (nc == 0) break;
-
-            int A = 0, plen = 0, L = 0;
-            if (wid < nc) {
-                const int q = s_cand[wid];
-                const long long po = a.pp_off[base + q];
-                plen = (int)(a.pp_off[base + q + 1] - po);
-                const int *pv = a.pp_vert + po;
-                const int f = plen > 0 ? pv[0] : 0, l = plen > 0 ? pv[plen - 1] : 0;
-                const int pl = g.pre_len[vb + f], sl = g.suf_len[vb + l];
-                if (plen < 1 || pl == 0 || sl == 0 || pl - 1 + plen + sl - 1 > LM) {
-                    if (lane == 0) atomicOr(a.err, (pl == 0 || sl == 0) ? ERR_UNREACH : ERR_INVAL);
-                    plen = 0;
-                } else {
-                    A = pl - 1;
-                    L = A + plen + sl - 1;
-                }
-                // TP(p): prefix path (without its last vertex, p's first), p,
-                // suffix path (without its first vertex, p's last)
-                const int *pre = g.pre_seq + g.pre_off[vb + f];
-                const int *suf = g.suf_seq + g.suf_off[vb + l];
-                for (int k = lane; k < L; k += 32)
-                    t[k] = (unsigned short)(k < A ? pre[k] : (k < A + plen ? pv[k - A] : suf[k - A - plen + 1]));
-                __syncwarp();
-                const bool cyc = plen > 1 && t[A] == t[A + plen - 1];
-                for (int k = A + lane; k < L; k += 32) {
-                    if (k >= A + plen) posB[t[k]] = (short)k;
-                    else if (!(cyc && k == A + plen - 1)) posP[t[k]] = (short)k;
-                }
-                __syncwarp();
-                for (int k = lane; k < L; k += 32) {
-                    const int v = t[k];
-                    unsigned x = TOUR_INF;
-                    if (k < A) x = posP[v] >= 0 ? (unsigned)posP[v] : (posB[v] >= 0 ? (unsigned)posB[v] : TOUR_INF);
-                    else if (k < A + plen) x = (cyc && k == A) ? (unsigned)(A + plen - 1)
-                                                               : (posB[v] >= 0 ? (unsigned)posB[v] : TOUR_INF);
-                    nxt[k] = (unsigned short)x;
-                }
-                __syncwarp();
-                // S = suffix minimum of nxt
-                unsigned carry = TOUR_INF;
-                for (int c = (L - 1) >> 5; c >= 0; --c) {
-                    const int k = c * 32 + lane;
-                    unsigned x = k < L ? nxt[k] : TOUR_INF;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const unsigned y = __shfl_down_sync(0xffffffffu, x, o);
-                        if (lane + o < 32) x = min(x, y);
-                    }
-                    x = min(x, carry);
-                    if (k < L) Sm[k] = (unsigned short)x;
-                    carry = __shfl_sync(0xffffffffu, x, 0);
-                }
-                if (lane == 0) s_ncov[wid] = 0;
-                __syncwarp();
-                // the one candidate window per start position, looked up
-                unsigned mine = 0;
-                for (int i = lane; i < L; i += 32) {
-                    const unsigned sn = i + 1 < L ? Sm[i + 1] : TOUR_INF;
-                    int e;
-                    if (nxt[i] < sn) e = nxt[i];
-                    else e = Sm[i] >= (unsigned)L ? L - 1 : (int)Sm[i] - 1;
-                    const long long r = table_find(a.pp_tab, a.pp_off, a.pp_vert, base, base + Pg, gi, t + i, e - i + 1);
-                    if (r >= 0) {
-                        const int qq = (int)(r - base);
-                        cover[atomicAdd(&s_ncov[wid], 1)] = qq;
-                        for (int c = 0; c < nc; ++c)
-                            if (s_cand[c] == qq) mine |= 1u << c;
-                    }
-                }
-                mine = __reduce_or_sync(0xffffffffu, mine);
-                if (lane == 0) {
-                    // TP(p) holds p: its own bit is set (and forced, so that
-                    // every round covers its first candidate)
-                    if (plen && !(mine & (1u << wid))) atomicOr(a.err, ERR_INVAL);
-                    s_M[wid] = mine | (1u << wid);
-                }
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_down_sync(0xffffffffu, x, o);
+                if (lane + o < 32) x = min(x, y);
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned covm = 0, picked = 0;
-                for (int c = 0; c < nc; ++c)
-                    if (!((covm >> c) & 1u)) {
-                        picked |= 1u << c;
-                        covm |= s_M[c];
-                    }
-                s_picked = picked;
-            }
-            __syncthreads();
-            if (wid < nc) {
-                if ((s_picked >> wid) & 1u) {
-                    const int n = s_ncov[wid];
-                    for (int j = lane; j < n; j += 32) a.cov[base + cover[j]] = 1;
-                    if (lane == 0) {
-                        a.cov[base + s_cand[wid]] = 1;
-                        if (L > 0) {
-                            const long long r = table_find(a.tp_tab, a.tp_off, a.tp_vert, tlo, thi, gi, t, L);
-                            if (r >= 0) a.sel[r] = 1;
-                            else atomicOr(a.err, ERR_INVAL);
-                        }
-                    }
-                }
-                for (int k = A + lane; k < L; k += 32) posP[t[k]] = posB[t[k]] = -1;
-            }
-            __syncthreads();
+            x = min(x, carry);
+            if (k < L) S[k] = (unsigned short)x;
+            carry = __shfl_sync(0xffffffffu, x, 0);
         }
+        // prefix hashes Pf[k] = raw(t[0..k)), chunk by chunk: the affine
+        // maps x -> x B + (t[k] + 1) composed with a warp scan
+        unsigned long long run = 0ull;
+        for (int c = 0; c * 32 < L; ++c) {
+            const int k = c * 32 + lane;
+            unsigned long long m = k < L ? HB : 1ull, b = k < L ? (unsigned long long)(t[k] + 1u) : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long m0 = __shfl_up_sync(0xffffffffu, m, o);
+                const unsigned long long b0 = __shfl_up_sync(0xffffffffu, b, o);
+                if (lane >= o) {
+                    b = b0 * m + b;
+                    m = m0 * m;
+                }
+            }
+            const unsigned long long v = run * m + b;
+            if (k < L) Pf[k + 1] = v;
+            run = __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) {
+            Pf[0] = 0ull;
+            s_nhit[wid] = 0;
+        }
+        __syncwarp();
+        // the one possible PP per start position, looked up
+        for (int i = lane; i < L; i += 32) {
+            const unsigned si = S[i], sn = i + 1 < L ? S[i + 1] : TOUR_INF;
+            const int e = si < sn ? (int)si : (si >= (unsigned)L ? L - 1 : (int)si - 1);
+            const int len = e - i + 1;
+            const unsigned long long raw = Pf[e + 1] - Pf[i] * a.pw[len];
+            const unsigned long long h = hash_key(raw, gi, len);
+            long long j = (long long)(h & (unsigned long long)tmask);
+            for (long long probes = 0; probes <= tmask; ++probes, j = (j + 1) & tmask) {
+                const unsigned long long kj = tkey[j];
+                if (kj == 0ull) break;
+                if (kj != h) continue;
+                const long long q = tidx[j];
+                if (q < lo || q >= hi) continue;
+                const long long qo = a.pp_off[q];
+                if (a.pp_off[q + 1] - qo != len || !same_seq(a.pp_vert + qo, t + i, len)) continue;
+                // q comes after p: shorter, or as long and later in canonical order
+                if (len < plen || (len == plen && q > p)) hit[atomicAdd(&s_nhit[wid], 1)] = (int)q;
+                break;
+            }
+        }
+        __syncwarp();
+        const int n = s_nhit[wid];
+        if (n > 0) {
+            unsigned long long e0 = 0;
+            if (lane == 0) e0 = atomicAdd(a.edge_count, (unsigned long long)n);
+            e0 = __shfl_sync(0xffffffffu, e0, 0);
+            for (int j = lane; j < n; j += 32)
+                if ((long long)(e0 + j) < a.edge_cap) a.edges[e0 + j] = make_int2((int)p, hit[j]);
+        }
+        for (int k = A + lane; k < L; k += 32) posP[t[k]] = posB[t[k]] = -1;
+        __syncwarp();
+    }
+}
+
+__global__ void indeg_kernel(const int2 *edges, long long E, int *indeg) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < E;
+         k += (long long)gridDim.x * blockDim.x)
+        atomicAdd(indeg + edges[k].y, 1);
+}
+
+__global__ void group_kernel(const int2 *edges, long long E, const long long *in_off, int *indeg, int *in_src) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < E;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int2 e = edges[k];
+        in_src[in_off[e.y] + atomicSub(indeg + e.y, 1) - 1] = e.x;
+    }
+}
+
+__global__ void sweep_kernel(const long long *in_off, const int *in_src, long long P, unsigned char *state,
+                             unsigned long long *undecided) {
+    __shared__ unsigned s_left;
+    if (threadIdx.x == 0) s_left = 0;
+    __syncthreads();
+    unsigned left = 0;
+    volatile unsigned char *st = state;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P;
+         q += (long long)gridDim.x * blockDim.x) {
+        if (st[q]) continue;
+        bool chosen_src = false, all_done = true;
+        for (long long k = in_off[q], k1 = in_off[q + 1]; k < k1; ++k) {
+            const unsigned char s = st[in_src[k]];
+            if (s == 1) {
+                chosen_src = true;
+                break;
+            }
+            if (s == 0) all_done = false;
+        }
+        if (chosen_src) st[q] = 2;
+        else if (all_done) st[q] = 1;
+        else ++left;
+    }
+    if (left) atomicAdd(&s_left, left);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_left) atomicAdd(undecided, (unsigned long long)s_left);
+}
+
+__global__ void select_kernel(const unsigned char *state, const int *map, long long P, int *sel) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P;
+         q += (long long)gridDim.x * blockDim.x)
+        if (state[q] == 1) sel[map[q]] = 1;
+}
+
+__global__ void graph_ids_kernel(const long long *gptr, int G, long long n, int *ids) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = G;  // the last graph g with gptr[g] <= i
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (gptr[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        ids[i] = lo;
     }
 }
 
@@ -359,16 +330,83 @@ __global__ void keep_lengths_kernel(const int *sel, const long long *off, long l
 
 }  // namespace
 
-long long tour_table_slots(long long n) {
-    long long s = 1024;
-    while (s < 2 * n) s *= 2;
-    return s;
+long long tour_table_layout(const long long *gptr, int G, long long *tbase) {
+    tbase[0] = 0;
+    for (int g = 0; g < G; ++g) {
+        long long sz = 16;
+        while (sz < 2 * (gptr[g + 1] - gptr[g])) sz *= 2;
+        tbase[g + 1] = tbase[g] + sz;
+    }
+    return tbase[G];
 }
 
-cudaError_t tour_table_build(PathTable t, const long long *off, const int *vert, const int *graph_of,
-                             const long long *gptr, int G, long long n, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    table_build_kernel<<<grid_for(n), 256, 0, s>>>(t, off, vert, graph_of, gptr, G, n);
+int tour_max_tp(int maxn) { return 3 * maxn + 2; }
+
+cudaError_t tour_powers(unsigned long long *pw, int n, cudaStream_t s) {
+    powers_kernel<<<1, 32, 0, s>>>(pw, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tour_table_build(PathTable t, const long long *off, const int *vert, const int *graph_of, long long P,
+                             cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    table_build_kernel<<<grid_for(P), 256, 0, s>>>(t, off, vert, graph_of, P);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tour_edges(const TourEdgeArgs &a, int num_sms, int *warps_out, cudaStream_t s) {
+    if (a.P <= 0) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const TourLayout lay = tour_layout(a.maxn);
+    int warps = TOUR_WARPS;
+    while (warps > 1 && (size_t)warps * lay.warp_bytes + 1024 > (size_t)optin) --warps;
+    if ((size_t)warps * lay.warp_bytes + 1024 > (size_t)optin) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)warps * lay.warp_bytes;
+    e = cudaFuncSetAttribute(tour_edges_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tour_edges_kernel, 32 * warps, smem);
+    if (e != cudaSuccess) return e;
+    const long long need = (a.P + warps - 1) / warps;
+    const long long grid =
+        std::max(1LL, std::min<long long>(need, (long long)std::max(per_sm, 1) * std::max(num_sms, 1)));
+    tour_edges_kernel<<<(unsigned)grid, 32 * warps, smem, s>>>(a);
+    note_launch();
+    if (warps_out) *warps_out = warps;
+    return cudaGetLastError();
+}
+
+cudaError_t tour_indegrees(const int2 *edges, long long E, int *indeg, cudaStream_t s) {
+    if (E <= 0) return cudaSuccess;
+    indeg_kernel<<<grid_for(E), 256, 0, s>>>(edges, E, indeg);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tour_group_edges(const int2 *edges, long long E, const long long *in_off, int *indeg, int *in_src,
+                             cudaStream_t s) {
+    if (E <= 0) return cudaSuccess;
+    group_kernel<<<grid_for(E), 256, 0, s>>>(edges, E, in_off, indeg, in_src);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tour_sweep(const long long *in_off, const int *in_src, long long P, unsigned char *state,
+                       unsigned long long *undecided, cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    sweep_kernel<<<grid_for(P), 256, 0, s>>>(in_off, in_src, P, state, undecided);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tour_select(const unsigned char *state, const int *map, long long P, int *sel, cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    select_kernel<<<grid_for(P), 256, 0, s>>>(state, map, P, sel);
     note_launch();
     return cudaGetLastError();
 }
@@ -384,32 +422,6 @@ cudaError_t tour_keep_lengths(const int *sel, const long long *off, long long n,
                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     keep_lengths_kernel<<<grid_for(n), 256, 0, s>>>(sel, off, n, keep_len);
-    note_launch();
-    return cudaGetLastError();
-}
-
-size_t tour_smem_bytes(int maxn, int warps) {
-    const TourLayout l = tour_layout(maxn);
-    return l.block_bytes + (size_t)warps * l.warp_bytes;
-}
-
-int tour_warps(int maxn, size_t smem_max) {
-    int w = TOUR_MAXW;
-    while (w > 1 && tour_smem_bytes(maxn, w) > smem_max) --w;
-    return w;
-}
-
-cudaError_t tour_greedy(const TourArgs &a, int G, int warps, int num_sms, cudaStream_t s) {
-    if (G <= 0) return cudaSuccess;
-    if (warps < 1 || warps > TOUR_MAXW) return cudaErrorInvalidValue;
-    const size_t smem = tour_smem_bytes(a.maxn, warps);
-    cudaError_t e = cudaFuncSetAttribute(tour_greedy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tour_greedy_kernel, 32 * warps, smem);
-    if (e != cudaSuccess) return e;
-    const long long grid = std::min<long long>(G, (long long)std::max(per_sm, 1) * std::max(num_sms, 1));
-    tour_greedy_kernel<<<(unsigned)grid, 32 * warps, smem, s>>>(a, G, warps);
     note_launch();
     return cudaGetLastError();
 }

@@ -86,8 +86,9 @@ class _Stats(ctypes.Structure):
         ("t_result_copy_ms", ctypes.c_float),
         ("result_copy_bytes", ctypes.c_int64),
         ("t_touring_ms", ctypes.c_float),
-        ("touring_warps", ctypes.c_int32),
+        ("touring_sweeps", ctypes.c_int32),
         ("touring_test_paths", ctypes.c_int64),
+        ("touring_edges", ctypes.c_int64),
     ]
 
 

@@ -39,3 +39,13 @@ def assert_paths_equal(gpu_off, gpu_vert, ref_off, ref_vert, what=""):
         j = int(np.nonzero(gv != rv)[0][0])
         p = int(np.searchsorted(ref_off, j, side="right")) - 1
         raise AssertionError(f"{what}: vertex {j} differs (path {p}): {gv[j]} vs {rv[j]}")
+
+
+def touring_digest_update(h, off, vert):
+    """Feed one graph's TP list to a hashlib digest: its count, then every TP
+    as (length, vertices), int64 / int32 little-endian."""
+    off = np.asarray(off, np.int64)
+    vert = np.asarray(vert, np.int32)
+    h.update(np.int64(len(off) - 1).tobytes())
+    h.update((off[1:] - off[:-1]).astype("<i8").tobytes())
+    h.update(vert.astype("<i4").tobytes())
