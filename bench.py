@@ -489,15 +489,18 @@ def batch_record(tpg, cfggen, steps, tile=(1024, 1, 1)):
                                       "test_paths": st["t_test_paths_ms"]}}
 
 
-def touring_record(tpg, cfggen, steps, with_cpu):
+def touring_record(tpg, cfggen, steps, with_cpu, which=("batch4096", "config3")):
     """Longest-first touring (tpg_test_paths_greedy) after the one-per-PP TP
     list, on the 4096-graph batch and the 120-vertex CFG: TP counts and the
     touring's device time (hash tables, touring launch, compaction)."""
     import torch
 
     out = {}
-    cases = [("batch4096", cfggen.batch_cfgs(4096)), ("config3", [cfggen.config3_cfg()])]
-    for name, cfgs in cases:
+    cases = [("batch4096", lambda: cfggen.batch_cfgs(4096)), ("config3", lambda: [cfggen.config3_cfg()])]
+    for name, make in cases:
+        if name not in which:
+            continue
+        cfgs = make()
         ns, rp, col, ent, ext = cfggen.concat_batch(cfgs)
         h = tpg.tpg_load_cfg_batch(ns, rp, col, ent, ext, location=tpg.TPG_RESULT_DEVICE)
         with tpg.tpg_test_paths(h) as tp:
@@ -548,15 +551,17 @@ def run_touring(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     tpg.load_library(build=True)
-    rec = touring_record(tpg, cfggen, steps=max(args.steps, 1), with_cpu=not args.no_cpu_baseline)
+    which = ("batch4096", "config3") if args.touring_case == "all" else (args.touring_case,)
+    rec = touring_record(tpg, cfggen, steps=max(args.steps, 1), with_cpu=not args.no_cpu_baseline, which=which)
     if rank != 0:
         return None
-    P = rec["batch4096"]["prime_paths"]
-    ms = rec["batch4096"]["touring_device_ms"]
+    first = rec[which[0]]
+    P = first["prime_paths"]
+    ms = first["touring_device_ms"]
     return {"metric": "prime paths toured/sec (longest-first touring)", "value": P / (ms / 1e3), "unit": "PP/s",
             "n_gpus": world, "steps": args.steps, "higher_is_better": True, "dtype": "int32",
             "data": "synthetic (seeded structured CFGs)",
-            "config": {"workload": "longest-first touring of the 4096-graph batch"}, "touring": rec}
+            "config": {"workload": f"longest-first touring of {which[0]}"}, "touring": rec}
 
 
 def cpu_baseline_all_cores(cfg, budget_s=6.0, min_runs=2):
@@ -954,6 +959,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=40, help="sizer: training epochs")
     ap.add_argument("--margin", type=float, default=1.25, help="sizer: capacity margin over predictions")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the per-graph plain launches")
+    ap.add_argument("--touring-case", choices=["all", "batch4096", "config3"], default="all",
+                    help="touring: which inputs")
     ap.add_argument("--tile", default="",
                     help="fixed frontier tile 'block,items' (batch: instead of the autotuner)")
     args = ap.parse_args()
