@@ -525,7 +525,7 @@ def touring_record(tpg, cfggen, steps, with_cpu, which=("batch4096", "config3"))
                "call": "tpg_test_paths_greedy on a handle whose PPs are cached: one-per-PP TP pipeline, then "
                        "touring (device_ms covers the touring alone)"}
         h.close()
-        if with_cpu:
+        if with_cpu and len(cfgs) > 1:  # (the 120-vertex CFG alone takes the oracle ~2 minutes)
             import oracle
 
             oracle.build()
@@ -540,6 +540,55 @@ def touring_record(tpg, cfggen, steps, with_cpu, which=("batch4096", "config3"))
                                              f"single-threaded C -O2"}
         out[name] = rec
     return out
+
+
+def run_pervertex(args, rank, world, local_rank):
+    """The paper-style per-vertex-list baseline (tpg_prime_paths_pervertex)
+    beside tpg_prime_paths on out-degree-2 inputs: its device time, the
+    simple paths it copies and their bytes."""
+    import torch
+
+    from paper_2210_16998_gb300 import cfggen, tpg
+
+    torch.cuda.set_device(local_rank)
+    tpg.load_library(build=True)
+    cases = [("structured CFG, 24 vertices", cfggen.config1_cfg())] + \
+        [(f"diamond chain k={k}", cfggen.diamond_chain(k)) for k in (6, 8, 10)] + \
+        [("structured CFG of the 4096-graph batch (graph 25), switches binarised",
+          cfggen.binarise_switches(cfggen.random_cfg(cfggen.BATCH_SEED0 + 25)))]
+    rows = []
+    for name, cfg in cases:
+        h = tpg.tpg_load_cfg_device(cfg.n, cfg.m, torch.as_tensor(cfg.row_ptr, device="cuda"),
+                                    torch.as_tensor(cfg.col if cfg.m else np.zeros(1, np.int32), device="cuda"),
+                                    cfg.entry, cfg.exit)
+        tpg.tpg_set_result_location(h, tpg.TPG_RESULT_DEVICE)
+        pv, ours = [], []
+        for i in range(max(args.steps, 1) + 1):
+            a = tpg.tpg_prime_paths_pervertex(h)
+            P = a.num_paths
+            a.free()
+            st = tpg.tpg_get_stats(h)
+            b = tpg.tpg_prime_paths(h)
+            assert b.num_paths == P
+            b.free()
+            st2 = tpg.tpg_get_stats(h)
+            if i:
+                pv.append(st["t_pervertex_ms"])
+                ours.append(st2["t_enumerate_ms"] + st2["t_order_ms"])
+            tpg.tpg_release_cached_memory()
+        h.close()
+        rows.append({"input": name, "vertices": cfg.n, "prime_paths": P, "simple_paths": st["pervertex_paths"],
+                     "pervertex_ms": statistics.median(pv), "pervertex_list_bytes": st["pervertex_bytes"],
+                     "frontier_ms": statistics.median(ours),
+                     "speedup": statistics.median(pv) / max(statistics.median(ours), 1e-9)})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    if rank != 0:
+        return None
+    return {"metric": "per-vertex-list baseline vs the frontier path (device ms)", "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "higher_is_better": False, "dtype": "int32",
+            "data": "synthetic (seeded CFGs, out-degree <= 2)",
+            "config": {"workload": "paper-style baseline: one thread per vertex, copied path lists"},
+            "pervertex": rows}
 
 
 def run_touring(args, rank, world, local_rank):
@@ -954,7 +1003,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="chain: skip the structured-CFG and 4096-graph sub-records")
     ap.add_argument("--k", type=int, default=K_DIAMONDS, help="diamonds in the chain (22 = the benchmark workload)")
-    ap.add_argument("--workload", choices=["chain", "batch", "sizer", "touring"], default="chain")
+    ap.add_argument("--workload", choices=["chain", "batch", "sizer", "touring", "pervertex"], default="chain")
     ap.add_argument("--train-graphs", type=int, default=50000, help="sizer: training graphs")
     ap.add_argument("--epochs", type=int, default=40, help="sizer: training epochs")
     ap.add_argument("--margin", type=float, default=1.25, help="sizer: capacity margin over predictions")
@@ -977,7 +1026,8 @@ def main():
 
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-        line = {"batch": run_batch, "sizer": run_sizer, "touring": run_touring}.get(args.workload, run_ours)(
+        line = {"batch": run_batch, "sizer": run_sizer, "touring": run_touring,
+                "pervertex": run_pervertex}.get(args.workload, run_ours)(
             args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist

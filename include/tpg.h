@@ -117,6 +117,9 @@ typedef struct tpg_stats {
     int32_t touring_sweeps;     /* decision sweeps it took */
     int64_t touring_test_paths; /* TPs it chose */
     int64_t touring_edges;      /* cover edges (TP(p) holds q, q after p in the order) */
+    float t_pervertex_ms;       /* device time of the last tpg_prime_paths_pervertex */
+    int64_t pervertex_paths;    /* simple paths it copied into the vertex lists */
+    int64_t pervertex_bytes;    /* bytes of those lists (vertices, flags, per-vertex pointers) */
 } tpg_stats;
 
 /*
@@ -204,6 +207,24 @@ int tpg_test_paths(tpg_cfg *g, tpg_paths **out);
  * list holds 2^31 paths or more.
  */
 int tpg_test_paths_greedy(tpg_cfg *g, tpg_paths **out);
+
+/*
+ * tpg_prime_paths_pervertex -- a baseline in the paper's own design
+ * (Sec. 4 and 5, Alg. 1-4), for comparison with tpg_prime_paths: one thread
+ * per vertex, each vertex keeping the simple paths that end at it as whole
+ * copied vertex sequences with the paper's per-path flags (extended, read by
+ * the left / right successor, cyclic); one launch pair per path length
+ * instead of the paper's self-stabilising loop (threads of different blocks
+ * cannot wait on one another), then each vertex prunes its own list (a path
+ * extended by a successor, or a proper suffix of a longer path of the same
+ * list, is not a PP).  The result holds the same PPs as tpg_prime_paths,
+ * grouped by END VERTEX as Problem 1 states the output: num_graphs = n and
+ * graph_path_ptr[v] .. graph_path_ptr[v+1]-1 are the PPs finished at v (by
+ * length, then in creation order).  Single-graph handles only, every vertex
+ * of out-degree at most 2 (binarise switches first, Sec. 3): else
+ * TPG_EINVAL.  Its memory grows with the total length of all simple paths.
+ */
+int tpg_prime_paths_pervertex(tpg_cfg *g, tpg_paths **out);
 
 /* Release a tpg_cfg*, tpg_paths* or tpg_sizer* (tag-checked).  NULL is a no-op. */
 void tpg_free(void *handle);

@@ -301,6 +301,31 @@ def diamond_chain(k: int) -> CFG:
     return CFG(n, row_ptr, col, 0, n - 1, f"diamond-chain-{k}")
 
 
+def binarise_switches(cfg: CFG) -> CFG:
+    """The input restriction of Sec. 3: every vertex of out-degree k > 2
+    (a switch) gets k - 2 new intermediate vertices, so that no vertex has
+    more than two successors.  For v with successors w1 < ... < wk:
+    v -> w1, v -> x1; x1 -> w2, x1 -> x2; ...; x(k-2) -> w(k-1), x(k-2) -> wk.
+    Every original arc v -> wi becomes the path v, x1, ..., x(i-1), wi.  New
+    ids follow the original ones (n, n+1, ...) in order of v, then of the
+    chain; entry and exit are kept."""
+    arcs = []
+    nxt = cfg.n
+    for v in range(cfg.n):
+        ws = [int(w) for w in cfg.succ(v)]
+        if len(ws) <= 2:
+            arcs += [(v, w) for w in ws]
+            continue
+        cur = v
+        for i, w in enumerate(ws[:-2]):
+            arcs += [(cur, w), (cur, nxt)]
+            cur = nxt
+            nxt += 1
+        arcs += [(cur, ws[-2]), (cur, ws[-1])]
+    rp, col = csr_from_arcs(nxt, arcs)
+    return CFG(nxt, rp, col, cfg.entry, cfg.exit, f"{cfg.name}-binarised")
+
+
 def ring(n: int) -> CFG:
     """Directed cycle 0 -> 1 -> ... -> n-1 -> 0 (no valid entry/exit)."""
     row_ptr, col = csr_from_arcs(n, [(i, (i + 1) % n) for i in range(n)])

@@ -15,6 +15,7 @@
 #include "kernels.h"
 #include "testpaths.h"
 #include "touring.h"
+#include "pervertex.h"
 
 using namespace tpg;
 
@@ -1010,11 +1011,14 @@ int run_prime_paths(tpg_cfg *g) {
 }
 
 // Package device blocks as a result in the handle's result location.
-int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, long long V, tpg_paths **out) {
+// groups = entries of gptr minus one (the handle's graphs unless given)
+int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, long long V, tpg_paths **out,
+                int groups = -1) {
+    const int ngroups = groups >= 0 ? groups : g->G;
     PathsImpl *r = new PathsImpl();
     std::memset(&r->pub, 0, sizeof(r->pub));
     r->pub.magic = MAGIC_PATHS;
-    r->pub.num_graphs = g->G;
+    r->pub.num_graphs = ngroups;
     r->pub.num_paths = P;
     r->pub.num_vertices = V;
     r->location = g->location;
@@ -1031,7 +1035,7 @@ int make_result(tpg_cfg *g, Block *off, Block *vert, Block *gptr, long long P, l
         g->stats.t_result_copy_ms = 0.f;
         g->stats.result_copy_bytes = 0;
     } else {
-        const size_t sz[3] = {sizeof(long long) * (g->G + 1), sizeof(long long) * (P + 1),
+        const size_t sz[3] = {sizeof(long long) * (ngroups + 1), sizeof(long long) * (P + 1),
                               sizeof(int) * (size_t)std::max<long long>(V, 1)};
         Block *b[3] = {gptr, off, vert};
         bool copied = false;
@@ -1929,6 +1933,119 @@ int tpg_test_paths_greedy(tpg_cfg *g, tpg_paths **out) {
     block_unref(vert);
     block_unref(gptr);
     release(g, map);
+    return rc;
+}
+
+int tpg_prime_paths_pervertex(tpg_cfg *g, tpg_paths **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (g->G != 1) return TPG_EINVAL;
+    cudaStream_t s = g->stream;
+    const int n = g->N;
+    // the two successor flags: out-degree at most 2
+    std::vector<int> hrp(n + 1);
+    CK(cudaMemcpyAsync(hrp.data(), g->rp.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int v = 0; v < n; ++v)
+        if (hrp[v + 1] - hrp[v] > 2) return TPG_EINVAL;
+    const int *rp = g->rp.as<int>(), *col = g->col.as<int>(), *prp = g->prp.as<int>(), *pcol = g->pcol.as<int>();
+    std::vector<PvLevel> lv(n + 3);
+    std::vector<DevBuf> bufs;  // every level's arrays
+    DevBuf cnt, cnt2, tmp, lvtab, pbase, vbase;
+    int rc = TPG_OK, levels = 0;
+    long long paths = 0, bytes = 0, P = 0, V = 0;
+    Block *off = nullptr, *vert = nullptr, *gptr = nullptr;
+    long long *h = (long long *)g->h_small;
+    // a level: ptr (n + 1), verts (C * k), four flag bytes per path
+    auto new_level = [&](int k, long long C, PvLevel &L, long long *&ptr) -> int {
+        bufs.emplace_back();
+        DevBuf &b = bufs.back();
+        const size_t pb = sizeof(long long) * (n + 1), vb = sizeof(int) * (size_t)std::max(C * k, 1LL);
+        const size_t fb = (size_t)std::max(C, 1LL);
+        RC(ensure(g, b, pb + vb + 4 * fb + 64));
+        char *base = b.as<char>();
+        ptr = (long long *)base;
+        L.ptr = ptr;
+        L.verts = (int *)(base + pb);
+        L.ext = (unsigned char *)(base + pb + vb);
+        L.read_left = L.ext + fb;
+        L.read_right = L.read_left + fb;
+        L.cyc = L.read_right + fb;
+        bytes += (long long)(pb + vb + 4 * fb);
+        return TPG_OK;
+    };
+    do {
+        if ((rc = ensure(g, cnt, sizeof(long long) * (n + 1))) || (rc = ensure(g, cnt2, sizeof(long long) * (n + 1))) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(n + 1))))
+            break;
+        if ((rc = cuda_err(cudaEventRecord(g->ev[10], s)))) break;
+        // level 1: <v> at v
+        long long *ptr = nullptr;
+        if ((rc = new_level(1, n, lv[1], ptr))) break;
+        if ((rc = cuda_err(tp_iota(ptr, n + 1, s))) ||
+            (rc = cuda_err(cudaMemsetAsync(lv[1].ext, 0, 4 * (size_t)n, s))) ||
+            (rc = cuda_err(pv_iota(lv[1].verts, n, s))))
+            break;
+        paths = n;
+        levels = 1;
+        for (int k = 2; k <= n + 1; ++k) {
+            if ((rc = cuda_err(pv_extend(k, n, rp, col, prp, pcol, lv[k - 1], lv[k - 1], cnt.as<long long>(), false,
+                                         s))) ||
+                (rc = cuda_err(scan_i64(cnt.as<long long>(), cnt2.as<long long>(), n, tmp.as<long long>(), s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(h, cnt2.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost,
+                                               s))) ||
+                (rc = cuda_err(cudaStreamSynchronize(s))))
+                break;
+            const long long C = h[0];
+            if (C == 0) break;
+            if ((rc = new_level(k, C, lv[k], ptr)) ||
+                (rc = cuda_err(cudaMemcpyAsync(ptr, cnt2.p, sizeof(long long) * (n + 1), cudaMemcpyDeviceToDevice, s))) ||
+                (rc = cuda_err(pv_extend(k, n, rp, col, prp, pcol, lv[k - 1], lv[k], nullptr, true, s))))
+                break;
+            paths += C;
+            levels = k;
+        }
+        if (rc) break;
+        // prune every vertex's list, then gather its PPs
+        if ((rc = ensure(g, lvtab, sizeof(PvLevel) * (levels + 2))) || (rc = ensure(g, pbase, sizeof(long long) * (n + 1))) ||
+            (rc = ensure(g, vbase, sizeof(long long) * (n + 1))) ||
+            (rc = cuda_err(cudaMemcpyAsync(lvtab.p, lv.data(), sizeof(PvLevel) * (levels + 2), cudaMemcpyHostToDevice,
+                                           s))) ||
+            (rc = cuda_err(pv_prune(n, levels, lvtab.as<PvLevel>(), cnt.as<long long>(), cnt2.as<long long>(), nullptr,
+                                    nullptr, nullptr, nullptr, false, s))) ||
+            (rc = cuda_err(scan_i64(cnt.as<long long>(), pbase.as<long long>(), n, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(scan_i64(cnt2.as<long long>(), vbase.as<long long>(), n, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(h, pbase.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(h + 1, vbase.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost,
+                                           s))) ||
+            (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+        P = h[0];
+        V = h[1];
+        off = block_new(g->fns, sizeof(long long) * (P + 1), s);
+        vert = block_new(g->fns, sizeof(int) * std::max<long long>(V, 1), s);
+        gptr = block_new(g->fns, sizeof(long long) * (n + 1), s);
+        if (!off || !vert || !gptr) { rc = TPG_ENOMEM; break; }
+        h[2] = V;
+        if ((rc = cuda_err(pv_prune(n, levels, lvtab.as<PvLevel>(), nullptr, nullptr, pbase.as<long long>(),
+                                    vbase.as<long long>(), (long long *)off->p, (int *)vert->p, true, s))) ||
+            (rc = cuda_err(cudaMemcpyAsync((long long *)off->p + P, h + 2, sizeof(long long), cudaMemcpyHostToDevice,
+                                           s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(gptr->p, pbase.p, sizeof(long long) * (n + 1), cudaMemcpyDeviceToDevice, s))) ||
+            (rc = cuda_err(cudaEventRecord(g->ev[11], s))) || (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+        cudaEventElapsedTime(&g->stats.t_pervertex_ms, g->ev[10], g->ev[11]);
+        g->stats.pervertex_paths = paths;
+        g->stats.pervertex_bytes = bytes;
+    } while (false);
+    if (rc != TPG_OK) cudaStreamSynchronize(s);
+    for (auto &b : bufs) release(g, b);
+    for (DevBuf *b : {&cnt, &cnt2, &tmp, &lvtab, &pbase, &vbase}) release(g, *b);
+    if (rc == TPG_OK) rc = make_result(g, off, vert, gptr, P, V, out, n);
+    block_unref(off);
+    block_unref(vert);
+    block_unref(gptr);
     return rc;
 }
 

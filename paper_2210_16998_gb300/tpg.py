@@ -89,6 +89,9 @@ class _Stats(ctypes.Structure):
         ("touring_sweeps", ctypes.c_int32),
         ("touring_test_paths", ctypes.c_int64),
         ("touring_edges", ctypes.c_int64),
+        ("t_pervertex_ms", ctypes.c_float),
+        ("pervertex_paths", ctypes.c_int64),
+        ("pervertex_bytes", ctypes.c_int64),
     ]
 
 
@@ -133,6 +136,7 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_prime_paths.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_test_paths.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_test_paths_greedy.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
+        lib.tpg_prime_paths_pervertex.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_free.argtypes = [P]
         lib.tpg_free.restype = None
         lib.tpg_set_stream.argtypes = [P, P]
@@ -181,7 +185,8 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
                                                 ctypes.POINTER(ctypes.c_int64)]
         lib.tpg_prime_paths_noalloc.restype = ctypes.c_int
         for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
-                     "tpg_test_paths", "tpg_test_paths_greedy", "tpg_set_stream", "tpg_set_result_location",
+                     "tpg_test_paths", "tpg_test_paths_greedy", "tpg_prime_paths_pervertex", "tpg_set_stream",
+                     "tpg_set_result_location",
                      "tpg_set_allocator",
                      "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_work_split", "tpg_set_capacity",
                      "tpg_set_output_capacity",
@@ -424,6 +429,14 @@ def tpg_test_paths_greedy(cfg: Cfg) -> Paths:
     """The longest-first touring TP set (a subset of tpg_test_paths's list)."""
     out = ctypes.POINTER(_Paths)()
     _check(load_library().tpg_test_paths_greedy(cfg.handle, ctypes.byref(out)), "tpg_test_paths_greedy")
+    return Paths(out)
+
+
+def tpg_prime_paths_pervertex(cfg: Cfg) -> Paths:
+    """The paper-style per-vertex-list baseline: the PPs grouped by end vertex
+    (num_graphs = n)."""
+    out = ctypes.POINTER(_Paths)()
+    _check(load_library().tpg_prime_paths_pervertex(cfg.handle, ctypes.byref(out)), "tpg_prime_paths_pervertex")
     return Paths(out)
 
 
