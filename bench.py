@@ -591,6 +591,49 @@ def run_pervertex(args, rank, world, local_rank):
             "pervertex": rows}
 
 
+def run_scc(args, rank, world, local_rank):
+    """The per-SCC step of the compositional route (tpg_scc_internal_pps)
+    beside the direct PP enumeration, on single CFGs."""
+    import torch
+
+    from paper_2210_16998_gb300 import cfggen, tpg
+
+    torch.cuda.set_device(local_rank)
+    tpg.load_library(build=True)
+    cases = [("structured CFG, 24 vertices", cfggen.config1_cfg()),
+             ("structured CFG, 120 vertices", cfggen.config3_cfg())] + \
+        [(f"structured CFG of the 4096-graph batch (graph {i})", cfggen.random_cfg(cfggen.BATCH_SEED0 + i))
+         for i in (21, 47, 54)]
+    rows = []
+    for name, cfg in cases:
+        h = tpg.tpg_load_cfg(cfg.n, cfg.row_ptr, cfg.col, cfg.entry, cfg.exit, location=tpg.TPG_RESULT_DEVICE)
+        scc, direct = [], []
+        for i in range(max(args.steps, 1) + 1):
+            a = tpg.tpg_scc_internal_pps(h)
+            a.free()
+            st = tpg.tpg_get_stats(h)
+            b = tpg.tpg_prime_paths(h)
+            P = b.num_paths
+            b.free()
+            st2 = tpg.tpg_get_stats(h)
+            if i:
+                scc.append(st["t_scc_ms"])
+                direct.append(st2["t_enumerate_ms"] + st2["t_order_ms"])
+        comp = tpg.tpg_scc_ids(h, cfg.n)
+        h.close()
+        rows.append({"input": name, "vertices": cfg.n, "sccs": int(len(set(comp.tolist()))),
+                     "largest_scc": int(np.bincount(comp).max()), "prime_paths": P,
+                     "scc_subgraph_pps": st["scc_pps"], "scc_internal_pps": st["scc_internal_pps"],
+                     "scc_step_ms": statistics.median(scc), "direct_pp_ms": statistics.median(direct)})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    if rank != 0:
+        return None
+    return {"metric": "per-SCC step of the compositional route (device ms)", "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "higher_is_better": False, "dtype": "int32", "data": "synthetic (seeded CFGs)",
+            "config": {"workload": "SCC ids, intra-SCC subgraph through the frontier, SccInternalPPs"},
+            "scc": rows}
+
+
 def run_touring(args, rank, world, local_rank):
     """Only the touring sub-record (longest-first TP sets of the 4096-graph
     batch and the 120-vertex CFG)."""
@@ -1003,7 +1046,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="chain: skip the structured-CFG and 4096-graph sub-records")
     ap.add_argument("--k", type=int, default=K_DIAMONDS, help="diamonds in the chain (22 = the benchmark workload)")
-    ap.add_argument("--workload", choices=["chain", "batch", "sizer", "touring", "pervertex"], default="chain")
+    ap.add_argument("--workload", choices=["chain", "batch", "sizer", "touring", "pervertex", "scc"],
+                    default="chain")
     ap.add_argument("--train-graphs", type=int, default=50000, help="sizer: training graphs")
     ap.add_argument("--epochs", type=int, default=40, help="sizer: training epochs")
     ap.add_argument("--margin", type=float, default=1.25, help="sizer: capacity margin over predictions")
@@ -1027,7 +1071,7 @@ def main():
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         line = {"batch": run_batch, "sizer": run_sizer, "touring": run_touring,
-                "pervertex": run_pervertex}.get(args.workload, run_ours)(
+                "pervertex": run_pervertex, "scc": run_scc}.get(args.workload, run_ours)(
             args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist

@@ -120,6 +120,9 @@ typedef struct tpg_stats {
     float t_pervertex_ms;       /* device time of the last tpg_prime_paths_pervertex */
     int64_t pervertex_paths;    /* simple paths it copied into the vertex lists */
     int64_t pervertex_bytes;    /* bytes of those lists (vertices, flags, per-vertex pointers) */
+    float t_scc_ms;             /* device time of the last tpg_scc_internal_pps */
+    int64_t scc_pps;            /* PPs of the SCC subgraphs it found */
+    int64_t scc_internal_pps;   /* of them, SccInternalPPs */
 } tpg_stats;
 
 /*
@@ -225,6 +228,26 @@ int tpg_test_paths_greedy(tpg_cfg *g, tpg_paths **out);
  * TPG_EINVAL.  Its memory grows with the total length of all simple paths.
  */
 int tpg_prime_paths_pervertex(tpg_cfg *g, tpg_paths **out);
+
+/*
+ * The per-SCC step of the compositional route (Sec. 2.1, Defs. 3, 5, 9).
+ *
+ * tpg_scc_ids           comp_host[v] (n values) = the smallest vertex of
+ *                       v's strongly connected component (v and u share one
+ *                       iff each reaches the other), from the handle's BFS
+ *                       tables.
+ * tpg_scc_internal_pps  the SccInternalPPs of every SCC, canonical order:
+ *                       the PPs of the SCC's own subgraph (the graph
+ *                       restricted to arcs inside one SCC, run through the
+ *                       regular frontier path) that are cycles, or that
+ *                       neither start at an SccEntryVertex (a predecessor in
+ *                       another SCC) nor end at an SccExitVertex (a
+ *                       successor in another SCC).  On the worked example
+ *                       of Sec. 2.1 these are the 11 internal PPs it lists.
+ * Single-graph handles only (else TPG_EINVAL).
+ */
+int tpg_scc_ids(tpg_cfg *g, int32_t *comp_host);
+int tpg_scc_internal_pps(tpg_cfg *g, tpg_paths **out);
 
 /* Release a tpg_cfg*, tpg_paths* or tpg_sizer* (tag-checked).  NULL is a no-op. */
 void tpg_free(void *handle);

@@ -16,6 +16,7 @@
 #include "testpaths.h"
 #include "touring.h"
 #include "pervertex.h"
+#include "scc.h"
 
 using namespace tpg;
 
@@ -2046,6 +2047,109 @@ int tpg_prime_paths_pervertex(tpg_cfg *g, tpg_paths **out) {
     block_unref(off);
     block_unref(vert);
     block_unref(gptr);
+    return rc;
+}
+
+int tpg_scc_ids(tpg_cfg *g, int32_t *comp_host) {
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (!comp_host) return TPG_EINVAL;
+    if (g->G != 1) return TPG_EINVAL;
+    DevBuf comp;
+    RC(ensure(g, comp, sizeof(int) * g->N));
+    int rc = cuda_err(scc_ids(g->gd, comp.as<int>(), g->stream));
+    if (rc == TPG_OK) rc = cuda_err(cudaMemcpyAsync(comp_host, comp.p, sizeof(int) * g->N, cudaMemcpyDeviceToHost,
+                                                    g->stream));
+    if (rc == TPG_OK) rc = cuda_err(cudaStreamSynchronize(g->stream));
+    release(g, comp);
+    return rc;
+}
+
+int tpg_scc_internal_pps(tpg_cfg *g, tpg_paths **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (g->G != 1) return TPG_EINVAL;
+    cudaStream_t s = g->stream;
+    const int n = g->N;
+    DevBuf comp, cnt, off, tmp, rp, col, ent, ext, keep, klen, koff, krank, perm, ids, fgraph;
+    tpg_cfg *h = nullptr;
+    Block *f_off = nullptr, *f_vert = nullptr, *f_gptr = nullptr;
+    long long *hs = (long long *)g->h_small;
+    long long T = 0, TV = 0;
+    int rc = TPG_OK;
+    do {
+        if ((rc = ensure(g, comp, sizeof(int) * n)) || (rc = ensure(g, cnt, sizeof(int) * (n + 1))) ||
+            (rc = ensure(g, off, sizeof(long long) * (n + 2))) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(n + 1))) ||
+            (rc = ensure(g, rp, sizeof(int) * (n + 1))) || (rc = ensure(g, col, sizeof(int) * std::max<long long>(g->M, 1))) ||
+            (rc = ensure(g, ent, n)) || (rc = ensure(g, ext, n)))
+            break;
+        // SCCs, the intra-SCC CSR, the entry / exit flags
+        if ((rc = cuda_err(cudaEventRecord(g->ev[10], s))) || (rc = cuda_err(scc_ids(g->gd, comp.as<int>(), s))) ||
+            (rc = cuda_err(scc_intra_counts(g->gd, comp.as<int>(), cnt.as<int>(), s))) ||
+            (rc = cuda_err(scan_i32_to_i64(cnt.as<int>(), off.as<long long>(), n, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(scc_intra_write(g->gd, comp.as<int>(), off.as<long long>(), rp.as<int>(), col.as<int>(), s))) ||
+            (rc = cuda_err(scc_boundary(g->gd, comp.as<int>(), ent.as<unsigned char>(), ext.as<unsigned char>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(hs, off.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+        const long long mi = hs[0];
+        int entry = 0, exitv = 0;
+        if ((rc = cuda_err(cudaMemcpy(&entry, g->entry.p, sizeof(int), cudaMemcpyDeviceToHost))) ||
+            (rc = cuda_err(cudaMemcpy(&exitv, g->exitv.p, sizeof(int), cudaMemcpyDeviceToHost))))
+            break;
+        // the PPs of every SCC's subgraph: the regular path on the intra-SCC graph
+        // (its entry keeps in-degree 0 and its exit out-degree 0)
+        if ((rc = tpg_load_cfg_device(n, (int)mi, rp.as<int>(), col.as<int>(), entry, exitv, (void *)s, &h))) break;
+        if ((rc = run_prime_paths(h))) break;
+        const long long P = h->P;
+        const long long *pp_off = (const long long *)h->pp_off->p;
+        const int *pp_vert = (const int *)h->pp_vert->p;
+        if ((rc = ensure(g, keep, sizeof(int) * std::max(P, 1LL))) || (rc = ensure(g, klen, sizeof(long long) * std::max(P, 1LL))) ||
+            (rc = ensure(g, koff, sizeof(long long) * (P + 1))) || (rc = ensure(g, krank, sizeof(long long) * (P + 1))) ||
+            (rc = ensure(g, perm, sizeof(long long) * std::max(P, 1LL))) || (rc = ensure(g, ids, sizeof(int) * std::max(P, 1LL))) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(P + 1))))
+            break;
+        if ((rc = cuda_err(scc_internal_flags(pp_off, pp_vert, P, ent.as<unsigned char>(), ext.as<unsigned char>(),
+                                              keep.as<int>(), klen.as<long long>(), s))) ||
+            (rc = cuda_err(scan_i64(klen.as<long long>(), koff.as<long long>(), P, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(scan_i32_to_i64(keep.as<int>(), krank.as<long long>(), P, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(tp_iota(perm.as<long long>(), P, s))) ||
+            (rc = cuda_err(cudaMemsetAsync(ids.p, 0, sizeof(int) * std::max(P, 1LL), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(hs, krank.as<long long>() + P, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(hs + 1, koff.as<long long>() + P, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+        T = hs[0];
+        TV = hs[1];
+        f_off = block_new(g->fns, sizeof(long long) * (T + 1), s);
+        f_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
+        f_gptr = block_new(g->fns, sizeof(long long) * 2, s);
+        if (!f_off || !f_vert || !f_gptr) { rc = TPG_ENOMEM; break; }
+        if ((rc = ensure(g, fgraph, sizeof(int) * std::max<long long>(T, 1)))) break;
+        hs[2] = TV;
+        hs[3] = 0;
+        hs[4] = T;
+        if ((rc = cuda_err(tp_gather(perm.as<long long>(), keep.as<int>(), krank.as<long long>(), P, pp_off, pp_vert,
+                                     ids.as<int>(), koff.as<long long>(), (long long *)f_off->p, (int *)f_vert->p,
+                                     fgraph.as<int>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync((long long *)f_off->p + T, hs + 2, sizeof(long long), cudaMemcpyHostToDevice,
+                                           s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(f_gptr->p, hs + 3, 2 * sizeof(long long), cudaMemcpyHostToDevice, s))) ||
+            (rc = cuda_err(cudaEventRecord(g->ev[11], s))) || (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+        cudaEventElapsedTime(&g->stats.t_scc_ms, g->ev[10], g->ev[11]);
+        g->stats.scc_pps = P;
+        g->stats.scc_internal_pps = T;
+    } while (false);
+    if (rc != TPG_OK) cudaStreamSynchronize(s);
+    if (h) destroy_cfg(h);
+    for (DevBuf *b : {&comp, &cnt, &off, &tmp, &rp, &col, &ent, &ext, &keep, &klen, &koff, &krank, &perm, &ids, &fgraph})
+        release(g, *b);
+    if (rc == TPG_OK) rc = make_result(g, f_off, f_vert, f_gptr, T, TV, out);
+    block_unref(f_off);
+    block_unref(f_vert);
+    block_unref(f_gptr);
     return rc;
 }
 

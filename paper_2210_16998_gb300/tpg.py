@@ -92,6 +92,9 @@ class _Stats(ctypes.Structure):
         ("t_pervertex_ms", ctypes.c_float),
         ("pervertex_paths", ctypes.c_int64),
         ("pervertex_bytes", ctypes.c_int64),
+        ("t_scc_ms", ctypes.c_float),
+        ("scc_pps", ctypes.c_int64),
+        ("scc_internal_pps", ctypes.c_int64),
     ]
 
 
@@ -137,6 +140,8 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_test_paths.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_test_paths_greedy.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_prime_paths_pervertex.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
+        lib.tpg_scc_internal_pps.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
+        lib.tpg_scc_ids.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
         lib.tpg_free.argtypes = [P]
         lib.tpg_free.restype = None
         lib.tpg_set_stream.argtypes = [P, P]
@@ -185,7 +190,8 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
                                                 ctypes.POINTER(ctypes.c_int64)]
         lib.tpg_prime_paths_noalloc.restype = ctypes.c_int
         for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
-                     "tpg_test_paths", "tpg_test_paths_greedy", "tpg_prime_paths_pervertex", "tpg_set_stream",
+                     "tpg_test_paths", "tpg_test_paths_greedy", "tpg_prime_paths_pervertex", "tpg_scc_ids",
+                     "tpg_scc_internal_pps", "tpg_set_stream",
                      "tpg_set_result_location",
                      "tpg_set_allocator",
                      "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_work_split", "tpg_set_capacity",
@@ -437,6 +443,20 @@ def tpg_prime_paths_pervertex(cfg: Cfg) -> Paths:
     (num_graphs = n)."""
     out = ctypes.POINTER(_Paths)()
     _check(load_library().tpg_prime_paths_pervertex(cfg.handle, ctypes.byref(out)), "tpg_prime_paths_pervertex")
+    return Paths(out)
+
+
+def tpg_scc_ids(cfg: Cfg, n: int) -> np.ndarray:
+    """SCC of each of the graph's n vertices, named by its smallest member."""
+    out = np.empty(int(n), np.int32)
+    _check(load_library().tpg_scc_ids(cfg.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "tpg_scc_ids")
+    return out
+
+
+def tpg_scc_internal_pps(cfg: Cfg) -> Paths:
+    """The SccInternalPPs of every SCC (Def. 9), canonical order."""
+    out = ctypes.POINTER(_Paths)()
+    _check(load_library().tpg_scc_internal_pps(cfg.handle, ctypes.byref(out)), "tpg_scc_internal_pps")
     return Paths(out)
 
 
