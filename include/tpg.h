@@ -123,6 +123,11 @@ typedef struct tpg_stats {
     float t_scc_ms;             /* device time of the last tpg_scc_internal_pps */
     int64_t scc_pps;            /* PPs of the SCC subgraphs it found */
     int64_t scc_internal_pps;   /* of them, SccInternalPPs */
+    float t_compositional_ms;   /* device time of the last tpg_prime_paths_compositional */
+    int64_t comp_entry_exit_paths; /* its SccEntryExitPaths (Def. 6), all SCCs */
+    int64_t comp_exit_paths;       /* its SccExitPaths (Def. 7) */
+    int64_t comp_entry_paths;      /* its SccEntryPaths (Def. 8) */
+    int64_t comp_crossing_pps;     /* PPs it joined across SCCs */
 } tpg_stats;
 
 /*
@@ -248,6 +253,19 @@ int tpg_prime_paths_pervertex(tpg_cfg *g, tpg_paths **out);
  */
 int tpg_scc_ids(tpg_cfg *g, int32_t *comp_host);
 int tpg_scc_internal_pps(tpg_cfg *g, tpg_paths **out);
+
+/*
+ * tpg_prime_paths_compositional -- the PPs by the compositional route of
+ * Sec. 2.1 instead of the direct enumeration: the SccInternalPPs (above),
+ * plus every PP that crosses SCCs, joined from an SccExitPath (Def. 7: an
+ * acyclic path to an SccExitVertex whose first vertex has every predecessor
+ * on it), SccEntryExitPaths (Def. 6) of the SCCs it passes and an
+ * SccEntryPath (Def. 8: from an SccEntryVertex, every successor of its last
+ * vertex on it), consecutive parts linked by arcs between SCCs.  Same result
+ * as tpg_prime_paths, canonical order.  Single-graph handles (TPG_EINVAL)
+ * of at most 256 vertices (TPG_ETOOBIG).
+ */
+int tpg_prime_paths_compositional(tpg_cfg *g, tpg_paths **out);
 
 /* Release a tpg_cfg*, tpg_paths* or tpg_sizer* (tag-checked).  NULL is a no-op. */
 void tpg_free(void *handle);

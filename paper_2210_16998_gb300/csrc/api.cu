@@ -17,6 +17,7 @@
 #include "touring.h"
 #include "pervertex.h"
 #include "scc.h"
+#include "compositional.h"
 
 using namespace tpg;
 
@@ -2064,16 +2065,16 @@ int tpg_scc_ids(tpg_cfg *g, int32_t *comp_host) {
     return rc;
 }
 
-int tpg_scc_internal_pps(tpg_cfg *g, tpg_paths **out) {
-    if (!out) return TPG_EINVAL;
-    *out = nullptr;
-    if (!is_cfg(g)) return TPG_EHANDLE;
-    if (g->G != 1) return TPG_EINVAL;
+// The SccInternalPPs of a one-graph handle (canonical order) in *o_off /
+// *o_vert (T paths, TV vertices); comp, ent and ext keep the SCC ids and the
+// SccEntryVertex / SccExitVertex flags for the caller.
+static int scc_internal(tpg_cfg *g, DevBuf &comp, DevBuf &ent, DevBuf &ext, Block **o_off, Block **o_vert,
+                        long long *oT, long long *oTV) {
     cudaStream_t s = g->stream;
     const int n = g->N;
-    DevBuf comp, cnt, off, tmp, rp, col, ent, ext, keep, klen, koff, krank, perm, ids, fgraph;
+    DevBuf cnt, off, tmp, rp, col, keep, klen, koff, krank, perm, ids, fgraph;
     tpg_cfg *h = nullptr;
-    Block *f_off = nullptr, *f_vert = nullptr, *f_gptr = nullptr;
+    Block *f_off = nullptr, *f_vert = nullptr;
     long long *hs = (long long *)g->h_small;
     long long T = 0, TV = 0;
     int rc = TPG_OK;
@@ -2085,24 +2086,24 @@ int tpg_scc_internal_pps(tpg_cfg *g, tpg_paths **out) {
             (rc = ensure(g, ent, n)) || (rc = ensure(g, ext, n)))
             break;
         // SCCs, the intra-SCC CSR, the entry / exit flags
-        if ((rc = cuda_err(cudaEventRecord(g->ev[10], s))) || (rc = cuda_err(scc_ids(g->gd, comp.as<int>(), s))) ||
+        if ((rc = cuda_err(scc_ids(g->gd, comp.as<int>(), s))) ||
             (rc = cuda_err(scc_intra_counts(g->gd, comp.as<int>(), cnt.as<int>(), s))) ||
             (rc = cuda_err(scan_i32_to_i64(cnt.as<int>(), off.as<long long>(), n, tmp.as<long long>(), s))) ||
             (rc = cuda_err(scc_intra_write(g->gd, comp.as<int>(), off.as<long long>(), rp.as<int>(), col.as<int>(), s))) ||
             (rc = cuda_err(scc_boundary(g->gd, comp.as<int>(), ent.as<unsigned char>(), ext.as<unsigned char>(), s))) ||
             (rc = cuda_err(cudaMemcpyAsync(hs, off.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(hs + 1, g->entry.p, sizeof(int), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaMemcpyAsync((int *)(hs + 1) + 1, g->exitv.p, sizeof(int), cudaMemcpyDeviceToHost, s))) ||
             (rc = cuda_err(cudaStreamSynchronize(s))))
             break;
         const long long mi = hs[0];
-        int entry = 0, exitv = 0;
-        if ((rc = cuda_err(cudaMemcpy(&entry, g->entry.p, sizeof(int), cudaMemcpyDeviceToHost))) ||
-            (rc = cuda_err(cudaMemcpy(&exitv, g->exitv.p, sizeof(int), cudaMemcpyDeviceToHost))))
-            break;
+        const int entry = ((int *)(hs + 1))[0], exitv = ((int *)(hs + 1))[1];
         // the PPs of every SCC's subgraph: the regular path on the intra-SCC graph
         // (its entry keeps in-degree 0 and its exit out-degree 0)
         if ((rc = tpg_load_cfg_device(n, (int)mi, rp.as<int>(), col.as<int>(), entry, exitv, (void *)s, &h))) break;
         if ((rc = run_prime_paths(h))) break;
         const long long P = h->P;
+        g->stats.scc_pps = P;
         const long long *pp_off = (const long long *)h->pp_off->p;
         const int *pp_vert = (const int *)h->pp_vert->p;
         if ((rc = ensure(g, keep, sizeof(int) * std::max(P, 1LL))) || (rc = ensure(g, klen, sizeof(long long) * std::max(P, 1LL))) ||
@@ -2124,28 +2125,347 @@ int tpg_scc_internal_pps(tpg_cfg *g, tpg_paths **out) {
         TV = hs[1];
         f_off = block_new(g->fns, sizeof(long long) * (T + 1), s);
         f_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
-        f_gptr = block_new(g->fns, sizeof(long long) * 2, s);
-        if (!f_off || !f_vert || !f_gptr) { rc = TPG_ENOMEM; break; }
+        if (!f_off || !f_vert) { rc = TPG_ENOMEM; break; }
         if ((rc = ensure(g, fgraph, sizeof(int) * std::max<long long>(T, 1)))) break;
         hs[2] = TV;
-        hs[3] = 0;
-        hs[4] = T;
         if ((rc = cuda_err(tp_gather(perm.as<long long>(), keep.as<int>(), krank.as<long long>(), P, pp_off, pp_vert,
                                      ids.as<int>(), koff.as<long long>(), (long long *)f_off->p, (int *)f_vert->p,
                                      fgraph.as<int>(), s))) ||
             (rc = cuda_err(cudaMemcpyAsync((long long *)f_off->p + T, hs + 2, sizeof(long long), cudaMemcpyHostToDevice,
                                            s))) ||
-            (rc = cuda_err(cudaMemcpyAsync(f_gptr->p, hs + 3, 2 * sizeof(long long), cudaMemcpyHostToDevice, s))) ||
-            (rc = cuda_err(cudaEventRecord(g->ev[11], s))) || (rc = cuda_err(cudaStreamSynchronize(s))))
+            (rc = cuda_err(cudaStreamSynchronize(s))))
             break;
-        cudaEventElapsedTime(&g->stats.t_scc_ms, g->ev[10], g->ev[11]);
-        g->stats.scc_pps = P;
         g->stats.scc_internal_pps = T;
     } while (false);
     if (rc != TPG_OK) cudaStreamSynchronize(s);
     if (h) destroy_cfg(h);
-    for (DevBuf *b : {&comp, &cnt, &off, &tmp, &rp, &col, &ent, &ext, &keep, &klen, &koff, &krank, &perm, &ids, &fgraph})
+    for (DevBuf *b : {&cnt, &off, &tmp, &rp, &col, &keep, &klen, &koff, &krank, &perm, &ids, &fgraph}) release(g, *b);
+    if (rc != TPG_OK) {
+        block_unref(f_off);
+        block_unref(f_vert);
+        return rc;
+    }
+    *o_off = f_off;
+    *o_vert = f_vert;
+    *oT = T;
+    *oTV = TV;
+    return TPG_OK;
+}
+
+// gptr block of a one-graph result of P paths
+static Block *one_graph_ptr(tpg_cfg *g, long long P) {
+    Block *b = block_new(g->fns, sizeof(long long) * 2, g->stream);
+    if (!b) return nullptr;
+    long long *hs = (long long *)g->h_small;
+    hs[6] = 0;
+    hs[7] = P;
+    if (cudaMemcpyAsync(b->p, hs + 6, 2 * sizeof(long long), cudaMemcpyHostToDevice, g->stream) ||
+        cudaStreamSynchronize(g->stream)) {
+        cudaGetLastError();
+        block_unref(b);
+        return nullptr;
+    }
+    return b;
+}
+
+int tpg_scc_internal_pps(tpg_cfg *g, tpg_paths **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (g->G != 1) return TPG_EINVAL;
+    DevBuf comp, ent, ext;
+    Block *off = nullptr, *vert = nullptr;
+    long long T = 0, TV = 0;
+    CK(cudaEventRecord(g->ev[10], g->stream));
+    int rc = scc_internal(g, comp, ent, ext, &off, &vert, &T, &TV);
+    for (DevBuf *b : {&comp, &ent, &ext}) release(g, *b);
+    if (rc) return rc;
+    cudaEventRecord(g->ev[11], g->stream);
+    Block *gptr = one_graph_ptr(g, T);
+    if (!gptr) rc = TPG_ENOMEM;
+    if (rc == TPG_OK) {
+        cudaEventElapsedTime(&g->stats.t_scc_ms, g->ev[10], g->ev[11]);
+        rc = make_result(g, off, vert, gptr, T, TV, out);
+    }
+    block_unref(off);
+    block_unref(vert);
+    block_unref(gptr);
+    return rc;
+}
+
+// Sort a list of n paths (one graph) into canonical order and drop exact
+// duplicates: packed keys and merge rounds over runs (run_start flags the
+// first path of every sorted run), then a gather into new blocks.
+static int sort_paths(tpg_cfg *g, const long long *off, const int *vert, long long n, long long V, const int *run_start,
+                      Block **o_off, Block **o_vert, long long *oT, long long *oTV) {
+    cudaStream_t s = g->stream;
+    long long *hs = (long long *)g->h_small;
+    DevBuf klen, koff, key, rrank, bounds, rbase, perm0, perm1, keep, keep_len, keep_off, keep_rank, ids, fgraph, tmp, gp;
+    Block *f_off = nullptr, *f_vert = nullptr;
+    const int kbits = g->maxn <= 255 ? 8 : 16;
+    const long long K_ub = V / (64 / kbits) + n + 1;
+    int rc = TPG_OK;
+    long long T = 0, TV = 0;
+    do {
+        if ((rc = ensure(g, klen, sizeof(long long) * (n + 1))) || (rc = ensure(g, koff, sizeof(long long) * (n + 1))) ||
+            (rc = ensure(g, key, sizeof(unsigned long long) * K_ub)) || (rc = ensure(g, rrank, sizeof(long long) * (n + 1))) ||
+            (rc = ensure(g, bounds, sizeof(long long) * (n + 2))) || (rc = ensure(g, rbase, sizeof(long long) * 2)) ||
+            (rc = ensure(g, perm0, sizeof(long long) * n)) || (rc = ensure(g, perm1, sizeof(long long) * n)) ||
+            (rc = ensure(g, keep, sizeof(int) * n)) || (rc = ensure(g, keep_len, sizeof(long long) * n)) ||
+            (rc = ensure(g, keep_off, sizeof(long long) * (n + 1))) ||
+            (rc = ensure(g, keep_rank, sizeof(long long) * (n + 1))) || (rc = ensure(g, ids, sizeof(int) * n)) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(n + 1))) || (rc = ensure(g, gp, sizeof(long long) * 2)))
+            break;
+        hs[8] = 0;
+        hs[9] = n;
+        long long *perm[2] = {perm0.as<long long>(), perm1.as<long long>()};
+        if ((rc = cuda_err(cudaMemcpyAsync(gp.p, hs + 8, 2 * sizeof(long long), cudaMemcpyHostToDevice, s))) ||
+            (rc = cuda_err(cudaMemsetAsync(ids.p, 0, sizeof(int) * n, s))) ||
+            (rc = cuda_err(tp_key_lengths(off, n, kbits, klen.as<long long>(), s))) ||
+            (rc = cuda_err(scan_i64(klen.as<long long>(), koff.as<long long>(), n, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(tp_write_keys(off, vert, n, kbits, koff.as<long long>(), key.as<unsigned long long>(), s))) ||
+            (rc = cuda_err(scan_i32_to_i64(run_start, rrank.as<long long>(), n, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(hs, rrank.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+        const long long R = hs[0];
+        long long *nruns = rbase.as<long long>() + 1;
+        if ((rc = cuda_err(tp_run_bounds(run_start, rrank.as<long long>(), n, R, bounds.as<long long>(), s))) ||
+            (rc = cuda_err(tp_run_bases(gp.as<long long>(), rrank.as<long long>(), 1, rbase.as<long long>(), nruns, s))) ||
+            (rc = cuda_err(tp_iota(perm[0], n, s))))
+            break;
+        int cp = 0;
+        const int rounds = tp_merge_rounds(R);
+        for (int r = 0; r < rounds && rc == TPG_OK; ++r) {
+            rc = cuda_err(tp_merge_graph_round_keys(perm[cp], perm[cp ^ 1], bounds.as<long long>(), rbase.as<long long>(),
+                                                    nruns, gp.as<long long>(), 1, r, n, koff.as<long long>(),
+                                                    key.as<unsigned long long>(), s));
+            cp ^= 1;
+        }
+        if (rc) break;
+        if ((rc = cuda_err(tp_dedup_flags_keys(perm[cp], n, off, koff.as<long long>(), key.as<unsigned long long>(),
+                                               ids.as<int>(), keep_len.as<long long>(), keep.as<int>(), s))) ||
+            (rc = cuda_err(scan_i64(keep_len.as<long long>(), keep_off.as<long long>(), n, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(scan_i32_to_i64(keep.as<int>(), keep_rank.as<long long>(), n, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(hs, keep_rank.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(hs + 1, keep_off.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+        T = hs[0];
+        TV = hs[1];
+        f_off = block_new(g->fns, sizeof(long long) * (T + 1), s);
+        f_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
+        if (!f_off || !f_vert) { rc = TPG_ENOMEM; break; }
+        if ((rc = ensure(g, fgraph, sizeof(int) * std::max<long long>(T, 1)))) break;
+        hs[2] = TV;
+        if ((rc = cuda_err(tp_gather(perm[cp], keep.as<int>(), keep_rank.as<long long>(), n, off, vert, ids.as<int>(),
+                                     keep_off.as<long long>(), (long long *)f_off->p, (int *)f_vert->p, fgraph.as<int>(),
+                                     s))) ||
+            (rc = cuda_err(cudaMemcpyAsync((long long *)f_off->p + T, hs + 2, sizeof(long long), cudaMemcpyHostToDevice,
+                                           s))) ||
+            (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+    } while (false);
+    if (rc != TPG_OK) cudaStreamSynchronize(s);
+    for (DevBuf *b : {&klen, &koff, &key, &rrank, &bounds, &rbase, &perm0, &perm1, &keep, &keep_len, &keep_off,
+                      &keep_rank, &ids, &fgraph, &tmp, &gp})
         release(g, *b);
+    if (rc) {
+        block_unref(f_off);
+        block_unref(f_vert);
+        return rc;
+    }
+    *o_off = f_off;
+    *o_vert = f_vert;
+    *oT = T;
+    *oTV = TV;
+    return TPG_OK;
+}
+
+int tpg_prime_paths_compositional(tpg_cfg *g, tpg_paths **out) {
+    if (!out) return TPG_EINVAL;
+    *out = nullptr;
+    if (!is_cfg(g)) return TPG_EHANDLE;
+    if (g->G != 1) return TPG_EINVAL;
+    if (g->N > 256 || !g->gd.smask || !g->gd.pmask) return TPG_ETOOBIG;
+    cudaStream_t s = g->stream;
+    const int n = g->N;
+    long long *hs = (long long *)g->h_small;
+    DevBuf comp, ent, ext, counts, tmp, ptr[SEG_KINDS], vptr[SEG_KINDS], soff[SEG_KINDS], svert[SEG_KINDS];
+    DevBuf ocnt, ncnt, opos, npos, rec_seg, rec_par, rec_lvl, outs, len, coff, cvert, all_off, all_vert, runs;
+    std::vector<DevBuf> lv_seg, lv_par, lv_out;
+    std::vector<long long> lv_n, lv_o;
+    Block *ioff = nullptr, *ivert = nullptr, *f_off = nullptr, *f_vert = nullptr, *f_gptr = nullptr;
+    long long TI = 0, TVI = 0, T = 0, TV = 0, O = 0, VO = 0, nseg[SEG_KINDS] = {0, 0, 0};
+    int rc = TPG_OK;
+    do {
+        if ((rc = cuda_err(cudaEventRecord(g->ev[10], s)))) break;
+        // (1) the SccInternalPPs, the SCC ids and the entry / exit flags
+        if ((rc = scc_internal(g, comp, ent, ext, &ioff, &ivert, &TI, &TVI))) break;
+        // (2) entry-exit, exit and entry paths of every SCC
+        SegList L[SEG_KINDS] = {};
+        if ((rc = ensure(g, counts, sizeof(long long) * 2 * SEG_KINDS * n)) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(n + 1))) ||
+            (rc = cuda_err(comp_segments(g->gd, comp.as<int>(), ent.as<unsigned char>(), ext.as<unsigned char>(),
+                                         counts.as<long long>(), L, false, s))))
+            break;
+        for (int c = 0; c < SEG_KINDS && rc == TPG_OK; ++c) {
+            if ((rc = ensure(g, ptr[c], sizeof(long long) * (n + 1))) || (rc = ensure(g, vptr[c], sizeof(long long) * (n + 1))) ||
+                (rc = cuda_err(scan_i64(counts.as<long long>() + (long long)c * n, ptr[c].as<long long>(), n,
+                                        tmp.as<long long>(), s))) ||
+                (rc = cuda_err(scan_i64(counts.as<long long>() + (long long)(SEG_KINDS + c) * n, vptr[c].as<long long>(), n,
+                                        tmp.as<long long>(), s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(hs + 2 * c, ptr[c].as<long long>() + n, sizeof(long long),
+                                               cudaMemcpyDeviceToHost, s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(hs + 2 * c + 1, vptr[c].as<long long>() + n, sizeof(long long),
+                                               cudaMemcpyDeviceToHost, s))))
+                break;
+        }
+        if (rc || (rc = cuda_err(cudaStreamSynchronize(s)))) break;
+        long long segv[SEG_KINDS];
+        for (int c = 0; c < SEG_KINDS; ++c) {
+            nseg[c] = hs[2 * c];
+            segv[c] = hs[2 * c + 1];
+        }
+        if (std::max({nseg[0], nseg[1], nseg[2]}) >= (long long)MAX31) { rc = TPG_ETOOBIG; break; }
+        for (int c = 0; c < SEG_KINDS && rc == TPG_OK; ++c) {
+            if ((rc = ensure(g, soff[c], sizeof(long long) * (nseg[c] + 1))) ||
+                (rc = ensure(g, svert[c], sizeof(int) * std::max(segv[c], 1LL))))
+                break;
+            hs[10 + c] = segv[c];
+            L[c] = SegList{ptr[c].as<long long>(), soff[c].as<long long>(), svert[c].as<int>(), vptr[c].as<long long>()};
+            rc = cuda_err(cudaMemcpyAsync(soff[c].as<long long>() + nseg[c], hs + 10 + c, sizeof(long long),
+                                          cudaMemcpyHostToDevice, s));
+        }
+        if (rc || (rc = cuda_err(comp_segments(g->gd, comp.as<int>(), ent.as<unsigned char>(), ext.as<unsigned char>(),
+                                               counts.as<long long>(), L, true, s))))
+            break;
+        // (3) the merge: a frontier of partial concatenations, level 0 the exit paths
+        long long level_n = nseg[SEG_EX], base = 0;
+        lv_seg.emplace_back();
+        lv_par.emplace_back();
+        if ((rc = ensure(g, lv_seg.back(), sizeof(int) * std::max(level_n, 1LL))) ||
+            (rc = ensure(g, lv_par.back(), sizeof(long long) * std::max(level_n, 1LL))) ||
+            (rc = cuda_err(comp_level0(lv_seg.back().as<int>(), lv_par.back().as<long long>(), level_n, s))))
+            break;
+        for (int d = 0; level_n > 0 && rc == TPG_OK; ++d) {
+            if (d >= 256) { rc = TPG_ECUDA; break; }  // a record chain never passes more SCCs than vertices
+            const SegList &S = d == 0 ? L[SEG_EX] : L[SEG_EE];
+            MergeLevel lv{lv_seg[d].as<int>(), level_n, base, S.off, S.vert};
+            if ((rc = ensure(g, ocnt, sizeof(long long) * level_n)) || (rc = ensure(g, ncnt, sizeof(long long) * level_n)) ||
+                (rc = ensure(g, opos, sizeof(long long) * (level_n + 1))) ||
+                (rc = ensure(g, npos, sizeof(long long) * (level_n + 1))) ||
+                (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(level_n + 1))) ||
+                (rc = cuda_err(comp_merge_level(g->gd, comp.as<int>(), lv, L[SEG_EE], L[SEG_EN], ocnt.as<long long>(),
+                                                ncnt.as<long long>(), nullptr, nullptr, nullptr, nullptr, nullptr, false,
+                                                s))) ||
+                (rc = cuda_err(scan_i64(ocnt.as<long long>(), opos.as<long long>(), level_n, tmp.as<long long>(), s))) ||
+                (rc = cuda_err(scan_i64(ncnt.as<long long>(), npos.as<long long>(), level_n, tmp.as<long long>(), s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(hs, opos.as<long long>() + level_n, sizeof(long long),
+                                               cudaMemcpyDeviceToHost, s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(hs + 1, npos.as<long long>() + level_n, sizeof(long long),
+                                               cudaMemcpyDeviceToHost, s))) ||
+                (rc = cuda_err(cudaStreamSynchronize(s))))
+                break;
+            const long long no = hs[0], nn = hs[1];
+            if (base + level_n + nn >= (long long)MAX31) { rc = TPG_ETOOBIG; break; }
+            lv_n.push_back(level_n);
+            lv_o.push_back(no);
+            lv_out.emplace_back();
+            lv_seg.emplace_back();
+            lv_par.emplace_back();
+            if ((rc = ensure(g, lv_out.back(), sizeof(int2) * std::max(no, 1LL))) ||
+                (rc = ensure(g, lv_seg.back(), sizeof(int) * std::max(nn, 1LL))) ||
+                (rc = ensure(g, lv_par.back(), sizeof(long long) * std::max(nn, 1LL))) ||
+                (rc = cuda_err(comp_merge_level(g->gd, comp.as<int>(), lv, L[SEG_EE], L[SEG_EN], nullptr, nullptr,
+                                                opos.as<long long>(), npos.as<long long>(), lv_out.back().as<int2>(),
+                                                lv_seg.back().as<int>(), lv_par.back().as<long long>(), true, s))))
+                break;
+            base += level_n;
+            level_n = nn;
+            O += no;
+        }
+        if (rc) break;
+        // every record and every completed PP in one array each
+        const long long NR = base;
+        if ((rc = ensure(g, rec_seg, sizeof(int) * std::max(NR, 1LL))) ||
+            (rc = ensure(g, rec_par, sizeof(long long) * std::max(NR, 1LL))) ||
+            (rc = ensure(g, rec_lvl, sizeof(int) * std::max(NR, 1LL))) ||
+            (rc = ensure(g, outs, sizeof(int2) * std::max(O, 1LL))))
+            break;
+        long long rb = 0, ob = 0;
+        for (size_t d = 0; d < lv_n.size() && rc == TPG_OK; ++d) {
+            if ((rc = cuda_err(cudaMemcpyAsync(rec_seg.as<int>() + rb, lv_seg[d].p, sizeof(int) * lv_n[d],
+                                               cudaMemcpyDeviceToDevice, s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(rec_par.as<long long>() + rb, lv_par[d].p, sizeof(long long) * lv_n[d],
+                                               cudaMemcpyDeviceToDevice, s))) ||
+                (rc = cuda_err(comp_fill(rec_lvl.as<int>() + rb, lv_n[d], (int)d, s))) ||
+                (lv_o[d] > 0 && (rc = cuda_err(cudaMemcpyAsync(outs.as<int2>() + ob, lv_out[d].p, sizeof(int2) * lv_o[d],
+                                                               cudaMemcpyDeviceToDevice, s)))))
+                break;
+            rb += lv_n[d];
+            ob += lv_o[d];
+        }
+        if (rc) break;
+        // (4) the crossing PPs as vertex sequences
+        if ((rc = ensure(g, len, sizeof(long long) * std::max(O, 1LL))) ||
+            (rc = ensure(g, coff, sizeof(long long) * (O + 1))) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(O + 1))) ||
+            (rc = cuda_err(comp_materialise(outs.as<int2>(), O, rec_seg.as<int>(), rec_par.as<long long>(),
+                                            rec_lvl.as<int>(), L[SEG_EE], L[SEG_EX], L[SEG_EN], len.as<long long>(),
+                                            nullptr, nullptr, false, s))) ||
+            (rc = cuda_err(scan_i64(len.as<long long>(), coff.as<long long>(), O, tmp.as<long long>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(hs, coff.as<long long>() + O, sizeof(long long), cudaMemcpyDeviceToHost, s))) ||
+            (rc = cuda_err(cudaStreamSynchronize(s))))
+            break;
+        VO = O > 0 ? hs[0] : 0;
+        if ((rc = ensure(g, cvert, sizeof(int) * std::max(VO, 1LL))) ||
+            (rc = cuda_err(comp_materialise(outs.as<int2>(), O, rec_seg.as<int>(), rec_par.as<long long>(),
+                                            rec_lvl.as<int>(), L[SEG_EE], L[SEG_EX], L[SEG_EN], nullptr,
+                                            coff.as<long long>(), cvert.as<int>(), true, s))))
+            break;
+        // (5) SccInternalPPs and crossing PPs in one list, then canonical order
+        const long long PA = TI + O, VA = TVI + VO;
+        hs[12] = VA;
+        if ((rc = ensure(g, all_off, sizeof(long long) * (PA + 1))) ||
+            (rc = ensure(g, all_vert, sizeof(int) * std::max(VA, 1LL))) ||
+            (rc = ensure(g, runs, sizeof(int) * std::max(PA, 1LL))) ||
+            (rc = cuda_err(comp_append((const long long *)ioff->p, (const int *)ivert->p, TI, 0, 0,
+                                       all_off.as<long long>(), all_vert.as<int>(), s))) ||
+            (rc = cuda_err(comp_append(coff.as<long long>(), cvert.as<int>(), O, TI, TVI, all_off.as<long long>(),
+                                       all_vert.as<int>(), s))) ||
+            (rc = cuda_err(cudaMemcpyAsync(all_off.as<long long>() + PA, hs + 12, sizeof(long long),
+                                           cudaMemcpyHostToDevice, s))) ||
+            (rc = cuda_err(comp_run_starts(runs.as<int>(), PA, TI > 0 ? TI : 0, s))))
+            break;
+        if (PA > 0) {
+            if ((rc = sort_paths(g, all_off.as<long long>(), all_vert.as<int>(), PA, VA, runs.as<int>(), &f_off, &f_vert,
+                                 &T, &TV)))
+                break;
+        } else {
+            f_off = block_new(g->fns, sizeof(long long), s);
+            f_vert = block_new(g->fns, 16, s);
+            if (!f_off || !f_vert || cudaMemsetAsync(f_off->p, 0, sizeof(long long), s)) { rc = TPG_ENOMEM; break; }
+        }
+        f_gptr = one_graph_ptr(g, T);
+        if (!f_gptr) { rc = TPG_ENOMEM; break; }
+        if ((rc = cuda_err(cudaEventRecord(g->ev[11], s))) || (rc = cuda_err(cudaStreamSynchronize(s)))) break;
+        cudaEventElapsedTime(&g->stats.t_compositional_ms, g->ev[10], g->ev[11]);
+        g->stats.comp_entry_exit_paths = nseg[SEG_EE];
+        g->stats.comp_exit_paths = nseg[SEG_EX];
+        g->stats.comp_entry_paths = nseg[SEG_EN];
+        g->stats.comp_crossing_pps = O;
+    } while (false);
+    if (rc != TPG_OK) cudaStreamSynchronize(s);
+    for (DevBuf *b : {&comp, &ent, &ext, &counts, &tmp, &ocnt, &ncnt, &opos, &npos, &rec_seg, &rec_par, &rec_lvl, &outs,
+                      &len, &coff, &cvert, &all_off, &all_vert, &runs})
+        release(g, *b);
+    for (int c = 0; c < SEG_KINDS; ++c)
+        for (DevBuf *b : {&ptr[c], &vptr[c], &soff[c], &svert[c]}) release(g, *b);
+    for (auto *v : {&lv_seg, &lv_par, &lv_out})
+        for (auto &b : *v) release(g, b);
+    block_unref(ioff);
+    block_unref(ivert);
     if (rc == TPG_OK) rc = make_result(g, f_off, f_vert, f_gptr, T, TV, out);
     block_unref(f_off);
     block_unref(f_vert);

@@ -95,6 +95,11 @@ class _Stats(ctypes.Structure):
         ("t_scc_ms", ctypes.c_float),
         ("scc_pps", ctypes.c_int64),
         ("scc_internal_pps", ctypes.c_int64),
+        ("t_compositional_ms", ctypes.c_float),
+        ("comp_entry_exit_paths", ctypes.c_int64),
+        ("comp_exit_paths", ctypes.c_int64),
+        ("comp_entry_paths", ctypes.c_int64),
+        ("comp_crossing_pps", ctypes.c_int64),
     ]
 
 
@@ -142,6 +147,7 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_prime_paths_pervertex.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_scc_internal_pps.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_scc_ids.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+        lib.tpg_prime_paths_compositional.argtypes = [P, ctypes.POINTER(ctypes.POINTER(_Paths))]
         lib.tpg_free.argtypes = [P]
         lib.tpg_free.restype = None
         lib.tpg_set_stream.argtypes = [P, P]
@@ -191,7 +197,7 @@ def load_library(path: str | None = None, build: bool = False, install_torch_all
         lib.tpg_prime_paths_noalloc.restype = ctypes.c_int
         for name in ("tpg_load_cfg", "tpg_load_cfg_device", "tpg_load_cfg_batch", "tpg_prime_paths",
                      "tpg_test_paths", "tpg_test_paths_greedy", "tpg_prime_paths_pervertex", "tpg_scc_ids",
-                     "tpg_scc_internal_pps", "tpg_set_stream",
+                     "tpg_scc_internal_pps", "tpg_prime_paths_compositional", "tpg_set_stream",
                      "tpg_set_result_location",
                      "tpg_set_allocator",
                      "tpg_get_stats", "tpg_set_tile_shape", "tpg_set_work_split", "tpg_set_capacity",
@@ -457,6 +463,14 @@ def tpg_scc_internal_pps(cfg: Cfg) -> Paths:
     """The SccInternalPPs of every SCC (Def. 9), canonical order."""
     out = ctypes.POINTER(_Paths)()
     _check(load_library().tpg_scc_internal_pps(cfg.handle, ctypes.byref(out)), "tpg_scc_internal_pps")
+    return Paths(out)
+
+
+def tpg_prime_paths_compositional(cfg: Cfg) -> Paths:
+    """The PPs by the SCC-compositional route (same list as tpg_prime_paths)."""
+    out = ctypes.POINTER(_Paths)()
+    _check(load_library().tpg_prime_paths_compositional(cfg.handle, ctypes.byref(out)),
+           "tpg_prime_paths_compositional")
     return Paths(out)
 
 
