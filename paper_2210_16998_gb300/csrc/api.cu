@@ -2292,6 +2292,7 @@ int tpg_prime_paths_compositional(tpg_cfg *g, tpg_paths **out) {
     const int n = g->N;
     long long *hs = (long long *)g->h_small;
     DevBuf comp, ent, ext, counts, tmp, ptr[SEG_KINDS], vptr[SEG_KINDS], soff[SEG_KINDS], svert[SEG_KINDS];
+    DevBuf tcnt, tpos, tvert, tlen, tp_pos[SEG_KINDS], tp_vpos[SEG_KINDS];
     DevBuf ocnt, ncnt, opos, npos, rec_seg, rec_par, rec_lvl, outs, len, coff, cvert, all_off, all_vert, runs;
     std::vector<DevBuf> lv_seg, lv_par, lv_out;
     std::vector<long long> lv_n, lv_o;
@@ -2302,24 +2303,53 @@ int tpg_prime_paths_compositional(tpg_cfg *g, tpg_paths **out) {
         if ((rc = cuda_err(cudaEventRecord(g->ev[10], s)))) break;
         // (1) the SccInternalPPs, the SCC ids and the entry / exit flags
         if ((rc = scc_internal(g, comp, ent, ext, &ioff, &ivert, &TI, &TVI))) break;
-        // (2) entry-exit, exit and entry paths of every SCC
+        // (2) entry-exit, exit and entry paths of every SCC: prefix tasks of at
+        // most D vertices, then one depth-first walk below each D-vertex prefix
+        // (deeper prefixes until there are enough tasks to spread a large SCC)
         SegList L[SEG_KINDS] = {};
-        if ((rc = ensure(g, counts, sizeof(long long) * 2 * SEG_KINDS * n)) ||
-            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(n + 1))) ||
-            (rc = cuda_err(comp_segments(g->gd, comp.as<int>(), ent.as<unsigned char>(), ext.as<unsigned char>(),
-                                         counts.as<long long>(), L, false, s))))
+        int D = 0;
+        long long NT = 0;
+        if ((rc = ensure(g, tcnt, sizeof(long long) * (n + 1))) || (rc = ensure(g, tpos, sizeof(long long) * (n + 1))) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(n + 1))))
+            break;
+        for (D = std::min(n, 8);; D = std::min(n, D + 4)) {
+            if ((rc = cuda_err(comp_prefix_tasks(g->gd, comp.as<int>(), D, tcnt.as<long long>(), nullptr, nullptr, nullptr,
+                                                 false, s))) ||
+                (rc = cuda_err(scan_i64(tcnt.as<long long>(), tpos.as<long long>(), n, tmp.as<long long>(), s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(hs, tpos.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost,
+                                               s))) ||
+                (rc = cuda_err(cudaStreamSynchronize(s))))
+                break;
+            NT = hs[0];
+            if (NT >= (1 << 16) || D >= n || D >= 32) break;
+        }
+        if (rc) break;
+        if ((rc = ensure(g, tvert, sizeof(int) * std::max(NT * D, 1LL))) ||
+            (rc = ensure(g, tlen, sizeof(int) * std::max(NT, 1LL))) ||
+            (rc = cuda_err(comp_prefix_tasks(g->gd, comp.as<int>(), D, nullptr, tpos.as<long long>(), tvert.as<int>(),
+                                             tlen.as<int>(), true, s))) ||
+            (rc = ensure(g, counts, sizeof(long long) * 2 * SEG_KINDS * std::max(NT, 1LL))) ||
+            (rc = ensure(g, tmp, sizeof(long long) * scan_tmp_elems(NT + 1))))
+            break;
+        SegTaskOut to{};
+        if ((rc = cuda_err(comp_segments(g->gd, comp.as<int>(), ent.as<unsigned char>(), ext.as<unsigned char>(), D, NT,
+                                         tvert.as<int>(), tlen.as<int>(), counts.as<long long>(), to, false, s))))
             break;
         for (int c = 0; c < SEG_KINDS && rc == TPG_OK; ++c) {
-            if ((rc = ensure(g, ptr[c], sizeof(long long) * (n + 1))) || (rc = ensure(g, vptr[c], sizeof(long long) * (n + 1))) ||
-                (rc = cuda_err(scan_i64(counts.as<long long>() + (long long)c * n, ptr[c].as<long long>(), n,
+            if ((rc = ensure(g, tp_pos[c], sizeof(long long) * (NT + 1))) ||
+                (rc = ensure(g, tp_vpos[c], sizeof(long long) * (NT + 1))) ||
+                (rc = ensure(g, ptr[c], sizeof(long long) * (n + 1))) || (rc = ensure(g, vptr[c], sizeof(long long) * (n + 1))) ||
+                (rc = cuda_err(scan_i64(counts.as<long long>() + (long long)c * NT, tp_pos[c].as<long long>(), NT,
                                         tmp.as<long long>(), s))) ||
-                (rc = cuda_err(scan_i64(counts.as<long long>() + (long long)(SEG_KINDS + c) * n, vptr[c].as<long long>(), n,
-                                        tmp.as<long long>(), s))) ||
-                (rc = cuda_err(cudaMemcpyAsync(hs + 2 * c, ptr[c].as<long long>() + n, sizeof(long long),
+                (rc = cuda_err(scan_i64(counts.as<long long>() + (long long)(SEG_KINDS + c) * NT,
+                                        tp_vpos[c].as<long long>(), NT, tmp.as<long long>(), s))) ||
+                (rc = cuda_err(cudaMemcpyAsync(hs + 2 * c, tp_pos[c].as<long long>() + NT, sizeof(long long),
                                                cudaMemcpyDeviceToHost, s))) ||
-                (rc = cuda_err(cudaMemcpyAsync(hs + 2 * c + 1, vptr[c].as<long long>() + n, sizeof(long long),
+                (rc = cuda_err(cudaMemcpyAsync(hs + 2 * c + 1, tp_vpos[c].as<long long>() + NT, sizeof(long long),
                                                cudaMemcpyDeviceToHost, s))))
                 break;
+            to.pos[c] = tp_pos[c].as<long long>();
+            to.vpos[c] = tp_vpos[c].as<long long>();
         }
         if (rc || (rc = cuda_err(cudaStreamSynchronize(s)))) break;
         long long segv[SEG_KINDS];
@@ -2328,17 +2358,24 @@ int tpg_prime_paths_compositional(tpg_cfg *g, tpg_paths **out) {
             segv[c] = hs[2 * c + 1];
         }
         if (std::max({nseg[0], nseg[1], nseg[2]}) >= (long long)MAX31) { rc = TPG_ETOOBIG; break; }
+        SegPtrs sp{};
         for (int c = 0; c < SEG_KINDS && rc == TPG_OK; ++c) {
             if ((rc = ensure(g, soff[c], sizeof(long long) * (nseg[c] + 1))) ||
                 (rc = ensure(g, svert[c], sizeof(int) * std::max(segv[c], 1LL))))
                 break;
             hs[10 + c] = segv[c];
             L[c] = SegList{ptr[c].as<long long>(), soff[c].as<long long>(), svert[c].as<int>(), vptr[c].as<long long>()};
+            to.off[c] = soff[c].as<long long>();
+            to.vert[c] = svert[c].as<int>();
+            sp.ptr[c] = ptr[c].as<long long>();
+            sp.vptr[c] = vptr[c].as<long long>();
             rc = cuda_err(cudaMemcpyAsync(soff[c].as<long long>() + nseg[c], hs + 10 + c, sizeof(long long),
                                           cudaMemcpyHostToDevice, s));
         }
-        if (rc || (rc = cuda_err(comp_segments(g->gd, comp.as<int>(), ent.as<unsigned char>(), ext.as<unsigned char>(),
-                                               counts.as<long long>(), L, true, s))))
+        if (rc || (rc = cuda_err(comp_segments(g->gd, comp.as<int>(), ent.as<unsigned char>(), ext.as<unsigned char>(), D,
+                                               NT, tvert.as<int>(), tlen.as<int>(), counts.as<long long>(), to, true,
+                                               s))) ||
+            (rc = cuda_err(comp_group_ptrs(n, tpos.as<long long>(), to, sp, s))))
             break;
         // (3) the merge: a frontier of partial concatenations, level 0 the exit paths
         long long level_n = nseg[SEG_EX], base = 0;
@@ -2461,7 +2498,8 @@ int tpg_prime_paths_compositional(tpg_cfg *g, tpg_paths **out) {
                       &len, &coff, &cvert, &all_off, &all_vert, &runs})
         release(g, *b);
     for (int c = 0; c < SEG_KINDS; ++c)
-        for (DevBuf *b : {&ptr[c], &vptr[c], &soff[c], &svert[c]}) release(g, *b);
+        for (DevBuf *b : {&ptr[c], &vptr[c], &soff[c], &svert[c], &tp_pos[c], &tp_vpos[c]}) release(g, *b);
+    for (DevBuf *b : {&tcnt, &tpos, &tvert, &tlen}) release(g, *b);
     for (auto *v : {&lv_seg, &lv_par, &lv_out})
         for (auto &b : *v) release(g, b);
     block_unref(ioff);

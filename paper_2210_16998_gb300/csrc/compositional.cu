@@ -10,12 +10,14 @@
 // on it), consecutive parts joined by arcs between SCCs.  The PPs inside one
 // SCC are the SccInternalPPs (Def. 9, scc.cu).
 //
-// GPU design.  Extraction: one thread per first vertex walks every acyclic
-// simple path inside its SCC depth-first (successors ascending, so each
-// thread's paths come out in canonical order, and the threads' outputs in
-// first-vertex order), holding the path's vertex set as a bitset of at most
-// 8 words, and tests the three kinds with the vertex bitsets of the graph; a
-// count pass sizes the lists.  Merge: a level-synchronous frontier over
+// GPU design.  Extraction: the acyclic simple paths inside each SCC of at
+// most D vertices are enumerated first, one thread per first vertex; each
+// becomes a task, and one thread per task walks the paths that extend a
+// D-vertex prefix depth-first, holding the path's vertex set as a bitset of
+// at most 8 words, and tests the three kinds with the vertex bitsets of the
+// graph (a large SCC is so spread over many threads); tasks stay grouped by
+// first vertex, so each kind's list is grouped by first vertex; count
+// passes size the lists.  Merge: a level-synchronous frontier over
 // partial concatenations (records {segment, parent record}), level 0 the
 // exit paths; a record ending at x is joined, over every arc x -> y to
 // another SCC, to the entry paths starting at y (a completed PP) and to the
@@ -40,73 +42,150 @@ unsigned grid_for(long long n, int block = 128) {
     return (unsigned)b;
 }
 
+// Prefix tasks: every acyclic simple path inside an SCC of at most D
+// vertices, walked depth-first from each first vertex (count pass:
+// task_cnt[r]; write pass: the paths at task_pos[r], D ints each, and their
+// lengths).  Each is one extraction task (below).
 template <bool WRITE>
-__global__ void segments_kernel(GraphDev g, const int *comp, const unsigned char *is_entry,
-                                const unsigned char *is_exit, long long *counts, SegList ee, SegList ex, SegList en) {
-    const int n = g.N, W = g.W;
+__global__ void prefix_kernel(GraphDev g, const int *comp, int D, long long *task_cnt, const long long *task_pos,
+                              int *task_vert, int *task_len) {
+    const int n = g.N;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int path[CMAX_N], eidx[CMAX_N];
     unsigned vis[CW];
 #pragma unroll
     for (int j = 0; j < CW; ++j) vis[j] = 0u;
-    long long np[SEG_KINDS] = {0, 0, 0}, nv[SEG_KINDS] = {0, 0, 0};
-    const SegList L[SEG_KINDS] = {ee, ex, en};
     const int cr = comp[r];
-    // the kinds of the path path[0..d] (its vertex set in vis), counted or written
-    auto visit = [&](int d) {
-        const int last = path[d];
-        bool pred_in = true, succ_in = true;
-        for (int j = 0; j < W; ++j) {
-            pred_in &= (g.pmask[(long long)r * W + j] & ~vis[j]) == 0u;
-            succ_in &= (g.smask[(long long)last * W + j] & ~vis[j]) == 0u;
+    long long c = 0;
+    auto emit = [&](int d) {
+        if (WRITE) {
+            const long long t = task_pos[r] + c;
+            for (int i = 0; i <= d; ++i) task_vert[t * D + i] = path[i];
+            task_len[t] = d + 1;
         }
-        const bool kind[SEG_KINDS] = {is_entry[r] && is_exit[last], is_exit[last] && pred_in,
-                                      is_entry[r] && succ_in};
-        for (int c = 0; c < SEG_KINDS; ++c) {
-            if (!kind[c]) continue;
-            if (WRITE) {
-                const long long p = L[c].ptr[r] + np[c], v0 = L[c].vptr[r] + nv[c];
-                L[c].off[p] = v0;
-                for (int t = 0; t <= d; ++t) L[c].vert[v0 + t] = path[t];
-            }
-            ++np[c];
-            nv[c] += d + 1;
-        }
+        ++c;
     };
-    // depth-first over the acyclic simple paths from r inside its SCC,
-    // successors in ascending order (canonical order of the visits)
     int d = 0;
     path[0] = r;
     eidx[0] = g.rp[r];
     vis[r >> 5] |= 1u << (r & 31);
-    visit(0);
+    emit(0);
     for (;;) {
         const int x = path[d];
         int w = -1;
-        while (eidx[d] < g.rp[x + 1]) {
+        while (d + 1 < D && eidx[d] < g.rp[x + 1]) {
             const int y = g.col[eidx[d]++];
             if (comp[y] == cr && !((vis[y >> 5] >> (y & 31)) & 1u)) {
                 w = y;
                 break;
             }
         }
-        if (w >= 0 && d + 1 < CMAX_N) {
+        if (w >= 0) {
             ++d;
             path[d] = w;
             eidx[d] = g.rp[w];
             vis[w >> 5] |= 1u << (w & 31);
-            visit(d);
+            emit(d);
             continue;
         }
         if (d == 0) break;
         vis[x >> 5] &= ~(1u << (x & 31));
         --d;
     }
-    if (!WRITE) {
+    if (!WRITE) task_cnt[r] = c;
+}
+
+// One extraction task: its prefix path, and, when the prefix has D
+// vertices, every acyclic simple path inside the SCC that extends it,
+// depth-first; each path is sorted into entry-exit, exit and entry paths
+// (count pass: counts[kind][t] paths and counts[3 + kind][t] vertices;
+// write pass at the scanned per-task offsets pos[kind] / vpos[kind]).
+template <bool WRITE>
+__global__ void segments_kernel(GraphDev g, const int *comp, const unsigned char *is_entry,
+                                const unsigned char *is_exit, int D, long long T, const int *task_vert,
+                                const int *task_len, long long *counts, SegTaskOut out) {
+    const int n = g.N, W = g.W;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T;
+         t += (long long)gridDim.x * blockDim.x) {
+        int path[CMAX_N], eidx[CMAX_N];
+        unsigned vis[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) vis[j] = 0u;
+        const int len = task_len[t];
+        for (int i = 0; i < len; ++i) {
+            const int v = task_vert[t * D + i];
+            path[i] = v;
+            vis[v >> 5] |= 1u << (v & 31);
+        }
+        const int r = path[0], cr = comp[r];
+        long long np[SEG_KINDS] = {0, 0, 0}, nv[SEG_KINDS] = {0, 0, 0};
+        auto visit = [&](int d) {
+            const int last = path[d];
+            bool pred_in = true, succ_in = true;
+            for (int j = 0; j < W; ++j) {
+                pred_in &= (g.pmask[(long long)r * W + j] & ~vis[j]) == 0u;
+                succ_in &= (g.smask[(long long)last * W + j] & ~vis[j]) == 0u;
+            }
+            const bool kind[SEG_KINDS] = {is_entry[r] && is_exit[last], is_exit[last] && pred_in,
+                                          is_entry[r] && succ_in};
+            for (int c = 0; c < SEG_KINDS; ++c) {
+                if (!kind[c]) continue;
+                if (WRITE) {
+                    const long long p = out.pos[c][t] + np[c], v0 = out.vpos[c][t] + nv[c];
+                    out.off[c][p] = v0;
+                    for (int i = 0; i <= d; ++i) out.vert[c][v0 + i] = path[i];
+                }
+                ++np[c];
+                nv[c] += d + 1;
+            }
+        };
+        const int floor_d = len - 1;
+        int d = floor_d;
+        visit(d);
+        if (len == D) {
+            eidx[d] = g.rp[path[d]];
+            for (;;) {
+                const int x = path[d];
+                int w = -1;
+                while (eidx[d] < g.rp[x + 1]) {
+                    const int y = g.col[eidx[d]++];
+                    if (comp[y] == cr && !((vis[y >> 5] >> (y & 31)) & 1u)) {
+                        w = y;
+                        break;
+                    }
+                }
+                if (w >= 0 && d + 1 < CMAX_N) {
+                    ++d;
+                    path[d] = w;
+                    eidx[d] = g.rp[w];
+                    vis[w >> 5] |= 1u << (w & 31);
+                    visit(d);
+                    continue;
+                }
+                if (d == floor_d) break;
+                vis[x >> 5] &= ~(1u << (x & 31));
+                --d;
+            }
+        }
+        if (!WRITE) {
+            for (int c = 0; c < SEG_KINDS; ++c) {
+                counts[(long long)c * T + t] = np[c];
+                counts[(long long)(SEG_KINDS + c) * T + t] = nv[c];
+            }
+        }
+        (void)n;
+    }
+}
+
+// per first vertex v: where its paths start in each kind's list (the scans
+// over tasks, read at v's first task)
+__global__ void group_ptr_kernel(int n, const long long *task_pos, SegTaskOut out, SegPtrs ptrs) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
+        const long long t = task_pos[v];
         for (int c = 0; c < SEG_KINDS; ++c) {
-            counts[(long long)c * n + r] = np[c];
-            counts[(long long)(SEG_KINDS + c) * n + r] = nv[c];
+            ptrs.ptr[c][v] = out.pos[c][t];
+            ptrs.vptr[c][v] = out.vpos[c][t];
         }
     }
 }
@@ -203,16 +282,35 @@ __global__ void append_kernel(const long long *off, const int *vert, long long n
 
 }  // namespace
 
-cudaError_t comp_segments(const GraphDev &g, const int *comp, const unsigned char *is_entry,
-                          const unsigned char *is_exit, long long *counts, const SegList *lists, bool write,
-                          cudaStream_t s) {
-    if (g.N > CMAX_N || g.W > CW || !g.smask || !g.pmask) return cudaErrorInvalidValue;
+cudaError_t comp_prefix_tasks(const GraphDev &g, const int *comp, int D, long long *task_cnt,
+                              const long long *task_pos, int *task_vert, int *task_len, bool write, cudaStream_t s) {
+    if (g.N > CMAX_N || g.W > CW || D < 1 || D > CMAX_N) return cudaErrorInvalidValue;
     if (write)
-        segments_kernel<true><<<grid_for(g.N, 32), 32, 0, s>>>(g, comp, is_entry, is_exit, counts, lists[SEG_EE],
-                                                                lists[SEG_EX], lists[SEG_EN]);
+        prefix_kernel<true><<<grid_for(g.N, 32), 32, 0, s>>>(g, comp, D, task_cnt, task_pos, task_vert, task_len);
     else
-        segments_kernel<false><<<grid_for(g.N, 32), 32, 0, s>>>(g, comp, is_entry, is_exit, counts, lists[SEG_EE],
-                                                                 lists[SEG_EX], lists[SEG_EN]);
+        prefix_kernel<false><<<grid_for(g.N, 32), 32, 0, s>>>(g, comp, D, task_cnt, task_pos, task_vert, task_len);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t comp_segments(const GraphDev &g, const int *comp, const unsigned char *is_entry,
+                          const unsigned char *is_exit, int D, long long T, const int *task_vert, const int *task_len,
+                          long long *counts, const SegTaskOut &out, bool write, cudaStream_t s) {
+    if (g.N > CMAX_N || g.W > CW || !g.smask || !g.pmask) return cudaErrorInvalidValue;
+    if (T <= 0) return cudaSuccess;
+    if (write)
+        segments_kernel<true><<<grid_for(T, 64), 64, 0, s>>>(g, comp, is_entry, is_exit, D, T, task_vert, task_len,
+                                                             counts, out);
+    else
+        segments_kernel<false><<<grid_for(T, 64), 64, 0, s>>>(g, comp, is_entry, is_exit, D, T, task_vert, task_len,
+                                                              counts, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t comp_group_ptrs(int n, const long long *task_pos, const SegTaskOut &out, const SegPtrs &ptrs,
+                            cudaStream_t s) {
+    group_ptr_kernel<<<grid_for(n + 1, 128), 128, 0, s>>>(n, task_pos, out, ptrs);
     note_launch();
     return cudaGetLastError();
 }

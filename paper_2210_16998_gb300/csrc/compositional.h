@@ -18,13 +18,34 @@ struct SegList {
     const long long *vptr;  // [n + 1] vertex offset of the paths starting at v
 };
 
-// count pass (counts: [SEG_KINDS][n] paths and [SEG_KINDS][n] vertices per
-// first vertex) or write pass (lists from the scans of those counts): every
-// acyclic simple path inside one SCC, by a depth-first search per first
-// vertex, sorted into entry-exit, exit and entry paths
+// Per-task outputs of the extraction: per kind, the scanned path and vertex
+// offsets of every task (pos[c][T] and vpos[c][T] are the totals) and the
+// kind's offsets / vertices arrays.
+struct SegTaskOut {
+    const long long *pos[SEG_KINDS];
+    const long long *vpos[SEG_KINDS];
+    long long *off[SEG_KINDS];
+    int *vert[SEG_KINDS];
+};
+struct SegPtrs {
+    long long *ptr[SEG_KINDS];
+    long long *vptr[SEG_KINDS];
+};
+
+// prefix tasks: every acyclic simple path inside one SCC of at most D
+// vertices, per first vertex (count pass: task_cnt[n]; write pass: D ints
+// per task at task_pos, and the task's length)
+cudaError_t comp_prefix_tasks(const GraphDev &g, const int *comp, int D, long long *task_cnt,
+                              const long long *task_pos, int *task_vert, int *task_len, bool write, cudaStream_t s);
+// extraction: each task's prefix and, for D-vertex prefixes, every acyclic
+// simple path inside the SCC that extends it, sorted into entry-exit, exit
+// and entry paths; count pass (counts: [2 * SEG_KINDS][T]) or write pass
 cudaError_t comp_segments(const GraphDev &g, const int *comp, const unsigned char *is_entry,
-                          const unsigned char *is_exit, long long *counts, const SegList *lists, bool write,
-                          cudaStream_t s);
+                          const unsigned char *is_exit, int D, long long T, const int *task_vert, const int *task_len,
+                          long long *counts, const SegTaskOut &out, bool write, cudaStream_t s);
+// each kind's per-first-vertex pointers (n + 1) from the per-task scans
+cudaError_t comp_group_ptrs(int n, const long long *task_pos, const SegTaskOut &out, const SegPtrs &ptrs,
+                            cudaStream_t s);
 
 // One level of the merge: a record is a partial concatenation ending in
 // segment seg (an exit path at level 0, an entry-exit path later) with its
