@@ -160,6 +160,9 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 #ifndef TPG_ENUM_MASK
 #define TPG_ENUM_MASK 1  // evaluate paths with the vertex bitsets where they exist
 #endif
+#ifndef TPG_ENUM_PREFETCH
+#define TPG_ENUM_PREFETCH 1  // load a warp's next tile of records while it processes the current one
+#endif
 #ifndef TPG_ENUM_LANEWISE
 #define TPG_ENUM_LANEWISE 1  // lane-wise child writing when it needs no more rounds than dealing
 #endif
@@ -480,6 +483,24 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                 pos_p += (int)__reduce_add_sync(0xffffffffu, sp);
             }
 
+#if TPG_ENUM_PREFETCH
+            // the records of the next tile load while this one is processed
+            int2 pfl[ITEMS];
+            unsigned pcw[ITEMS], pvis[ITEMS][W];
+            auto load_tile = [&](int t0) {
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) {
+                    const int i = t0 + j * 32 + lane;
+                    if (i < hi) {
+                        pfl[j] = __ldcg(in_fl + i);
+                        pcw[j] = __ldcg(in_cnt + i);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) pvis[j][w] = __ldcg(in_vis + w * a.lvl_cap + i);
+                    }
+                }
+            };
+            if (lo < hi) load_tile(lo);
+#endif
             for (int t0 = lo; t0 < hi; t0 += WT) {
                 int first[ITEMS], last[ITEMS];
                 unsigned cw[ITEMS];
@@ -488,14 +509,21 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                 for (int j = 0; j < ITEMS; ++j) {
                     const int i = t0 + j * 32 + lane;
                     if (i < hi) {
+#if TPG_ENUM_PREFETCH
+                        const int2 fl = pfl[j];
+                        cw[j] = pcw[j];
+#pragma unroll
+                        for (int w = 0; w < W; ++w) vis[j][w] = pvis[j][w];
+#else
                         const int2 fl = __ldcg(in_fl + i);
+                        cw[j] = __ldcg(in_cnt + i);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) vis[j][w] = __ldcg(in_vis + w * a.lvl_cap + i);
+#endif
                         // clamped into range before any use as an index (see
                         // the counting pass)
                         first[j] = (int)min((unsigned)fl.x, (unsigned)(g.N - 1));
                         last[j] = (int)min((unsigned)fl.y, (unsigned)(g.N - 1));
-                        cw[j] = __ldcg(in_cnt + i);
-#pragma unroll
-                        for (int w = 0; w < W; ++w) vis[j][w] = __ldcg(in_vis + w * a.lvl_cap + i);
                     } else {
                         first[j] = -1;
                         last[j] = 0;
@@ -504,6 +532,9 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                         for (int w = 0; w < W; ++w) vis[j][w] = 0u;
                     }
                 }
+#if TPG_ENUM_PREFETCH
+                if (t0 + WT < hi) load_tile(t0 + WT);
+#endif
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) {
                     const int i = t0 + j * 32 + lane;
