@@ -31,6 +31,8 @@ CASES = [
     ("diamond-7", lambda: G.diamond_chain(7)),
     ("ring-tail-9", lambda: ring_with_tail(9)),
     ("self-loop", lambda: G.CFG(4, *G.csr_from_arcs(4, [(0, 1), (1, 1), (1, 2), (2, 1), (2, 3)]), 0, 3, "loop")),
+    ("two-vertices", lambda: G.CFG(2, *G.csr_from_arcs(2, [(0, 1)]), 0, 1, "edge")),
+    ("complete-5-wrapped", lambda: wrap_digraph(G.complete_digraph(5))),
 ] + [(f"cfg-{s}", (lambda s=s: G.random_cfg(G.BATCH_SEED0 + s))) for s in (3, 21, 24, 25, 30, 47)] + [
     (f"digraph-{s}", (lambda s=s: wrap_digraph(G.random_digraph(6, 0.4, s, self_loops=True)))) for s in range(5)]
 

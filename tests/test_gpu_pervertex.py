@@ -36,6 +36,7 @@ CASES = [
     ("config1", G.config1_cfg),
     ("diamond-8", lambda: G.diamond_chain(8)),
     ("ring-tail-12", lambda: ring_with_tail(12)),
+    ("two-vertices", lambda: G.CFG(2, *G.csr_from_arcs(2, [(0, 1)]), 0, 1, "edge")),
     ("binarised-cfg-3", lambda: G.binarise_switches(G.random_cfg(G.BATCH_SEED0 + 3))),
     ("binarised-cfg-25", lambda: G.binarise_switches(G.random_cfg(G.BATCH_SEED0 + 25))),
     ("binarised-digraph", lambda: G.binarise_switches(wrap_digraph(G.random_digraph(6, 0.3, 2, self_loops=True)))),

@@ -42,6 +42,8 @@ CASES = [
     ("diamond-10", lambda: G.diamond_chain(10)),
     ("ring-tail-40", lambda: ring_with_tail(40)),
     ("while-ring-200", lambda: ring_with_tail(200)),
+    ("two-vertices", lambda: G.CFG(2, *G.csr_from_arcs(2, [(0, 1)]), 0, 1, "edge")),
+    ("complete-5-wrapped", lambda: wrap_digraph(G.complete_digraph(5))),
 ] + [(f"cfg-{s}", (lambda s=s: G.random_cfg(G.BATCH_SEED0 + s))) for s in (3, 21, 24, 25, 47, 54)] + [
     (f"digraph-{s}", (lambda s=s: wrap_digraph(G.random_digraph(7, 0.35, s, self_loops=True)))) for s in range(4)]
 
