@@ -1181,12 +1181,6 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
             if (pp_to_tp && cuda_err(tp_index_map(nullptr, nullptr, nullptr, P, pp_to_tp, s))) rc = TPG_ECUDA;
             break;
         }
-        tp_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
-        if (!tp_vert) { rc = TPG_ENOMEM; break; }
-        if (cuda_err(tp_write(pp_off, pp_vert, pp_graph, P, g->gd, (const long long *)tp_off->p, (int *)tp_vert->p, s))) {
-            rc = TPG_ECUDA;
-            break;
-        }
         // graphs that own at least one PP: one sorted run each means no merge
         long long graphs_with_pp = 1;
         if (g->G > 1) {
@@ -1199,6 +1193,13 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
         if (R == graphs_with_pp) {
             // every graph's TPs form one run: sorted, and distinct PPs with a
             // common first vertex give distinct TPs, so nothing to dedup
+            tp_vert = block_new(g->fns, sizeof(int) * std::max<long long>(TV, 1), s);
+            if (!tp_vert) { rc = TPG_ENOMEM; break; }
+            if (cuda_err(tp_write(pp_off, pp_vert, pp_graph, P, g->gd, (const long long *)tp_off->p, (int *)tp_vert->p,
+                                  s))) {
+                rc = TPG_ECUDA;
+                break;
+            }
             f_off = tp_off;
             f_vert = tp_vert;
             tp_off = tp_vert = nullptr;
@@ -1230,8 +1231,8 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
         unsigned long long *key = g->tp_key.as<unsigned long long>();
         if (cuda_err(tp_key_lengths((const long long *)tp_off->p, P, kbits, g->s_len.as<long long>(), s)) ||
             cuda_err(scan_i64(g->s_len.as<long long>(), key_off, P, g->s_tmp.as<long long>(), s)) ||
-            cuda_err(tp_write_keys((const long long *)tp_off->p, (const int *)tp_vert->p, P, kbits, key_off, key,
-                                   s))) {
+            cuda_err(tp_write_keys_parts(pp_off, pp_vert, pp_graph, P, g->gd, (const long long *)tp_off->p, kbits,
+                                         key_off, key, s))) {
             rc = TPG_ECUDA;
             break;
         }
@@ -1277,8 +1278,9 @@ int run_test_paths(tpg_cfg *g, Block **o_off, Block **o_vert, Block **o_gptr, lo
         if (!f_off || !f_vert || !f_gptr) { rc = TPG_ENOMEM; break; }
         if ((rc = ensure(g, g->s_i32[2], sizeof(int) * (T + 1)))) break;
         int *f_graph = g->s_i32[2].as<int>();
-        if (cuda_err(tp_gather(perm[cp], keep, keep_rank, P, (const long long *)tp_off->p, (const int *)tp_vert->p,
-                               tp_graph, keep_off, (long long *)f_off->p, (int *)f_vert->p, f_graph, s))) {
+        if (cuda_err(tp_assemble(perm[cp], keep, keep_rank, P, pp_off, pp_vert, pp_graph, g->gd,
+                                 (const long long *)tp_off->p, keep_off, (long long *)f_off->p, (int *)f_vert->p, f_graph,
+                                 s))) {
             rc = TPG_ECUDA;
             break;
         }
@@ -1356,7 +1358,7 @@ int capture_plan(tpg_cfg *g) {
     RC(ensure(g, p.nruns, sizeof(long long) * g->G));
     RC(ensure(g, p.bounds0, sizeof(long long) * (Pc + 1)));
     RC(ensure(g, p.tp_off0, sizeof(long long) * (Pc + 1)));
-    RC(ensure(g, p.tp_vert0, sizeof(int) * p.TV0_cap));
+    RC(ensure(g, p.tp_vert0, 16));  // (the raw TP list is never written: TPs are assembled in sorted order)
     RC(ensure(g, p.keep, sizeof(int) * Pc));
     RC(ensure(g, p.keep_off, sizeof(long long) * (Pc + 1)));
     RC(ensure(g, p.keep_rank, sizeof(long long) * (Pc + 1)));

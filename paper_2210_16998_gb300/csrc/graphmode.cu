@@ -257,6 +257,8 @@ struct TpParts {
 
 constexpr int TP_LANES = 8;  // lanes per TP in the write and gather kernels
 
+// The packed comparison keys of every TP, read from its parts (the TPs
+// themselves are assembled once, in sorted order, by gm_tp_gather).
 __global__ void __launch_bounds__(GMB) gm_tp_write(GmArgs a) {
     const long long P = gm_P_tp(a);
     const GraphDev &g = a.g;
@@ -274,9 +276,7 @@ __global__ void __launch_bounds__(GMB) gm_tp_write(GmArgs a) {
         t.pre = g.pre_seq + g.pre_off[f];
         t.pp = a.pp_vert + o0;
         t.suf = g.suf_seq + g.suf_off[l] + 1;
-        const long long d0 = a.tp_off0[i], total = a.tp_off0[i + 1] - d0;
-        int *dst = a.tp_vert0 + d0;
-        for (long long p = sub; p < total; p += TP_LANES) dst[p] = t.at(p);
+        const long long total = a.tp_off0[i + 1] - a.tp_off0[i];
         const long long k0 = a.key_off[i], nw = a.key_off[i + 1] - k0;
         for (long long w = sub; w < nw; w += TP_LANES) {
             unsigned long long word = 0;
@@ -359,16 +359,30 @@ __device__ __forceinline__ long long gm_P_final(const GmArgs &a) {
     return gm_P_tp(a);
 }
 
+// The kept TPs in sorted order, each assembled from its parts (prefix path,
+// PP, suffix path) straight into its final place: the TP list is never
+// written in PP order.
 __global__ void __launch_bounds__(GMB) gm_tp_gather(GmArgs a, int buf) {
     const long long P = gm_P_final(a);
     const long long *perm = a.perm[buf];
+    const GraphDev &g = a.g;
     const int sub = threadIdx.x & (TP_LANES - 1);
     const long long ngroups = (long long)gridDim.x * (GMB / TP_LANES);
     for (long long i = blockIdx.x * (long long)(GMB / TP_LANES) + (threadIdx.x / TP_LANES); i < P; i += ngroups) {
         if (!a.keep[i]) continue;
         const long long x = perm[i], rk = a.keep_rank[i];
-        const long long s0 = a.tp_off0[x], len = a.tp_off0[x + 1] - s0, d0 = a.keep_off[i];
-        for (long long p = sub; p < len; p += TP_LANES) a.tp_vert[d0 + p] = a.tp_vert0[s0 + p];
+        const long long o0 = a.pp_off[x], o1 = a.pp_off[x + 1];
+        const int gid = g.G > 1 ? a.pp_graph[x] : 0;
+        const int vb = g.vgraph ? g.vbase[gid] : 0;
+        const int f = a.pp_vert[o0] + vb, l = a.pp_vert[o1 - 1] + vb;
+        TpParts t;
+        t.pl = g.pre_len[f] - 1;
+        t.plen = o1 - o0;
+        t.pre = g.pre_seq + g.pre_off[f];
+        t.pp = a.pp_vert + o0;
+        t.suf = g.suf_seq + g.suf_off[l] + 1;
+        const long long len = a.tp_off0[x + 1] - a.tp_off0[x], d0 = a.keep_off[i];
+        for (long long p = sub; p < len; p += TP_LANES) a.tp_vert[d0 + p] = t.at(p);
         if (sub == 0) {
             a.tp_graph[rk] = a.tp_graph0[x];
             a.tp_off[rk] = d0;

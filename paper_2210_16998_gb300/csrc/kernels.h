@@ -188,7 +188,7 @@ struct GmArgs {
     long long *run_base, *nruns;  // [G]
     long long *bounds0;     // [P_cap+1]
     long long *tp_off0;     // [P_cap+1]
-    int *tp_vert0;          // [TV0_cap]
+    int *tp_vert0;          // unused: TPs are assembled from their parts in sorted order
     long long *key_off;     // [P_cap+1] word offsets of the packed TP keys
     unsigned long long *key;  // [K_cap] packed TP keys
     long long K_cap;

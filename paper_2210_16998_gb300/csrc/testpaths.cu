@@ -341,6 +341,100 @@ cudaError_t tp_index_map(const long long *perm, const int *keep, const long long
     return cudaGetLastError();
 }
 
+// A TP as its three parts: path(entry -> first p) without its last vertex,
+// the PP, path(last p -> exit) without its first vertex.
+struct TpView {
+    const int *pre, *pp, *suf;
+    long long pl, plen;
+    __device__ __forceinline__ int at(long long p) const {
+        if (p < pl) return pre[p];
+        if (p < pl + plen) return pp[p - pl];
+        return suf[p - pl - plen];
+    }
+};
+
+__device__ __forceinline__ TpView tp_view(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long i,
+                                          const GraphDev &g) {
+    const long long o0 = pp_off[i], o1 = pp_off[i + 1];
+    const int gid = pp_graph ? pp_graph[i] : 0;
+    const int vb = g.vgraph ? g.vbase[gid] : 0;
+    const int f = pp_vert[o0] + vb, l = pp_vert[o1 - 1] + vb;
+    TpView t;
+    t.pl = g.pre_len[f] - 1;
+    t.plen = o1 - o0;
+    t.pre = g.pre_seq + g.pre_off[f];
+    t.pp = pp_vert + o0;
+    t.suf = g.suf_seq + g.suf_off[l] + 1;
+    return t;
+}
+
+constexpr int TPV_LANES = 8;  // lanes per TP in the key and assembly kernels
+
+// packed keys of TP(p) for every PP p, read from the parts
+__global__ void keys_parts_kernel(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
+                                  GraphDev g, const long long *tp_off, int bits, const long long *key_off,
+                                  unsigned long long *key) {
+    const int sub = threadIdx.x & (TPV_LANES - 1), vpw = 64 / bits;
+    const long long ngroups = (long long)gridDim.x * (blockDim.x / TPV_LANES);
+    for (long long i = blockIdx.x * (long long)(blockDim.x / TPV_LANES) + (threadIdx.x / TPV_LANES); i < P;
+         i += ngroups) {
+        const TpView t = tp_view(pp_off, pp_vert, pp_graph, i, g);
+        const long long total = tp_off[i + 1] - tp_off[i];
+        const long long k0 = key_off[i], nw = key_off[i + 1] - k0;
+        for (long long w = sub; w < nw; w += TPV_LANES) {
+            unsigned long long word = 0;
+            for (int q = 0; q < vpw; ++q) {
+                const long long p = w * vpw + q;
+                word = (word << bits) | (p < total ? (unsigned long long)(t.at(p) + 1) : 0ull);
+            }
+            key[k0 + w] = word;
+        }
+    }
+}
+
+cudaError_t tp_write_keys_parts(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
+                                const GraphDev &g, const long long *tp_off, int bits, const long long *key_off,
+                                unsigned long long *key, cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    keys_parts_kernel<<<grid_for(P * TPV_LANES), 256, 0, s>>>(pp_off, pp_vert, pp_graph, P, g, tp_off, bits, key_off,
+                                                              key);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// the kept TPs in sorted order, each assembled from its parts straight into
+// its final place (the TP list is never written in PP order)
+__global__ void assemble_kernel(const long long *perm, const int *keep, const long long *keep_rank, long long P,
+                                const long long *pp_off, const int *pp_vert, const int *pp_graph, GraphDev g,
+                                const long long *tp_off, const long long *keep_off, long long *final_off,
+                                int *out_vert, int *out_graph) {
+    const int sub = threadIdx.x & (TPV_LANES - 1);
+    const long long ngroups = (long long)gridDim.x * (blockDim.x / TPV_LANES);
+    for (long long i = blockIdx.x * (long long)(blockDim.x / TPV_LANES) + (threadIdx.x / TPV_LANES); i < P;
+         i += ngroups) {
+        if (!keep[i]) continue;
+        const long long x = perm[i], r = keep_rank[i];
+        const TpView t = tp_view(pp_off, pp_vert, pp_graph, x, g);
+        const long long len = tp_off[x + 1] - tp_off[x], d0 = keep_off[i];
+        for (long long p = sub; p < len; p += TPV_LANES) out_vert[d0 + p] = t.at(p);
+        if (sub == 0) {
+            out_graph[r] = pp_graph ? pp_graph[x] : 0;
+            final_off[r] = d0;
+        }
+    }
+}
+
+cudaError_t tp_assemble(const long long *perm, const int *keep, const long long *keep_rank, long long P,
+                        const long long *pp_off, const int *pp_vert, const int *pp_graph, const GraphDev &g,
+                        const long long *tp_off, const long long *keep_off, long long *final_off, int *out_vert,
+                        int *out_graph, cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    assemble_kernel<<<grid_for(P * TPV_LANES), 256, 0, s>>>(perm, keep, keep_rank, P, pp_off, pp_vert, pp_graph, g,
+                                                            tp_off, keep_off, final_off, out_vert, out_graph);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // one warp per kept TP: copy into its final slot
 __global__ void tp_gather_kernel(const long long *perm, const int *keep, const long long *keep_rank, long long P,
                                  const long long *off, const int *vert, const int *graph,

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace tpg {
 
 // run_base[g] / nruns[g]: the first run of graph g and its number of runs,
@@ -33,6 +35,17 @@ cudaError_t tp_dedup_flags_keys(const long long *perm, long long P, const long l
                                 const unsigned long long *key, const int *tp_graph, long long *keep_len, int *keep,
                                 cudaStream_t s);
 
+// packed keys (as tp_write_keys) of TP(p) for every PP p, read from the
+// TP's parts (prefix path, PP, suffix path) instead of a written TP list;
+// tp_off holds the TPs' offsets (for their lengths)
+cudaError_t tp_write_keys_parts(const long long *pp_off, const int *pp_vert, const int *pp_graph, long long P,
+                                const GraphDev &g, const long long *tp_off, int bits, const long long *key_off,
+                                unsigned long long *key, cudaStream_t s);
+// as tp_gather, but every kept TP is assembled from its parts
+cudaError_t tp_assemble(const long long *perm, const int *keep, const long long *keep_rank, long long P,
+                        const long long *pp_off, const int *pp_vert, const int *pp_graph, const GraphDev &g,
+                        const long long *tp_off, const long long *keep_off, long long *final_off, int *out_vert,
+                        int *out_graph, cudaStream_t s);
 // map[perm[i]] = the final index of sorted TP i (keep_rank[i] if it is kept,
 // else that of the kept TP it duplicates, keep_rank[i] - 1); with perm null
 // the identity map[i] = i
