@@ -811,6 +811,7 @@ int enumerate_levels(tpg_cfg *g) {
         a.err = g->ctl.as<int>();
         a.stop_level = g->ctl.as<int>() + 1;
         a.bar = (unsigned *)(g->ctl.as<char>() + CTL_BAR_OFFSET);
+        a.handoff = (int *)(g->ctl.as<char>() + CTL_HANDOFF_OFFSET);
         a.root_counts = g->root_counts;
         a.spin_ns = g->spin_ns;
         a.trace = nullptr;

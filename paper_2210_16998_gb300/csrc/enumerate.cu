@@ -167,6 +167,141 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 #define TPG_ENUM_LANEWISE 1  // lane-wise child writing when it needs no more rounds than dealing
 #endif
 
+#ifndef TPG_ENUM_PROLOGUE
+#define TPG_ENUM_PROLOGUE 1  // a fresh run's small first levels run in block 0 alone
+#endif
+
+// The small first levels of a fresh run in one block.  A single graph's
+// first levels hold few paths (one per vertex, then a few more per level),
+// and with the whole grid each still costs a grid barrier and a prefix step
+// for a few microseconds of work.  Block 0 walks them alone while a level
+// holds at most BLOCK * PI paths: thread t takes a contiguous run of at most
+// PI paths of the level, evaluates them (count word: extending successors,
+// primality), one block scan places their children and PPs, the children
+// are written in order (parent order, ascending successor id, as in the
+// grid's levels), and __syncthreads separates the levels.  Every level makes
+// the grid's capacity checks and stops the same way (the flags, the stop
+// level, the level record).  Returns the level handed to the grid (the
+// first one above the bound, or an empty one), 0 after a stop.
+template <int W, int BLOCK, int PI, bool MASK>
+__device__ __forceinline__ int enum_prologue(const EnumArgs &a) {
+    const GraphDev &g = a.g;
+    const int tid = threadIdx.x;
+    int k = 1;
+    long long count = __ldcg(&a.levels[1].count);
+    int2 *lnodes = (int2 *)__ldcg((const unsigned long long *)&a.levels[1].nodes);
+    int *lpp = (int *)__ldcg((const unsigned long long *)&a.levels[1].pp);
+    while (count > 0 && count <= (long long)BLOCK * PI && k + 1 < a.max_levels) {
+        const unsigned long long t_start = a.trace ? global_ns() : 0ull;
+        int2 *const next = lnodes + count;
+        const long long next_off = next - a.seg, pp_off = lpp - a.pp_seg;
+        const int2 *in_fl = a.tfl[k & 1];
+        const unsigned *in_vis = a.tvis[k & 1];
+        int2 *out_fl = a.tfl[(k + 1) & 1];
+        unsigned *out_vis = a.tvis[(k + 1) & 1];
+        const int n = (int)count, q = (n + BLOCK - 1) / BLOCK;  // q <= PI
+        const int lo = min(tid * q, n), hi = min(lo + q, n);
+        int first[PI], last[PI], vb[PI];
+        unsigned vis[PI][W], cw[PI];
+#pragma unroll
+        for (int j = 0; j < PI; ++j) {
+            const int i = lo + j;
+            first[j] = last[j] = vb[j] = 0;
+            cw[j] = 0u;
+#pragma unroll
+            for (int w = 0; w < W; ++w) vis[j][w] = 0u;
+            if (i < hi) {
+                const int2 fl = __ldcg(in_fl + i);
+                // clamped into range before any use as an index (as in the grid's levels)
+                first[j] = (int)min((unsigned)fl.x, (unsigned)(g.N - 1));
+                last[j] = (int)min((unsigned)fl.y, (unsigned)(g.N - 1));
+#pragma unroll
+                for (int w = 0; w < W; ++w) vis[j][w] = __ldcg(in_vis + w * a.lvl_cap + i);
+            }
+        }
+        unsigned long long cp = 0;  // children << 32 | PPs of this thread's paths
+#pragma unroll
+        for (int j = 0; j < PI; ++j) {
+            if (lo + j < hi) {
+                vb[j] = g.vgraph ? __ldg(g.vbase + __ldg(g.vgraph + first[j])) : 0;
+                if constexpr (MASK) cw[j] = eval_mask<W>(g, k, first[j], last[j], vb[j], vis[j]);
+                else cw[j] = eval_path<W>(g, k, first[j], last[j], vb[j], vis[j], -1);
+                cp += ((unsigned long long)cnt_children(cw[j]) << 32) | (cw[j] >> 15);
+            }
+        }
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan_u64<BLOCK>(cp, tot);
+        const long long C = (long long)(tot >> 32), P = (long long)(tot & 0xffffffffull);
+        int e = 0;
+        if (C >= (long long)MAX31 || P >= (long long)MAX31) e |= ERR_OVF_COUNT;
+        if (next_off + C > a.seg_cap) e |= ERR_OVF_NODES;
+        if (C > a.lvl_cap) e |= ERR_OVF_LEVEL;
+        if (pp_off + P > a.pp_seg_cap) e |= ERR_OVF_PP;
+        if (k + 2 >= a.max_levels && C > 0) e |= ERR_OVF_LEVELS;
+        if (tid == 0) {
+            a.levels[k].pp_count = P;
+            a.levels[k].children = C;
+            if (e) {
+                *a.stop_level = k;
+                atomicOr(a.err, e);
+            } else {
+                LevelRec r = {};
+                r.nodes = next;
+                r.count = C;
+                r.pp = lpp + P;
+                a.levels[k + 1] = r;
+            }
+        }
+        if (e) return 0;
+        int pos_c = (int)(ex >> 32), pos_p = (int)(ex & 0xffffffffull);
+#pragma unroll
+        for (int j = 0; j < PI; ++j) {
+            const int i = lo + j;
+            if (i >= hi) continue;
+            if (cw[j] & CNT_PP) lpp[pos_p++] = i;
+            if (cnt_children(cw[j]) == 0) continue;
+            auto child = [&](int w) {
+                const int bb = w - vb[j];
+                next[pos_c] = make_int2(w, i);
+                out_fl[pos_c] = make_int2(first[j], w);
+                if (w != first[j]) {
+#pragma unroll
+                    for (int ww = 0; ww < W; ++ww)
+                        out_vis[ww * a.lvl_cap + pos_c] = vis[j][ww] | ((ww == (bb >> 5)) ? (1u << (bb & 31)) : 0u);
+                }
+                ++pos_c;
+            };
+            if constexpr (MASK) {
+                unsigned m[W];
+                ext_mask<W>(g, first[j], last[j], vb[j], vis[j], m);
+#pragma unroll
+                for (int ww = 0; ww < W; ++ww)
+                    for (unsigned x = m[ww]; x; x &= x - 1) child(vb[j] + 32 * ww + __ffs(x) - 1);
+            } else {
+                const int e0 = __ldg(g.rp + last[j]), e1 = __ldg(g.rp + last[j] + 1);
+                for (int ed = e0; ed < e1; ++ed) {
+                    const int w = __ldg(g.col + ed);
+                    if (w == first[j] || !test_bit<W>(vis[j], w - vb[j])) child(w);
+                }
+            }
+        }
+        if (a.trace && tid == 0) {
+            unsigned long long *tr = a.trace + LEVEL_TRACE_WORDS * k;
+            const unsigned long long t_end = global_ns();
+            atomicMax(tr, ~t_start);
+            atomicMax(tr + 1, t_end);
+            atomicAdd(tr + 2, t_end - t_start);
+            atomicAdd(tr + 3, 1ull);
+        }
+        __syncthreads();  // this level's records are read by other threads of the block next
+        count = C;
+        lnodes = next;
+        lpp += P;
+        ++k;
+    }
+    return k;
+}
+
 // paths per chunk of a level of `count` paths cut into nchk chunks:
 // ceil(count / nchk) rounded up to a multiple of 32
 __device__ __forceinline__ int level_chunk(long long count, int nchk) {
@@ -234,8 +369,9 @@ __device__ __forceinline__ void flush_counts(const AggSlots &A, int s, int own, 
 //
 // Slots rotate: level k reads slot k%3, accumulates into slot (k+1)%3, and
 // each block clears its group's entries of slot (k+2)%3, which nobody reads
-// or accumulates until after the next barrier.  The first level of a launch
-// (level 1 of a fresh run, or the level a resume starts at) is counted by a
+// or accumulates until after the next barrier.  The first level the grid
+// walks (level 1 of a fresh run, the level a resume starts at, or the level
+// handed over by the single-block start, enum_prologue) is counted by a
 // separate pass with a static chunk assignment.
 template <int W, int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_kernel(EnumArgs a) {
@@ -268,9 +404,24 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
         else return grid_barrier_count(a.bar, target, a.err, stop, a.spin_ns);
     };
 
+    // a fresh run's small first levels: block 0 alone, the grid waits once
+    int k_first = a.start_level;
+    if constexpr (TPG_ENUM_PROLOGUE) {
+        if (a.handoff && a.seed_level1 && a.start_level == 1 && !a.root_counts) {
+            constexpr int PI = (W <= 4 ? 4 : 2) * BLOCK <= 2048 ? (W <= 4 ? 4 : 2) : 2048 / BLOCK;
+            if (b == 0) {
+                const int k0 = enum_prologue<W, BLOCK, PI, MASK>(a);
+                if (tid == 0) *a.handoff = k0;
+            }
+            bar_target += G;
+            if (!enum_barrier(bar_target, ERR_TIMEOUT | ERR_OVERFLOW_MASK | ERR_OVF_COUNT | ERR_OVF_LEVELS)) return;
+            k_first = __ldcg(a.handoff);
+        }
+    }
+
     // ---- counting pass over the first level of this launch ----
     {
-        const int k = a.start_level;
+        const int k = k_first;
         const long long count = __ldcg(&a.levels[k].count);
         const int chunk = level_chunk(count, NC);
         const int2 *in_fl = a.tfl[k & 1];
@@ -336,10 +487,10 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
 
     // the level being processed; after the first, every block derives the
     // next level's record from the totals it computed itself
-    long long count = __ldcg(&a.levels[a.start_level].count);
-    int2 *lnodes = (int2 *)__ldcg((const unsigned long long *)&a.levels[a.start_level].nodes);
-    int *lpp = (int *)__ldcg((const unsigned long long *)&a.levels[a.start_level].pp);
-    for (int k = a.start_level; k + 1 < a.max_levels && count > 0; ++k) {
+    long long count = __ldcg(&a.levels[k_first].count);
+    int2 *lnodes = (int2 *)__ldcg((const unsigned long long *)&a.levels[k_first].nodes);
+    int *lpp = (int *)__ldcg((const unsigned long long *)&a.levels[k_first].pp);
+    for (int k = k_first; k + 1 < a.max_levels && count > 0; ++k) {
         int2 *const next = (k == a.start_level && a.next_nodes) ? a.next_nodes : lnodes + count;
         const long long next_off = next - a.seg;  // offset of the next level in the segment
         const long long pp_off = lpp - a.pp_seg;  // offset of this level's PPs in their segment

@@ -47,6 +47,7 @@ __host__ __device__ inline int cnt_children(unsigned cw) {
 constexpr int CTL_BYTES = 1024;
 constexpr int CTL_BAR_OFFSET = 256;
 constexpr int CTL_RANK_BAR_OFFSET = 512;  // grid barrier of the PP ranking
+constexpr int CTL_HANDOFF_OFFSET = 64;    // level a frontier launch's single-block start hands to the grid
 
 struct EnumArgs {
     GraphDev g;
@@ -72,6 +73,8 @@ struct EnumArgs {
     unsigned long long *root_counts;  // optional [3*N]: per first vertex, simple paths, PPs, PP vertices
     unsigned long long spin_ns;       // limit of every grid-barrier wait (SPIN_LIMIT_NS unless set)
     unsigned long long *trace;        // optional [LEVEL_TRACE_WORDS * max_levels] per-level timing
+    int *handoff;            // optional: on a fresh run, block 0 walks the small first levels alone and
+                             // leaves here the level the grid starts at (null: the grid does every level)
 };
 // per-level trace of a frontier launch, 4 words per level: ~(earliest block
 // start), latest warp end, summed busy time of the warps with work, number
