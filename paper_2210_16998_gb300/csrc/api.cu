@@ -971,7 +971,9 @@ int run_prime_paths(tpg_cfg *g) {
         RC(ensure(g, g->rank_noff, sizeof(long long) * (g->max_levels + 8)));
         RC(ensure(g, g->rank_bsum, sizeof(long long) * rank_pps_grid(g->num_sms)));
         CK(cudaMemsetAsync(g->ctl.p, 0, CTL_BYTES, s));
+        CK(cudaMemsetAsync(g->rank_cnt.p, 0, sizeof(int) * nodes, s));
         RankArgs r{};
+        r.cnt_zeroed = 1;
         r.levels = dlev;
         r.max_levels = g->max_levels;
         r.cnt = g->rank_cnt.as<int>();

@@ -146,6 +146,7 @@ struct RankArgs {
     int *err;             // ERR_INVAL (a capacity too small), ERR_TIMEOUT
     const int *skip;      // optional: nothing is done when (*skip & skip_mask)
     int skip_mask;
+    int cnt_zeroed;       // 1: cnt[0 .. all simple paths) is zero at launch (else the launch zeroes it)
 };
 // scratch of rank_pps beyond cnt/pre: noff [max_levels + 8], bsum [rank_pps_grid(num_sms)]
 int rank_pps_grid(int num_sms);
