@@ -184,7 +184,10 @@ __device__ __forceinline__ bool grid_barrier_count(unsigned *ctr, unsigned targe
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
+        // No full fences: the block's writes are ordered before the arrival
+        // by __syncthreads and the release, and the acquire load that sees
+        // the last arrival (then __syncthreads) orders every later read of
+        // the block after the other blocks' writes.
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
         if (ld_acquire_u32(ctr) < target) {
             const unsigned long long t0 = global_ns();
@@ -197,7 +200,6 @@ __device__ __forceinline__ bool grid_barrier_count(unsigned *ctr, unsigned targe
                 }
             }
         }
-        __threadfence();
         if (__ldcg(err) & stop) ok = 0;
         s_ok = ok;
     }
