@@ -85,39 +85,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).
-// bar[0] = arrival count, bar[1] = generation.  Every wait is bounded by
-// SPIN_LIMIT_NS; on expiry ERR_TIMEOUT is raised and false returned.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        unsigned gen = ld_acquire_u32(bar + 1);
-        __threadfence();
-        unsigned prev = atomicAdd(bar, 1u);
-        if (prev == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned long long t0 = global_ns();
-            while (ld_acquire_u32(bar + 1) == gen) {
-                __nanosleep(100);
-                if (global_ns() - t0 > SPIN_LIMIT_NS) {
-                    atomicOr(err, ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // Grid-wide barrier with tree arrival: a block arrives at one of
 // BAR_GROUPS group counters; the last block of a group arrives at the top
 // counter; the last group flips the generation that everyone else waits on.
