@@ -722,15 +722,48 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                     // one child record: arena node, frontier record with the
                     // child's own count word (evaluated here), bitset, and its
                     // share of the next level's chunk counts
-                    auto emit = [&](int w, int cpos, int pf, int pvb, const unsigned (&pvis)[W], int pi) {
+                    // fbm: the parent's first vertex as a W-word bitset (with
+                    // the vertex bitsets; a successor equal to it closes a cycle)
+                    auto emit = [&](int w, int cpos, int pf, int pvb, const unsigned (&pvis)[W], int pi,
+                                    const unsigned (&fbm)[W]) {
                         const bool closes = (w == pf);
                         const int bb = w - pvb;
                         unsigned cvis[W];  // the child's visited set
 #pragma unroll
                         for (int ww = 0; ww < W; ++ww) cvis[ww] = pvis[ww] | ((ww == (bb >> 5)) ? (1u << (bb & 31)) : 0u);
-                        unsigned c2w;
-                        if constexpr (MASK) c2w = eval_mask<W>(g, k + 1, pf, w, pvb, cvis);
-                        else c2w = eval_path<W>(g, k + 1, pf, w, pvb, pvis, w);
+                        // the child's count word (eval_mask / eval_path), with its
+                        // children and PP flag kept apart for the chunk counts
+                        unsigned c2w, cc, cp;
+                        if constexpr (MASK) {
+                            if (closes) {
+                                c2w = CNT_PP;
+                                cc = 0u;
+                                cp = 1u;
+                            } else {
+                                const unsigned *sm = g.smask + (long long)w * W;
+                                unsigned c = 0u;
+#pragma unroll
+                                for (int ww = 0; ww < W; ++ww) c += __popc(__ldg(sm + ww) & (~cvis[ww] | fbm[ww]));
+                                if (c) {
+                                    c2w = CNT_WIDE | c;
+                                    cc = c;
+                                    cp = 0u;
+                                } else {
+                                    // prime iff every predecessor of the first vertex is on it
+                                    const unsigned *pm = g.pmask + (long long)pf * W;
+                                    unsigned off = 0u;
+#pragma unroll
+                                    for (int ww = 0; ww < W; ++ww) off |= __ldg(pm + ww) & ~cvis[ww];
+                                    cp = off ? 0u : 1u;
+                                    c2w = off ? 0u : CNT_PP;
+                                    cc = 0u;
+                                }
+                            }
+                        } else {
+                            c2w = eval_path<W>(g, k + 1, pf, w, pvb, pvis, w);
+                            cc = (unsigned)cnt_children(c2w);
+                            cp = c2w >> 15;
+                        }
                         if (cpos < C) {  // holds when the counts agree; C fits the segment and the frontier
                             next[cpos] = make_int2(w, pi);
                             out_fl[cpos] = make_int2(pf, w);
@@ -750,9 +783,14 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                                 bound = (unsigned)(cur_own + 1) * (unsigned)chunk_n;
                                 acc_c = acc_p = 0;
                             }
-                            acc_c += (unsigned)cnt_children(c2w);
-                            acc_p += c2w >> 15;
+                            acc_c += cc;
+                            acc_p += cp;
                         }
+                    };
+                    auto first_bits = [&](int pf, int pvb, unsigned (&fbm)[W]) {
+                        const int fb = pf - pvb;
+#pragma unroll
+                        for (int ww = 0; ww < W; ++ww) fbm[ww] = (ww == (fb >> 5)) ? (1u << (fb & 31)) : 0u;
                     };
                     // Two ways to write the item's children.  Lane-wise: each
                     // lane writes its own path's children, one per round, for
@@ -769,9 +807,13 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                     // with the vertex bitsets, the extending successors as a
                     // bitset (none when the count word says so: a closed cycle)
                     unsigned xm[MASK ? W : 1];
+                    unsigned fbm_l[W];  // this lane's parent's first vertex (lane-wise writing)
                     if constexpr (MASK) {
+                        first_bits(first[j], vb_l, fbm_l);
                         if (nch > 0) {
-                            ext_mask<W>(g, first[j], last[j], vb_l, vis[j], xm);
+                            const unsigned *sm = g.smask + (long long)last[j] * W;
+#pragma unroll
+                            for (int ww = 0; ww < W; ++ww) xm[ww] = __ldg(sm + ww) & (~vis[j][ww] | fbm_l[ww]);
                         } else {
 #pragma unroll
                             for (int ww = 0; ww < W; ++ww) xm[ww] = 0u;
@@ -793,7 +835,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                                         w = vb_l + 32 * ww + __ffs(xm[ww]) - 1;
                                         xm[ww] &= xm[ww] - 1;
                                     }
-                                if (w >= 0) emit(w, pos_c + excl + r, first[j], vb_l, vis[j], pi);
+                                if (w >= 0) emit(w, pos_c + excl + r, first[j], vb_l, vis[j], pi, fbm_l);
                             }
                         } else {
                             unsigned m = cw[j] & CNT_BITS;
@@ -803,7 +845,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                                     m &= m - 1;
                                     // (clamped: a wrong count word must not index past the arcs)
                                     const int w = __ldg(g.col + min((unsigned)(e0_l + sidx), (unsigned)(g.M - 1)));
-                                    emit(w, pos_c + excl + r, first[j], vb_l, vis[j], pi);
+                                    emit(w, pos_c + excl + r, first[j], vb_l, vis[j], pi, fbm_l);
                                 }
                             }
                         }
@@ -838,7 +880,9 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                                         else rr -= c;
                                     }
                                 }
-                                if (w >= 0) emit(w, pos_c + q, pf, pvb, pvis, pi);
+                                unsigned fbm[W];
+                                first_bits(pf, pvb, fbm);
+                                if (w >= 0) emit(w, pos_c + q, pf, pvb, pvis, pi, fbm);
                                 continue;
                             }
                             const int pl = __shfl_sync(0xffffffffu, last[j], p);
@@ -863,7 +907,7 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
                                 }
                                 w = __ldg(g.col + (e < pe1 ? e : pe1 - 1));
                             }
-                            emit(w, pos_c + q, pf, pvb, pvis, pi);
+                            emit(w, pos_c + q, pf, pvb, pvis, pi, fbm_l);
                         }
                     }
                     if (pp) {
