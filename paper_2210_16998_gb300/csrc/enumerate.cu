@@ -596,17 +596,17 @@ __global__ void __launch_bounds__(BLOCK, W <= 8 ? 1024 / BLOCK : 1) enumerate_ke
         const int sub = ((chunk + SPLIT - 1) / SPLIT + 31) & ~31;
         long long ec, ep;
         int u = b + G * wid;
-        load_entries(u / SPLIT, ec, ep);
+        load_entries(SPLIT == 1 ? u : u / SPLIT, ec, ep);
         if (a.trace && lane == 0) s_t0[wid] = u < nunit ? global_ns() : 0ull;
         while (u < nunit) {
-            const int c = u / SPLIT, part = u - c * SPLIT;
+            const int c = SPLIT == 1 ? u : u / SPLIT, part = u - c * SPLIT;
             // the next unit is claimed, and its chunk entries load, while
             // this unit is processed
             int i_next = 0;
             if (lane == 0) i_next = atomicAdd(&s_next, 1);
             const int u_next = b + G * __shfl_sync(0xffffffffu, i_next, 0);
             long long ec_next, ep_next;
-            load_entries(u_next / SPLIT, ec_next, ep_next);
+            load_entries(SPLIT == 1 ? u_next : u_next / SPLIT, ec_next, ep_next);
             // offsets of chunk c: its group's prefix plus the chunks before it
             // in the group; its own entry is checked when its last part is done
             const int grp = c / CPG;
