@@ -24,7 +24,10 @@ namespace {
 
 constexpr int GMB = 256;      // threads per block of the streaming kernels
 constexpr int GM_ITEMS = 4;   // outputs per thread of the PP merge
-constexpr int TPM_ITEMS = 4;  // outputs per thread of the TP run merge
+#ifndef TPG_TPM_ITEMS
+#define TPG_TPM_ITEMS 4  // outputs per thread of a TP merge round
+#endif
+constexpr int TPM_ITEMS = TPG_TPM_ITEMS;  // outputs per thread of the TP run merge
 constexpr int GM_SCAN_ITEMS = 8;
 constexpr long long GM_SCAN_TILE = (long long)GMB * GM_SCAN_ITEMS;
 

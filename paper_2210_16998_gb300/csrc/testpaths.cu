@@ -164,7 +164,10 @@ cudaError_t tp_iota(long long *perm, long long P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-constexpr int TPM_ITEMS = 4;
+#ifndef TPG_TPM_ITEMS
+#define TPG_TPM_ITEMS 4  // outputs per thread of a TP merge round
+#endif
+constexpr int TPM_ITEMS = TPG_TPM_ITEMS;
 
 // largest s in [lo, hi] with a[s] <= x (a nondecreasing, a[lo] <= x)
 __device__ __forceinline__ long long tp_slot(const long long *a, long long lo, long long hi, long long x) {
